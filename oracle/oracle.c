@@ -1,0 +1,533 @@
+/*
+ * pCMD forward-model ORACLE -- test infrastructure only.
+ *
+ * A plain, slow CPU restatement of the pixel colour-magnitude-diagram forward model of
+ * Cook, Conroy, van Dokkum & Speagle (2019), Section 2.1 and Section 2.2, written to check the
+ * CUDA path against.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load it; the product library never links, calls or reads anything here, and this file
+ * includes no header of the product.
+ *
+ * Precision: weights, fluxes, dust, PSF, noise and magnitudes are FP64.  The Poisson sampler's
+ * decisions follow the sampler specification exactly (FP64 CDF for inversion, FP32 IEEE basic
+ * operations for transformed rejection) so that star counts can be compared bit for bit.
+ * Build with -ffp-contract=off and without -ffast-math: every float operation below is one
+ * IEEE-754 round-to-nearest operation in the order written.
+ *
+ * Sampler specification (the same one the CUDA path implements independently):
+ *   RNG      Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011, "Parallel random numbers: as easy
+ *            as 1, 2, 3"), key = 64-bit seed, counter = (pixel, index, set, tag).
+ *   tag      kind << 28 | half << 27 | sub;  kinds HI=1, LO=2, PTRS=3, DUST=4, NOISE=5.
+ *   uniform  u(w) = ((w >> 8) | 1) * 2^-24, exact in FP32, in (0, 1).
+ *   inversion (lambda < 10): x = hi16 << 16 | lo16 with hi16 / lo16 the (i & 7)-th 16-bit
+ *            slot of the HI / LO call with index i >> 3; v = (x + 0.5) 2^-32;
+ *            n = min{k : v < F_k}, F_k the FP64 Poisson CDF by p_k = p_{k-1} lambda / k,
+ *            capped at 64.
+ *   PTRS (lambda >= 10): Hormann (1993) transformed rejection with squeeze, attempts a use
+ *            words 2(a&1), 2(a&1)+1 of the PTRS call with sub = a >> 1; acceptance in the
+ *            deviance form of the log-pmf (Loader 2000), all in FP32 with the series log below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------------------- */
+/* Philox4x32-10: round function and key schedule as published by Salmon et al. (2011).   */
+/* ------------------------------------------------------------------------------------- */
+#define OR_PHILOX_M0 0xD2511F53u
+#define OR_PHILOX_M1 0xCD9E8D57u
+#define OR_PHILOX_W0 0x9E3779B9u
+#define OR_PHILOX_W1 0xBB67AE85u
+
+void or_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += OR_PHILOX_W0; k1 += OR_PHILOX_W1; }
+        uint64_t p0 = (uint64_t)OR_PHILOX_M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)OR_PHILOX_M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+enum { OR_KIND_HI = 1, OR_KIND_LO = 2, OR_KIND_PTRS = 3, OR_KIND_DUST = 4, OR_KIND_NOISE = 5 };
+
+static uint32_t or_tag(uint32_t kind, uint32_t half, uint32_t sub)
+{
+    return (kind << 28) | (half << 27) | sub;
+}
+
+static void or_call(uint64_t seed, uint32_t pix, uint32_t index, uint32_t set, uint32_t tag,
+                    uint32_t out[4])
+{
+    uint32_t ctr[4] = {pix, index, set, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox(ctr, key, out);
+}
+
+static uint32_t or_slot16(const uint32_t w[4], uint32_t j)
+{
+    uint32_t word = w[j >> 1];
+    return (j & 1u) ? (word >> 16) : (word & 0xFFFFu);
+}
+
+/* The 32-bit draw word of inversion entry (half, point i) at pixel pix. */
+uint32_t or_draw_word(uint64_t seed, uint32_t pix, uint32_t i, uint32_t set, uint32_t half)
+{
+    uint32_t whi[4], wlo[4];
+    or_call(seed, pix, i >> 3, set, or_tag(OR_KIND_HI, half, 0), whi);
+    or_call(seed, pix, i >> 3, set, or_tag(OR_KIND_LO, half, 0), wlo);
+    return (or_slot16(whi, i & 7u) << 16) | or_slot16(wlo, i & 7u);
+}
+
+float or_uniform(uint32_t w)
+{
+    return (float)((w >> 8) | 1u) * 0x1p-24f;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* FP32 natural log from basic operations: exponent split, mantissa reduced to            */
+/* [sqrt(1/2), sqrt(2)], atanh series ln m = 2 (s + s^3/3 + ... + s^11/11), s=(m-1)/(m+1) */
+/* (Abramowitz & Stegun 4.1.27).  Valid for finite normal x > 0.                          */
+/* ------------------------------------------------------------------------------------- */
+static float or_f32_from_bits(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static uint32_t or_bits_from_f32(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+float or_lnf(float x)
+{
+    const float SQRT2 = or_f32_from_bits(0x3FB504F3u);        /* fl32(sqrt 2) */
+    const float LN2_HI = 0.693145751953125f;                   /* 45426 / 2^16 */
+    const float LN2_LO = (float)(0.69314718055994530942 - 0.693145751953125);
+    const float C3 = (float)(1.0 / 3.0), C5 = (float)(1.0 / 5.0), C7 = (float)(1.0 / 7.0);
+    const float C9 = (float)(1.0 / 9.0), C11 = (float)(1.0 / 11.0);
+    uint32_t u = or_bits_from_f32(x);
+    int e = (int)(u >> 23) - 127;
+    float m = or_f32_from_bits((u & 0x007FFFFFu) | 0x3F800000u);
+    if (m > SQRT2) { m = m * 0.5f; e = e + 1; }
+    float num = m - 1.0f;
+    float den = m + 1.0f;
+    float s = num / den;
+    float z = s * s;
+    float p = C11;
+    p = p * z; p = p + C9;
+    p = p * z; p = p + C7;
+    p = p * z; p = p + C5;
+    p = p * z; p = p + C3;
+    float t = s * z;
+    t = t * p;
+    float lnm = s + t;
+    lnm = lnm + lnm;
+    float ef = (float)e;
+    float hi = ef * LN2_HI;
+    float lo = ef * LN2_LO;
+    float r = lnm + lo;
+    r = r + hi;
+    return r;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Poisson sampler                                                                        */
+/* ------------------------------------------------------------------------------------- */
+
+/* Inversion for lambda < 10: n = min{k : v < F_k}, v = (x + 0.5) 2^-32, FP64 CDF. */
+uint32_t or_poisson_inversion(float lam_f, uint32_t x)
+{
+    double lam = (double)lam_f;
+    double p = exp(-lam);
+    double F = p;
+    double v = ldexp((double)x + 0.5, -32);
+    uint32_t k = 0;
+    while (v >= F && k < 64u) {
+        k = k + 1u;
+        p = p * lam;
+        p = p / (double)k;
+        F = F + p;
+    }
+    return k;
+}
+
+/* Per-point constants of transformed rejection (Hormann 1993), FP64 rounded to FP32. */
+typedef struct { float lam, b, a, twoa, vr, log_ia; } or_ptrs_consts;
+
+void or_ptrs_setup(float lam_f, float out6[6])
+{
+    double lam = (double)lam_f;
+    double slam = sqrt(lam);
+    double b = 0.931 + 2.53 * slam;
+    double a = -0.059 + 0.02483 * b;
+    double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+    double vr = 0.9277 - 3.6224 / (b - 2.0);
+    out6[0] = lam_f;
+    out6[1] = (float)b;
+    out6[2] = (float)a;
+    out6[3] = (float)(2.0 * a);
+    out6[4] = (float)vr;
+    out6[5] = (float)log(inv_alpha);
+}
+
+/* stirlerr(k) = ln k! - (k ln k - k + 0.5 ln(2 pi k)): FP64 table for k < 16 (from lgamma),
+ * FP32 Stirling series 1/(12k) - 1/(360k^3) + 1/(1260k^5) above (DLMF 5.11.1). */
+static float or_stirlerr(float kf)
+{
+    if (kf < 16.0f) {
+        double k = (double)kf;
+        double s = lgamma(k + 1.0);
+        s = s - (k + 0.5) * log(k);
+        s = s + k;
+        s = s - 0.5 * log(2.0 * M_PI);
+        return (float)s;
+    }
+    const float S1 = (float)(1.0 / 12.0), S2 = (float)(1.0 / 360.0), S3 = (float)(1.0 / 1260.0);
+    float r = 1.0f / kf;
+    float r2 = r * r;
+    float t = r2 * S3;
+    t = S2 - t;
+    t = t * r2;
+    t = S1 - t;
+    return t * r;
+}
+
+/* phi(x) = (1 + x) ln(1 + x) - x, series sum_{n=2}^{13} (-1)^n x^n / (n (n-1)) for |x| < 1/4. */
+static float or_phi(float x)
+{
+    if (fabsf(x) < 0.25f) {
+        float c[14];
+        for (int n = 2; n <= 13; ++n)
+            c[n] = (float)(((n % 2 == 0) ? 1.0 : -1.0) / ((double)n * ((double)n - 1.0)));
+        float p = c[13];
+        for (int n = 12; n >= 2; --n) { p = p * x; p = p + c[n]; }
+        float r = p * x;
+        return r * x;
+    }
+    float y = 1.0f + x;
+    float r = y * or_lnf(y);
+    return r - x;
+}
+
+/* log Poisson pmf in the deviance form: -lambda phi((k-lambda)/lambda) - 0.5 ln(2 pi k)
+ * - stirlerr(k), the form that avoids cancelling k ln lambda against ln k! (Loader 2000). */
+float or_log_pmf(float kf, float lam)
+{
+    if (kf == 0.0f) return -lam;
+    const float HALF_LN_2PI = (float)0.91893853320467274178;
+    float d = kf - lam;
+    float x = d / lam;
+    float bd0 = lam * or_phi(x);
+    float st = or_stirlerr(kf);
+    float t = or_lnf(kf);
+    t = 0.5f * t;
+    t = t + HALF_LN_2PI;
+    float r = -bd0;
+    r = r - t;
+    r = r - st;
+    return r;
+}
+
+#define OR_PTRS_MAX_ATTEMPTS 1024u
+
+/* Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Returns the count,
+ * or UINT32_MAX if the attempt cap is reached. */
+uint32_t or_poisson_ptrs(const float c6[6], uint64_t seed, uint32_t pix, uint32_t i,
+                         uint32_t set, uint32_t half, uint32_t *attempts_out)
+{
+    const float lam = c6[0], b = c6[1], a = c6[2], twoa = c6[3], vr = c6[4], log_ia = c6[5];
+    uint32_t w[4];
+    for (uint32_t at = 0; at < OR_PTRS_MAX_ATTEMPTS; ++at) {
+        if ((at & 1u) == 0u) or_call(seed, pix, i, set, or_tag(OR_KIND_PTRS, half, at >> 1), w);
+        uint32_t wu = w[2u * (at & 1u)], wv = w[2u * (at & 1u) + 1u];
+        float U = or_uniform(wu) - 0.5f;
+        float V = or_uniform(wv);
+        float us = 0.5f - fabsf(U);
+        float t = twoa / us;
+        t = t + b;
+        t = t * U;
+        t = t + lam;
+        t = t + 0.43f;
+        float kf = floorf(t);
+        if (us >= 0.07f && V <= vr) { if (attempts_out) *attempts_out = at + 1; return (uint32_t)kf; }
+        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        if (kf > 1.0e9f) continue;
+        float q = us * us;
+        q = a / q;
+        q = q + b;
+        float lhs = or_lnf(V);
+        lhs = lhs + log_ia;
+        lhs = lhs - or_lnf(q);
+        if (lhs <= or_log_pmf(kf, lam)) { if (attempts_out) *attempts_out = at + 1; return (uint32_t)kf; }
+    }
+    if (attempts_out) *attempts_out = OR_PTRS_MAX_ATTEMPTS;
+    return UINT32_MAX;
+}
+
+/* One Poisson draw of entry (half, i) with FP32 mean lam at pixel pix (Section 2.1: the number
+ * of stars of every age-[Fe/H]-mass bin in every pixel is Poisson). */
+uint32_t or_draw(float lam, uint64_t seed, uint32_t pix, uint32_t i, uint32_t set, uint32_t half,
+                 int *err)
+{
+    if (lam == 0.0f) return 0u;
+    if (lam < 10.0f) return or_poisson_inversion(lam, or_draw_word(seed, pix, i, set, half));
+    float c6[6];
+    or_ptrs_setup(lam, c6);
+    uint32_t n = or_poisson_ptrs(c6, seed, pix, i, set, half, NULL);
+    if (n == UINT32_MAX) { if (err) *err = 1; return 0u; }
+    return n;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Model weights (Section 2.1, Section 2.2)                                               */
+/* ------------------------------------------------------------------------------------- */
+
+/* lambda[j][k][i] = SFH_j * MDF_k * IMF_jk,i in FP64, summing to Npix = sum_j SFH_j.
+ *  SFH_j  = 10^log_sfh[j]                      (S5: log stars per pixel formed in bin j)
+ *  MDF_k  = Gaussian density at the grid [Fe/H], normalised, weights < mdf_cut removed,
+ *           renormalised (M2/M3); feh_sigma <= 0 puts all weight on the nearest grid point
+ *  IMF_i  = integral of m^-slope over the mass cell of point i (cells bounded by geometric
+ *           midpoints), normalised over the isochrone (Salpeter slope 2.35).  */
+void or_weights(int n_ages, int n_feh, int n_mass, const double *mass, double slope,
+                const double *feh_grid, const double *log_sfh, double feh_mean,
+                double feh_sigma, double mdf_cut, double *lam_out)
+{
+    double *mdf = (double *)calloc((size_t)n_feh, sizeof(double));
+    if (feh_sigma > 0.0) {
+        double s = 0.0;
+        for (int k = 0; k < n_feh; ++k) {
+            double t = feh_grid[k] - feh_mean;
+            t = t / feh_sigma;
+            mdf[k] = exp(-0.5 * (t * t));
+            s = s + mdf[k];
+        }
+        double s2 = 0.0;
+        for (int k = 0; k < n_feh; ++k) {
+            mdf[k] = mdf[k] / s;
+            if (mdf[k] < mdf_cut) mdf[k] = 0.0;
+            s2 = s2 + mdf[k];
+        }
+        for (int k = 0; k < n_feh; ++k) mdf[k] = mdf[k] / s2;
+    } else {
+        int best = 0;
+        for (int k = 1; k < n_feh; ++k)
+            if (fabs(feh_grid[k] - feh_mean) < fabs(feh_grid[best] - feh_mean)) best = k;
+        mdf[best] = 1.0;
+    }
+    double *omega = (double *)malloc(sizeof(double) * (size_t)n_mass);
+    double *edge = (double *)malloc(sizeof(double) * (size_t)(n_mass + 1));
+    for (int j = 0; j < n_ages; ++j) {
+        double sfh = pow(10.0, log_sfh[j]);
+        for (int k = 0; k < n_feh; ++k) {
+            const double *m = mass + ((size_t)j * n_feh + k) * n_mass;
+            double s = 0.0;
+            if (n_mass == 1) {
+                omega[0] = 1.0;
+                s = 1.0;
+            } else {
+                for (int i = 1; i < n_mass; ++i) edge[i] = sqrt(m[i - 1] * m[i]);
+                edge[0] = m[0] * m[0] / edge[1];
+                edge[n_mass] = m[n_mass - 1] * m[n_mass - 1] / edge[n_mass - 1];
+                double a1 = 1.0 - slope;
+                for (int i = 0; i < n_mass; ++i) {
+                    double w;
+                    if (a1 != 0.0) {
+                        w = pow(edge[i + 1], a1) - pow(edge[i], a1);
+                        w = w / a1;
+                    } else {
+                        w = log(edge[i + 1] / edge[i]);
+                    }
+                    omega[i] = w;
+                    s = s + w;
+                }
+            }
+            double wjk = sfh * mdf[k];
+            double *out = lam_out + ((size_t)j * n_feh + k) * n_mass;
+            for (int i = 0; i < n_mass; ++i) out[i] = wjk * (omega[i] / s);
+        }
+    }
+    free(omega);
+    free(edge);
+    free(mdf);
+}
+
+/* Per-star flux in electrons: t_b 10^(-0.4 ((M_b + dmod) - ZP_b)), FP64 (Section 2.1, D1/D2). */
+void or_fluxes(int n_pts, int n_bands, const double *abs_mag, double dmod, const double *zp,
+               const double *exptime, double *flux_out)
+{
+    for (int i = 0; i < n_pts; ++i)
+        for (int b = 0; b < n_bands; ++b) {
+            double s = abs_mag[(size_t)i * n_bands + b] + dmod;
+            s = s - zp[b];
+            s = -0.4 * s;
+            double f = pow(10.0, s);
+            flux_out[(size_t)i * n_bands + b] = exptime[b] * f;
+        }
+}
+
+/* Split lambda between stars in front of (half 0) and behind (half 1) a thin dust screen
+ * that reddens a fraction f_dust of the stars (Section 2.2): independent Poisson draws with
+ * means (1 - f) lambda and f lambda.  Without dust, or f = 0, only half 0 is drawn; f = 1
+ * draws half 1 only.  lam_h[h * n + i] receives FP32 means (0 where a half is unused). */
+int or_halves(int n, const double *lam, int dust, double f_dust, float *lam_h)
+{
+    for (int i = 0; i < n; ++i) {
+        double l0, l1;
+        if (!dust || f_dust <= 0.0) { l0 = lam[i]; l1 = 0.0; }
+        else if (f_dust >= 1.0) { l0 = 0.0; l1 = lam[i]; }
+        else { l0 = lam[i] * (1.0 - f_dust); l1 = lam[i] * f_dust; }
+        lam_h[i] = (float)l0;
+        lam_h[(size_t)n + i] = (float)l1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Simulation of the raw (pre-PSF) image                                                  */
+/* ------------------------------------------------------------------------------------- */
+
+/* Dust screen factors of one pixel (Section 2.2 E1-E3): E(B-V) = 10^log_ebv exp(sigma z),
+ * z ~ N(0,1) by Box-Muller from the pixel's DUST call; factor_b = 10^(-0.4 R_b E). */
+static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_bands,
+                            double log_ebv, double dust_sigma, const double *r_ext, double *fac)
+{
+    double z = 0.0;
+    if (dust_sigma != 0.0) {
+        uint32_t w[4];
+        or_call(seed, pix, 0, set, or_tag(OR_KIND_DUST, 0, 0), w);
+        double u1 = (double)or_uniform(w[0]), u2 = (double)or_uniform(w[1]);
+        z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    }
+    double ebv = exp(log(10.0) * log_ebv + dust_sigma * z);
+    for (int b = 0; b < n_bands; ++b) fac[b] = pow(10.0, -0.4 * r_ext[b] * ebv);
+}
+
+/* Raw image [n_bands][n_im][n_im] (FP64) for pixels [pix_begin, pix_end) of one model:
+ * per pixel, draws for every entry of both halves, flux sums per band in FP64, the dust factor
+ * on the behind half.  counts (optional) receives n for every (pixel, half, point) as
+ * counts[(p - pix_begin) * 2 * n_pts + h * n_pts + i].  Returns nonzero on a sampler overrun. */
+int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, int n_im,
+                uint32_t pix_begin, uint32_t pix_end, uint32_t set, uint64_t seed, int dust,
+                double log_ebv, double dust_sigma, const double *r_ext, double *image,
+                uint32_t *counts, int n_threads)
+{
+    int err = 0;
+    size_t npix = (size_t)n_im * (size_t)n_im;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
+#endif
+    for (long long pl = (long long)pix_begin; pl < (long long)pix_end; ++pl) {
+        uint32_t p = (uint32_t)pl;
+        double F[2][8];
+        memset(F, 0, sizeof F);
+        for (uint32_t h = 0; h < 2; ++h)
+            for (uint32_t i = 0; i < (uint32_t)n_pts; ++i) {
+                float lam = lam_h[(size_t)h * n_pts + i];
+                int e = 0;
+                uint32_t n = or_draw(lam, seed, p, i, set, h, &e);
+                err |= e;
+                if (counts) counts[(size_t)(p - pix_begin) * 2u * n_pts + h * n_pts + i] = n;
+                if (n == 0u) continue;
+                for (int b = 0; b < n_bands; ++b) F[h][b] += (double)n * flux[(size_t)i * n_bands + b];
+            }
+        double fac[8];
+        if (dust) or_dust_factors(seed, p, set, n_bands, log_ebv, dust_sigma, r_ext, fac);
+        for (int b = 0; b < n_bands; ++b) {
+            double v = F[0][b] + (dust ? fac[b] * F[1][b] : F[1][b]);
+            if (image) image[(size_t)b * npix + p] = v;
+        }
+    }
+    (void)n_threads;
+    return err;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* PSF, noise, magnitudes, Hess diagram (Section 2.1 Panels E-F, Section 2.5)             */
+/* ------------------------------------------------------------------------------------- */
+
+/* Periodic convolution, FP64: out[y][x] = sum_{u,v} K[u][v] in[(y+R-u) mod N][(x+R-v) mod N]. */
+void or_psf(int n_im, int ksize, const float *kernel, const double *in, double *out)
+{
+    int R = ksize / 2;
+    for (int y = 0; y < n_im; ++y)
+        for (int x = 0; x < n_im; ++x) {
+            double s = 0.0;
+            for (int u = 0; u < ksize; ++u) {
+                int yy = ((y + R - u) % n_im + n_im) % n_im;
+                for (int v = 0; v < ksize; ++v) {
+                    int xx = ((x + R - v) % n_im + n_im) % n_im;
+                    s += (double)kernel[u * ksize + v] * in[(size_t)yy * n_im + xx];
+                }
+            }
+            out[(size_t)y * n_im + x] = s;
+        }
+}
+
+/* Photon and sky noise (noise = sqrt(counts), sky subtracted in expectation) and magnitudes.
+ * F' = F + sqrt(max(F + sky, 0)) z_b, z from Box-Muller of the pixel's NOISE call for band pair
+ * b >> 1 (cos for even b, sin for odd b).  m_b = ZP_b - 2.5 log10(F'_b / t_b) in FP64, rounded
+ * to FP32.  A pixel is valid when F'_0 > 0 and F'_1 > 0.  mag = m_0, colour = m_1 - m_0 (FP32). */
+void or_noise_mags(int n_im, int n_bands, const double *image, int noise, const double *sky,
+                   const double *zp, const double *exptime, uint32_t set, uint64_t seed,
+                   float *mag, float *colour, uint8_t *valid, double *fluxes_out)
+{
+    size_t npix = (size_t)n_im * (size_t)n_im;
+    for (size_t p = 0; p < npix; ++p) {
+        double Fp[8];
+        for (int b = 0; b < n_bands; ++b) {
+            double F = image[(size_t)b * npix + p];
+            if (noise) {
+                uint32_t w[4];
+                or_call(seed, (uint32_t)p, (uint32_t)(b >> 1), set, or_tag(OR_KIND_NOISE, 0, 0), w);
+                double u1 = (double)or_uniform(w[0]), u2 = (double)or_uniform(w[1]);
+                double r = sqrt(-2.0 * log(u1));
+                double z = (b & 1) ? r * sin(2.0 * M_PI * u2) : r * cos(2.0 * M_PI * u2);
+                double var = F + sky[b];
+                if (var < 0.0) var = 0.0;
+                F = F + sqrt(var) * z;
+            }
+            Fp[b] = F;
+            if (fluxes_out) fluxes_out[(size_t)b * npix + p] = F;
+        }
+        int ok = Fp[0] > 0.0 && Fp[1] > 0.0;
+        valid[p] = (uint8_t)ok;
+        if (!ok) { mag[p] = 0.0f; colour[p] = 0.0f; continue; }
+        float m0 = (float)(zp[0] - 2.5 * log10(Fp[0] / exptime[0]));
+        float m1 = (float)(zp[1] - 2.5 * log10(Fp[1] / exptime[1]));
+        mag[p] = m0;
+        colour[p] = m1 - m0;
+    }
+}
+
+/* Hess diagram with the FP32 bin rule ix = floor((colour - c_lo) * inv_w), iy likewise for the
+ * magnitude; hist[iy][ix].  counters[0] = valid pixels outside the grid, counters[1] = invalid
+ * pixels.  moments = {sum colour, sum mag, n_valid} over valid pixels, FP64. */
+void or_hess(size_t n, const float *mag, const float *colour, const uint8_t *valid, int nx,
+             int ny, double c_lo, double m_lo, double width, uint32_t *hist, uint32_t *counters,
+             double *moments)
+{
+    const float c_lo_f = (float)c_lo, m_lo_f = (float)m_lo, inv_w = (float)(1.0 / width);
+    memset(hist, 0, sizeof(uint32_t) * (size_t)nx * ny);
+    counters[0] = counters[1] = 0;
+    moments[0] = moments[1] = moments[2] = 0.0;
+    for (size_t p = 0; p < n; ++p) {
+        if (!valid[p]) { counters[1]++; continue; }
+        moments[0] += (double)colour[p];
+        moments[1] += (double)mag[p];
+        moments[2] += 1.0;
+        float cx = colour[p] - c_lo_f;
+        cx = cx * inv_w;
+        float my = mag[p] - m_lo_f;
+        my = my * inv_w;
+        float fx = floorf(cx), fy = floorf(my);
+        if (fx >= 0.0f && fx < (float)nx && fy >= 0.0f && fy < (float)ny)
+            hist[(size_t)fy * nx + (size_t)fx]++;
+        else
+            counters[0]++;
+    }
+}
