@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 pCMD forward model.
+
+One step = one full likelihood evaluation of the plain full model (256x256 image, 2 bands,
+7 SFH bins x 7 [Fe/H] x 300 masses, log10 Npix = 2, log-normal dust, 25x25 PSF, sky + photon
+noise, 100x100 Hess, Eq. 2-4 likelihood) through the C ABI: host table build, draws, dust,
+PSF, noise, magnitudes, Hess, likelihood; the likelihood value is read back every step.
+Every step uses a new RNG set id (a new realisation of the model).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the host cores on
+a bounded pixel sample of the same workload.  Under torchrun every rank evaluates its own
+models (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = ("plain full model: 256x256, 2 bands, 7 SFH x 7 [Fe/H] x 300 masses (14700 points), "
+            "log10 Npix 2, log-normal dust F_dust 0.5, 25x25 Moffat PSF, sky + photon noise, "
+            "100x100 Hess, Eq. 2-4 likelihood")
+METRIC = "model pixels/s (plain full model, one likelihood evaluation per step)"
+PEAK_ISSUE_PER_SM_CLK = 128          # 4 schedulers x 32 lanes: thread-instructions per clock
+OPS_PER_INV_DRAW = 6.0               # 1/8 Philox4x32-10 block (40 instr) + 16-bit compare
+OPS_PER_PTRS_DRAW = 60.0             # 1/2 Philox block + ~40 FP32 ops of the squeeze test
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", type=int, default=1, help="also time the batched path")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != self.idx:
+                    continue
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------------------
+def oracle_step(w, n_pix_sample: int, crop: int, set_id: int, n_threads: int):
+    """The oracle's forward model on a bounded sample: draws + dust for n_pix_sample pixels of
+    the full image, PSF + noise + magnitudes + Hess for a crop x crop image; returns seconds
+    per pixel."""
+    import oracle as O
+    t0 = time.perf_counter()
+    O.simulate(w, 0, set_id, pix_begin=0, pix_end=n_pix_sample, n_threads=n_threads)
+    t1 = time.perf_counter()
+    img = np.random.default_rng(set_id).exponential(1e4, size=(w.n_bands, crop * crop))
+    conv = O.psf(img, w.psf, crop)
+    mag, col, valid, _ = O.noise_mags(w, conv, crop, set_id)
+    O.hess(w, mag, col, valid)
+    t2 = time.perf_counter()
+    return (t1 - t0) / n_pix_sample + (t2 - t1) / (crop * crop)
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    n_pix = 1024
+    per_px = []
+    t_start = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_start < budget_s or k < 1:
+        per_px.append(oracle_step(w, n_pix, 32, 10 + k, cores))
+        k += 1
+    v = 1.0 / statistics.median(per_px)
+    return {"value": v, "unit": "model pixels/s", "cores": cores, "kind": "oracle",
+            "sample": "%d steps of: draws+dust for %d of the 65536 pixels (OpenMP over pixels, %d "
+                      "threads) + PSF/noise/mags/Hess of a 32x32 image, scaled per pixel"
+                      % (k, n_pix, cores)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1904_00011_gb300 import workloads as W
+    import oracle as O
+    O.build()
+    w = W.full()
+    cores = os.cpu_count() or 1
+    n_pix = 1024
+    for i in range(args.warmup):
+        oracle_step(w, 256, 16, 100 + i, cores)
+    t = []
+    for i in range(args.steps):
+        t.append(oracle_step(w, n_pix, 32, 200 + i, cores) * 65536)
+    total = sum(t)
+    value = args.steps * 65536 / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "model pixels/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_im": 256, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "model pixels/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: draws+dust for %d of 65536 pixels + PSF/noise/"
+                                       "mags/Hess of a 32x32 image, scaled to the full image" % n_pix},
+            "e2e": {"value": value, "unit": "model pixels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------------------
+def algorithmic_ops(sim, params):
+    lam, _, _ = sim.tables(params)
+    inv = int(((lam > 0) & (lam < 10)).sum())
+    ptrs = int((lam >= 10).sum())
+    return inv * OPS_PER_INV_DRAW + ptrs * OPS_PER_PTRS_DRAW, inv, ptrs
+
+
+def run_gb300(args, world, rank, local):
+    import torch
+    import paper_1904_00011_gb300 as P
+    from paper_1904_00011_gb300 import build as B
+    from paper_1904_00011_gb300 import workloads as W
+
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = W.full()
+    n = w.n_im
+    npix = n * n
+    sim = P.Simulator(w, max_sets=1)
+    # the data: another realisation of the model (set ids far from the timed ones)
+    sim.simulate(w.params, [n], 1_000_000 + rank)
+    mh, mm, mc, _ = sim.hess(1, [n])
+    torch.cuda.synchronize()
+    mock_hess = mh[0].clone()
+    mock_mom = mm[0].cpu().numpy().copy()
+    mock_host = mock_hess.cpu().pin_memory()
+    mode = W.LL_PAPER
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    base_id = rank * 10_000_000
+
+    for i in range(args.warmup):
+        sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode, first_set_id=base_id + i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    clocks.start()
+    sim.profile(True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lls = []
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the interval)
+        ev0[i].record(stream)
+        ll = sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode,
+                          first_set_id=base_id + args.warmup + i)
+        ev1[i].record(stream)
+        lls.append(float(ll[0]))
+    torch.cuda.synchronize()
+    kt = sim.kernel_times()
+    sim.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    # end to end through the ABI from host buffers: mock Hess H2D from pinned memory each step
+    e2e_ms = []
+    for i in range(max(3, args.steps // 3)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mock_hess.copy_(mock_host, non_blocking=True)
+        ll = sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode,
+                          first_set_id=base_id + 5_000_000 + i)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms, sum(e2e_ms) / len(e2e_ms)], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_step = float(t[0]), float(t[1])
+    else:
+        e2e_step = sum(e2e_ms) / len(e2e_ms)
+
+    extras = {}
+    if args.extras and rank == 0:
+        extras["batched"] = run_batched(sim, P, W, torch)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+    value = world * args.steps * npix / (total_ms / 1e3)
+    evals = world * args.steps / (total_ms / 1e3)
+    draw_ms, draw_n = kt["draw"]
+    ops, n_inv, n_ptrs = algorithmic_ops(sim, w.params[0])
+    per_launch = ops * npix
+    avg_draw_s = (draw_ms / max(draw_n, 1)) / 1e3
+    peak = 152 * PEAK_ISSUE_PER_SM_CLK * 2070e6 / 1e12   # Tinstr/s at the maximum SM clock
+    achieved = per_launch / avg_draw_s / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+    launches_per_step = {k: c / args.steps for k, (ms, c) in kt.items() if c}
+    line = {
+        "metric": METRIC, "value": value, "unit": "model pixels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_im": n, "points": w.iso.n_points,
+                   "draw_entries_per_pixel": n_inv + n_ptrs, "ptrs_entries_per_pixel": n_ptrs,
+                   "l2": "flushed between timed steps (256 MB write outside the timed interval)",
+                   "launch": {"block": 256, "split": 4, "chunk": 64}},
+        "loglike_evals_per_s": evals,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "draw_kernel<2,false,IMAGE>",
+                     "avg_launch_ms": avg_draw_s * 1e3,
+                     "algorithmic": "%g instr/pixel = %d inversion draws x %g + %d PTRS draws x %g"
+                                    % (ops, n_inv, OPS_PER_INV_DRAW, n_ptrs, OPS_PER_PTRS_DRAW),
+                     "peak_basis": "152 SMs x 128 issue slots/clk x 2070 MHz (issue-slot roofline)"},
+        "kernel_ms_per_step": {k: ms / args.steps for k, (ms, c) in kt.items() if c},
+        "gpu_launches": int(round(sum(c for (ms, c) in kt.values()))),
+        "launches_per_step": launches_per_step,
+        "e2e": {"value": world * npix / (e2e_step / 1e3), "unit": "model pixels/s",
+                "h2d_bytes_per_step": int(mock_hess.numel() * 4 + 168),
+                "d2h_bytes_per_step": 8},
+        "clocks": clk,
+        "loglike_sample": lls[:3],
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def run_batched(sim_plain, P, W, torch):
+    """The batched path: 512 sampler live points with uneven images (128..512) and log10 Npix
+    1..6 in one graph-replayed persistent launch, Poisson likelihood against a mock."""
+    w = W.batch()
+    sim = P.Simulator(w, max_sets=w.n_sets)
+    mp = W.batch_mock_params()
+    wm = W.with_params(w, [mp], [256])
+    ms = P.Simulator(wm, max_sets=1, max_im=256)
+    ms.simulate([mp], [256], 777_777)
+    h, m, c, _ = ms.hess(1, [256])
+    torch.cuda.synchronize()
+    mock = h[0].clone()
+    mom = m[0].cpu().numpy().copy()
+    for i in range(2):
+        sim.evaluate(w.params, w.n_ims, mock, mom, 256 * 256, W.LL_POISSON, first_set_id=i * 1000)
+    torch.cuda.synchronize()
+    sim.profile(True)
+    t = []
+    reps = 5
+    for i in range(reps):
+        t0 = time.perf_counter()
+        sim.evaluate(w.params, w.n_ims, mock, mom, 256 * 256, W.LL_POISSON, first_set_id=10_000 + i * 1000)
+        t.append(time.perf_counter() - t0)
+    kt = sim.kernel_times()
+    sim.profile(False)
+    step = statistics.median(t)
+    pix = sum(n * n for n in w.n_ims)
+    return {"workload": "512 sets, images 128..512 (step 16), log10 Npix U[1,6], dmod U[22,26], "
+                        "log E(B-V) U[-1,0], 200-point isochrone, Poisson likelihood",
+            "evals_per_s": w.n_sets / step, "model_pixels_per_s": pix / step, "ms_per_batch": 1e3 * step,
+            "graph_ms_per_batch": kt["graph"][0] / max(1, kt["graph"][1])}
+
+
+def main():
+    args = _args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_gb300(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,775 @@
+// C ABI of libpcmd (declared in include/pcmd.h): contexts, argument checks, table upload and
+// the launch sequence of the forward model.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pcmd.h"
+#include "pcmd_internal.h"
+#include "tables.h"
+
+namespace pcmd {
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int block, size_t smem);
+}
+
+using namespace pcmd;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMallocHost(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+}  // namespace
+
+struct pcmd_ctx {
+    pcmd_config cfg;
+    Model model;
+    std::vector<float> psf;     // [B][S][S]
+    std::vector<float> psf25;   // [kMaxBands][625] when S == 25
+    cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    int device = 0, n_sm = 1;
+    int block = 256, split = 4, chunk = 64;
+
+    DevBuf tables, desc, items, order, partials, part_begin, part_count, image, pix_off, hess,
+        moments, counters, ll, psf_d, queue, err;
+    HostBuf h_tables, h_desc, h_items, h_order, h_meta, h_ll;
+    cudaEvent_t staged = nullptr;
+    bool staged_pending = false;
+    std::vector<uint8_t> tab;
+    std::vector<SetDesc> descs;
+    std::vector<SetStats> stats;
+    std::vector<uint2> item_list;
+    std::vector<uint32_t> order_list;
+
+    int n_sets = 0;
+    std::vector<int> n_im;
+    float *img_ptr = nullptr;
+    bool have_images = false, have_hess = false;
+    uint32_t *hess_ptr = nullptr;
+    double *mom_ptr = nullptr;
+    uint32_t *ctr_ptr = nullptr;
+
+    // graph of the fused evaluation
+    cudaGraphExec_t gexec = nullptr;
+    size_t gkey[12] = {0};
+
+    // kernel timing (pcmd_profile)
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PCMD_KERNEL_KINDS];
+
+    std::string err_text;
+};
+
+// Brackets one kernel launch with events on the context's stream while profiling is on.
+struct KTimer {
+    pcmd_ctx *ctx;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(pcmd_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k) {
+        if (!ctx->profiling) return;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+    }
+    void done(cudaStream_t st) {
+        if (!a) return;
+        cudaEventRecord(b, st);
+        ctx->ev[kind].push_back({a, b});
+        a = b = nullptr;
+    }
+};
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ctx->err_text = std::string(#call) + ": " + cudaGetErrorString(e_);     \
+            return e_ == cudaErrorMemoryAllocation ? PCMD_ERR_OOM : PCMD_ERR_CUDA;  \
+        }                                                                           \
+    } while (0)
+
+static pcmd_status arg_error(pcmd_ctx *ctx, const std::string &why) {
+    if (ctx) ctx->err_text = why;
+    return PCMD_ERR_ARG;
+}
+
+static bool is_fin(double v) { return std::isfinite(v); }
+
+static PixelConsts pixel_consts(const pcmd_ctx *ctx) {
+    const pcmd_config &c = ctx->cfg;
+    PixelConsts pc;
+    std::memset(&pc, 0, sizeof pc);
+    for (int b = 0; b < kMaxBands; ++b) {
+        const bool on = b < c.n_bands;
+        pc.sky[b] = on ? (float)c.sky[b] : 0.0f;
+        pc.t[b] = on ? (float)c.exptime[b] : 1.0f;
+        pc.zp[b] = on ? (float)c.zeropoint[b] : 0.0f;
+        pc.zp_lo[b] = on ? (float)(c.zeropoint[b] - (double)pc.zp[b]) : 0.0f;
+    }
+    pc.c_lo = (float)c.hess_c_lo;
+    pc.m_lo = (float)c.hess_m_lo;
+    pc.inv_w = (float)(1.0 / c.hess_width);
+    pc.nx = c.hess_nx;
+    pc.ny = c.hess_ny;
+    pc.noise = (c.flags & PCMD_FLAG_NOISE) ? 1 : 0;
+    pc.seed = c.seed;
+    return pc;
+}
+
+static pcmd_status check_params(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, const int *n_im) {
+    if (!p || !n_im) return arg_error(ctx, "params and n_im must not be NULL");
+    if (n_sets < 1 || n_sets > ctx->cfg.max_sets) return arg_error(ctx, "n_sets outside 1..max_sets");
+    for (int s = 0; s < n_sets; ++s) {
+        if (n_im[s] < 1 || n_im[s] > ctx->cfg.max_im) return arg_error(ctx, "n_im outside 1..max_im");
+        for (int j = 0; j < ctx->model.n_ages; ++j)
+            if (!is_fin(p[s].log_sfh[j]) || p[s].log_sfh[j] > 7.0)
+                return arg_error(ctx, "log_sfh must be finite and <= 7 (lambda must stay below 1e7)");
+        if (!is_fin(p[s].feh_mean) || !is_fin(p[s].feh_sigma) || !is_fin(p[s].log_ebv) ||
+            !is_fin(p[s].dust_sigma) || !is_fin(p[s].dmod))
+            return arg_error(ctx, "non-finite parameter");
+        if (p[s].dust_sigma < 0.0 || p[s].dust_sigma > 5.0) return arg_error(ctx, "dust_sigma outside [0, 5]");
+        if (p[s].log_ebv > 2.0 || p[s].log_ebv < -20.0) return arg_error(ctx, "log_ebv outside [-20, 2]");
+    }
+    return PCMD_OK;
+}
+
+// Build the tables of n_sets models and stage them (host pinned -> device) on the stream.
+// Items are pixel tiles of block / split pixels; `cost_sorted` orders the queue longest first.
+static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, const int *n_im,
+                              uint32_t first_set_id, bool cost_sorted, int ppc) {
+    const int B = ctx->model.n_bands;
+    ctx->tab.clear();
+    ctx->descs.assign(n_sets, SetDesc());
+    ctx->stats.assign(n_sets, SetStats());
+    ctx->item_list.clear();
+    uint64_t img_off = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        SetDesc &d = ctx->descs[s];
+        std::memset(&d, 0, sizeof d);
+        build_set_tables(ctx->model, p[s], ctx->tab, d, ctx->stats[s]);
+        d.n_im = (uint32_t)n_im[s];
+        d.set_id = first_set_id + (uint32_t)s;
+        d.img_off = img_off;
+        img_off += (uint64_t)B * n_im[s] * n_im[s];
+        const uint32_t npix = (uint32_t)n_im[s] * (uint32_t)n_im[s];
+        d.item_begin = (uint32_t)ctx->item_list.size();
+        d.n_items = (npix + ppc - 1) / ppc;
+        for (uint32_t t = 0; t < d.n_items; ++t) ctx->item_list.push_back(make_uint2((uint32_t)s, t));
+    }
+    if (ctx->tab.empty()) ctx->tab.resize(16, 0);
+    const size_t n_items = ctx->item_list.size();
+    ctx->order_list.resize(n_items);
+    std::iota(ctx->order_list.begin(), ctx->order_list.end(), 0u);
+    if (cost_sorted && n_sets > 1) {
+        std::stable_sort(ctx->order_list.begin(), ctx->order_list.end(), [&](uint32_t a, uint32_t b) {
+            return ctx->stats[ctx->item_list[a].x].cost_per_pixel >
+                   ctx->stats[ctx->item_list[b].x].cost_per_pixel;
+        });
+    }
+    if (ctx->staged_pending) {
+        CK(cudaEventSynchronize(ctx->staged));
+        ctx->staged_pending = false;
+    }
+    CK(ctx->h_tables.ensure(ctx->tab.size()));
+    CK(ctx->h_desc.ensure(sizeof(SetDesc) * n_sets));
+    CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
+    CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
+    CK(ctx->tables.ensure(ctx->tab.size()));
+    CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
+    CK(ctx->items.ensure(sizeof(uint2) * n_items));
+    CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
+    std::memcpy(ctx->h_tables.p, ctx->tab.data(), ctx->tab.size());
+    std::memcpy(ctx->h_desc.p, ctx->descs.data(), sizeof(SetDesc) * n_sets);
+    std::memcpy(ctx->h_items.p, ctx->item_list.data(), sizeof(uint2) * n_items);
+    std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
+    CK(cudaMemcpyAsync(ctx->tables.p, ctx->h_tables.p, ctx->tab.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaEventRecord(ctx->staged, ctx->st));
+    ctx->staged_pending = true;
+    ctx->n_sets = n_sets;
+    ctx->n_im.assign(n_im, n_im + n_sets);
+    return PCMD_OK;
+}
+
+static DrawArgs base_draw_args(pcmd_ctx *ctx) {
+    DrawArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.tables = ctx->tables.as<uint8_t>();
+    a.desc = ctx->desc.as<SetDesc>();
+    a.items = ctx->items.as<uint2>();
+    a.order = ctx->order.as<uint32_t>();
+    a.n_items = (uint32_t)ctx->item_list.size();
+    a.queue = ctx->queue.as<uint32_t>();
+    a.seed = ctx->cfg.seed;
+    a.err = ctx->err.as<uint32_t>();
+    a.chunk = ctx->chunk;
+    a.split = ctx->split;
+    a.n_points = (uint32_t)ctx->model.n_points();
+    a.pc = pixel_consts(ctx);
+    return a;
+}
+
+static pcmd_status launch_draw_mode(pcmd_ctx *ctx, DrawArgs &a, int mode) {
+    const int B = ctx->model.n_bands;
+    const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
+    const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, mode, ctx->cfg.hess_nx,
+                                        ctx->cfg.hess_ny);
+    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->block, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = std::min<int>((int)a.n_items, per_sm * ctx->n_sm);
+    if (grid < 1) grid = 1;
+    CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->st));
+    KTimer t(ctx, PCMD_K_DRAW, ctx->st);
+    CK(launch_draw(a, B, kahan, mode, grid, ctx->block, smem, ctx->st));
+    t.done(ctx->st);
+    return PCMD_OK;
+}
+
+extern "C" {
+
+pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
+    if (!out) return PCMD_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return PCMD_ERR_ARG;
+    const pcmd_config &c = *cfg;
+    if (c.n_bands < 2 || c.n_bands > PCMD_MAX_BANDS) return PCMD_ERR_ARG;
+    if (c.n_ages < 1 || c.n_ages > PCMD_MAX_SFH || c.n_feh < 1 || c.n_mass < 1) return PCMD_ERR_ARG;
+    if ((long long)c.n_ages * c.n_feh * c.n_mass > (1LL << 24)) return PCMD_ERR_ARG;
+    if (!c.feh_grid || !c.mass || !c.abs_mag) return PCMD_ERR_ARG;
+    if (!is_fin(c.imf_slope) || !is_fin(c.f_dust) || c.f_dust < 0.0 || c.f_dust > 1.0) return PCMD_ERR_ARG;
+    if (!is_fin(c.mdf_cut) || c.mdf_cut < 0.0 || c.mdf_cut >= 1.0) return PCMD_ERR_ARG;
+    if (c.hess_nx < 1 || c.hess_ny < 1 || (long long)c.hess_nx * c.hess_ny > 40000) return PCMD_ERR_ARG;
+    if (!(c.hess_width > 0.0) || !is_fin(c.hess_c_lo) || !is_fin(c.hess_m_lo)) return PCMD_ERR_ARG;
+    if (c.max_im < 1 || c.max_im > 16384 || c.max_sets < 1 || c.max_sets > 65535) return PCMD_ERR_ARG;
+    if (c.psf && (c.psf_size < 1 || c.psf_size > PCMD_MAX_PSF || (c.psf_size & 1) == 0)) return PCMD_ERR_ARG;
+    const size_t P = (size_t)c.n_ages * c.n_feh * c.n_mass;
+    for (int b = 0; b < c.n_bands; ++b)
+        if (!(c.exptime[b] > 0.0) || !is_fin(c.zeropoint[b]) || !is_fin(c.sky[b]) || c.sky[b] < 0.0 ||
+            !is_fin(c.r_ext[b]))
+            return PCMD_ERR_ARG;
+    for (size_t i = 0; i < P; ++i) {
+        if (!(c.mass[i] > 0.0) || !is_fin(c.mass[i])) return PCMD_ERR_ARG;
+        if (i % c.n_mass && !(c.mass[i] > c.mass[i - 1])) return PCMD_ERR_ARG;
+        for (int b = 0; b < c.n_bands; ++b)
+            if (!is_fin(c.abs_mag[i * c.n_bands + b])) return PCMD_ERR_ARG;
+    }
+    for (int k = 0; k < c.n_feh; ++k)
+        if (!is_fin(c.feh_grid[k])) return PCMD_ERR_ARG;
+
+    pcmd_ctx *ctx = new pcmd_ctx();
+    ctx->cfg = c;
+    Model &m = ctx->model;
+    m.n_bands = c.n_bands;
+    m.n_ages = c.n_ages;
+    m.n_feh = c.n_feh;
+    m.n_mass = c.n_mass;
+    m.feh.assign(c.feh_grid, c.feh_grid + c.n_feh);
+    m.mass.assign(c.mass, c.mass + P);
+    m.abs_mag.assign(c.abs_mag, c.abs_mag + P * c.n_bands);
+    m.imf_slope = c.imf_slope;
+    m.mdf_cut = c.mdf_cut;
+    m.f_dust = c.f_dust;
+    m.dust = (c.flags & PCMD_FLAG_DUST) != 0;
+    for (int b = 0; b < kMaxBands; ++b) {
+        m.exptime[b] = b < c.n_bands ? c.exptime[b] : 1.0;
+        m.zeropoint[b] = b < c.n_bands ? c.zeropoint[b] : 0.0;
+        m.r_ext[b] = b < c.n_bands ? c.r_ext[b] : 0.0;
+    }
+    m.build_imf();
+    ctx->cfg.feh_grid = nullptr;
+    ctx->cfg.mass = nullptr;
+    ctx->cfg.abs_mag = nullptr;
+    ctx->cfg.log_age = nullptr;
+    ctx->cfg.psf = nullptr;
+    if (c.psf) {
+        ctx->psf.assign(c.psf, c.psf + (size_t)c.n_bands * c.psf_size * c.psf_size);
+        if (c.psf_size == 25) {
+            ctx->psf25.assign((size_t)kMaxBands * 625, 0.0f);
+            std::copy(ctx->psf.begin(), ctx->psf.end(), ctx->psf25.begin());
+        }
+    }
+    ctx->st = (cudaStream_t)c.stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        delete ctx;
+        return PCMD_ERR_CUDA;
+    }
+    float st16[16];
+    stirlerr_table(st16);
+    pcmd_status rc = PCMD_OK;
+    do {
+        if (upload_stirlerr(st16) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        if (cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        if (cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        if (ctx->err.ensure(sizeof(uint32_t)) != cudaSuccess || ctx->queue.ensure(sizeof(uint32_t)) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+        if (cudaMemset(ctx->err.p, 0, sizeof(uint32_t)) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        if (!ctx->psf.empty()) {
+            if (ctx->psf_d.ensure(ctx->psf.size() * 4) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+            if (cudaMemcpy(ctx->psf_d.p, ctx->psf.data(), ctx->psf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        }
+        if (ctx->h_ll.ensure(sizeof(double) * c.max_sets) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+        if (ctx->h_meta.ensure(sizeof(uint64_t) * (size_t)c.max_sets * 3) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+    } while (0);
+    if (rc != PCMD_OK) {
+        pcmd_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return PCMD_OK;
+}
+
+void pcmd_destroy(pcmd_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (int k = 0; k < PCMD_KERNEL_KINDS; ++k)
+        for (auto &pr : ctx->ev[k]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    DevBuf *bufs[] = {&ctx->tables, &ctx->desc, &ctx->items, &ctx->order, &ctx->partials,
+                      &ctx->part_begin, &ctx->part_count, &ctx->image, &ctx->pix_off, &ctx->hess,
+                      &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err};
+    for (DevBuf *b : bufs) b->release();
+    HostBuf *hb[] = {&ctx->h_tables, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
+    for (HostBuf *b : hb) b->release();
+    if (ctx->staged) cudaEventDestroy(ctx->staged);
+    if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+    delete ctx;
+}
+
+const char *pcmd_last_error(const pcmd_ctx *ctx) { return ctx ? ctx->err_text.c_str() : "no context"; }
+
+int pcmd_n_points(const pcmd_ctx *ctx) { return ctx ? ctx->model.n_points() : 0; }
+
+pcmd_status pcmd_profile(pcmd_ctx *ctx, int enable) {
+    if (!ctx) return PCMD_ERR_ARG;
+    ctx->profiling = enable != 0;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_kernel_times(pcmd_ctx *ctx, double *h_ms, int *h_count) {
+    if (!ctx || !h_ms || !h_count) return PCMD_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int k = 0; k < PCMD_KERNEL_KINDS; ++k) {
+        double ms = 0.0;
+        for (auto &pr : ctx->ev[k]) {
+            float v = 0.0f;
+            if (cudaEventElapsedTime(&v, pr.first, pr.second) == cudaSuccess) ms += v;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        h_ms[k] = ms;
+        h_count[k] = (int)ctx->ev[k].size();
+        ctx->ev[k].clear();
+    }
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_set_launch(pcmd_ctx *ctx, int block, int split, int chunk) {
+    if (!ctx) return PCMD_ERR_ARG;
+    if (block < 32 || block > 256 || block % 32) return arg_error(ctx, "block must be 32..256, a multiple of 32");
+    if (split < 1 || block % (split * 32)) return arg_error(ctx, "block / split must be a multiple of 32");
+    if (chunk < 1 || chunk > 256) return arg_error(ctx, "chunk must be 1..256");
+    ctx->block = block;
+    ctx->split = split;
+    ctx->chunk = chunk;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_simulate(pcmd_ctx *ctx, const pcmd_params *h_params, int n_sets, const int *h_n_im,
+                          uint32_t first_set_id, float *d_image) {
+    if (!ctx) return PCMD_ERR_ARG;
+    pcmd_status rc = check_params(ctx, h_params, n_sets, h_n_im);
+    if (rc != PCMD_OK) return rc;
+    const int ppc = ctx->block / ctx->split;
+    rc = stage_sets(ctx, h_params, n_sets, h_n_im, first_set_id, n_sets > 1, ppc);
+    if (rc != PCMD_OK) return rc;
+    size_t floats = 0;
+    for (int s = 0; s < n_sets; ++s) floats += (size_t)ctx->model.n_bands * h_n_im[s] * h_n_im[s];
+    float *img = d_image;
+    if (!img) {
+        CK(ctx->image.ensure(floats * 4));
+        img = ctx->image.as<float>();
+    }
+    DrawArgs a = base_draw_args(ctx);
+    a.image = img;
+    rc = launch_draw_mode(ctx, a, kModeImage);
+    if (rc != PCMD_OK) return rc;
+    ctx->img_ptr = img;
+    ctx->have_images = true;
+    ctx->have_hess = false;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_hess(pcmd_ctx *ctx, uint32_t *d_hess, double *d_moments, uint32_t *d_counters,
+                      float *d_pixels) {
+    if (!ctx) return PCMD_ERR_ARG;
+    if (!ctx->have_images) {
+        ctx->err_text = "pcmd_hess needs a preceding pcmd_simulate";
+        return PCMD_ERR_STATE;
+    }
+    const int n_sets = ctx->n_sets;
+    const int nbins = ctx->cfg.hess_nx * ctx->cfg.hess_ny;
+    if (!d_hess) CK(ctx->hess.ensure(sizeof(uint32_t) * nbins * n_sets));
+    if (!d_moments) CK(ctx->moments.ensure(sizeof(double) * 3 * n_sets));
+    if (!d_counters) CK(ctx->counters.ensure(sizeof(uint32_t) * 2 * n_sets));
+    uint32_t *hh = d_hess ? d_hess : ctx->hess.as<uint32_t>();
+    double *mm = d_moments ? d_moments : ctx->moments.as<double>();
+    uint32_t *cc = d_counters ? d_counters : ctx->counters.as<uint32_t>();
+    int max_tiles = 1;
+    for (int s = 0; s < n_sets; ++s) {
+        const int tx = (ctx->n_im[s] + 31) / 32;
+        max_tiles = std::max(max_tiles, tx * tx);
+    }
+    int cps = std::max(1, (2 * ctx->n_sm + n_sets - 1) / n_sets);
+    cps = std::min(cps, max_tiles);
+    // per-set partial ranges and pixel-output offsets (pinned host staging, then device)
+    if (ctx->staged_pending) {
+        CK(cudaEventSynchronize(ctx->staged));
+        ctx->staged_pending = false;
+    }
+    CK(ctx->h_meta.ensure(sizeof(uint64_t) * (size_t)n_sets * 3));
+    uint32_t *hb = ctx->h_meta.as<uint32_t>();
+    uint32_t *hc = hb + n_sets;
+    uint64_t *hp = reinterpret_cast<uint64_t *>(ctx->h_meta.as<uint8_t>() + ((sizeof(uint32_t) * 2 * n_sets + 7) & ~size_t(7)));
+    uint64_t po = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        hb[s] = (uint32_t)(s * cps);
+        hc[s] = (uint32_t)cps;
+        hp[s] = po;
+        po += (uint64_t)(ctx->model.n_bands + 2) * ctx->n_im[s] * ctx->n_im[s];
+    }
+    CK(ctx->part_begin.ensure(sizeof(uint32_t) * n_sets));
+    CK(ctx->part_count.ensure(sizeof(uint32_t) * n_sets));
+    CK(ctx->pix_off.ensure(sizeof(uint64_t) * n_sets));
+    CK(ctx->partials.ensure(sizeof(double) * 3 * (size_t)cps * n_sets));
+    CK(cudaMemcpyAsync(ctx->part_begin.p, hb, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->part_count.p, hc, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->pix_off.p, hp, sizeof(uint64_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaEventRecord(ctx->staged, ctx->st));
+    ctx->staged_pending = true;
+    CK(cudaMemsetAsync(hh, 0, sizeof(uint32_t) * nbins * n_sets, ctx->st));
+    CK(cudaMemsetAsync(cc, 0, sizeof(uint32_t) * 2 * n_sets, ctx->st));
+    HessArgs h;
+    std::memset(&h, 0, sizeof h);
+    h.image = ctx->img_ptr;
+    h.desc = ctx->desc.as<SetDesc>();
+    h.n_sets = n_sets;
+    h.n_bands = ctx->model.n_bands;
+    h.psf = ctx->psf.empty() ? nullptr : ctx->psf_d.as<float>();
+    h.psf_size = ctx->psf.empty() ? 0 : ctx->cfg.psf_size;
+    h.hess = hh;
+    h.counters = cc;
+    h.cta_moments = ctx->partials.as<double>();
+    h.ctas_per_set = cps;
+    h.pixels = d_pixels;
+    h.pix_off = ctx->pix_off.as<uint64_t>();
+    h.pc = pixel_consts(ctx);
+    {
+        KTimer t(ctx, PCMD_K_HESS, ctx->st);
+        CK(launch_hess(h, ctx->psf25.empty() ? nullptr : ctx->psf25.data(), ctx->st));
+        t.done(ctx->st);
+    }
+    {
+        KTimer t(ctx, PCMD_K_FINALIZE, ctx->st);
+        CK(launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
+                                   ctx->part_count.as<uint32_t>(), n_sets, mm, ctx->st));
+        t.done(ctx->st);
+    }
+    ctx->hess_ptr = hh;
+    ctx->mom_ptr = mm;
+    ctx->ctr_ptr = cc;
+    ctx->have_hess = true;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_sync(pcmd_ctx *ctx) {
+    if (!ctx) return PCMD_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    uint32_t e = 0;
+    CK(cudaMemcpy(&e, ctx->err.p, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(cudaMemset(ctx->err.p, 0, sizeof(uint32_t)));
+        if (e & kErrTimeout) {
+            ctx->err_text = "a bounded wait inside a kernel ran out";
+            return PCMD_ERR_TIMEOUT;
+        }
+        ctx->err_text = "transformed rejection reached its attempt cap";
+        return PCMD_ERR_SAMPLER_LIMIT;
+    }
+    return PCMD_OK;
+}
+
+static pcmd_status check_mock(pcmd_ctx *ctx, const uint32_t *d_mock, const double *mom, double npix,
+                              int mode, double *h_ll) {
+    if (!d_mock || !mom || !h_ll) return arg_error(ctx, "mock Hess, mock moments and h_ll are required");
+    if (!(npix > 0.0) || !is_fin(npix)) return arg_error(ctx, "mock_n_pix must be positive");
+    if (mode != PCMD_LL_PAPER && mode != PCMD_LL_POISSON) return arg_error(ctx, "unknown likelihood mode");
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_loglike(pcmd_ctx *ctx, const uint32_t *d_mock_hess, const double *h_mock_moments,
+                         double mock_n_pix, int mode, double *h_ll) {
+    if (!ctx) return PCMD_ERR_ARG;
+    pcmd_status rc = check_mock(ctx, d_mock_hess, h_mock_moments, mock_n_pix, mode, h_ll);
+    if (rc != PCMD_OK) return rc;
+    if (!ctx->have_hess) {
+        ctx->err_text = "pcmd_loglike needs a preceding pcmd_hess";
+        return PCMD_ERR_STATE;
+    }
+    const int n_sets = ctx->n_sets;
+    CK(ctx->ll.ensure(sizeof(double) * n_sets));
+    {
+        KTimer t(ctx, PCMD_K_LOGLIKE, ctx->st);
+        CK(launch_loglike(ctx->hess_ptr, ctx->mom_ptr, ctx->desc.as<SetDesc>(), n_sets,
+                          ctx->cfg.hess_nx * ctx->cfg.hess_ny, d_mock_hess, h_mock_moments[0],
+                          h_mock_moments[1], h_mock_moments[2], mock_n_pix, mode,
+                          (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
+                          ctx->st));
+        t.done(ctx->st);
+    }
+    CK(cudaMemcpyAsync(ctx->h_ll.p, ctx->ll.p, sizeof(double) * n_sets, cudaMemcpyDeviceToHost, ctx->st));
+    rc = pcmd_sync(ctx);
+    std::memcpy(h_ll, ctx->h_ll.p, sizeof(double) * n_sets);
+    return rc;
+}
+
+// Fused evaluation without a PSF: one persistent draw launch does draws, dust, noise,
+// magnitudes and histograms of all sets; then moments and likelihoods.  The device-side
+// sequence is captured once per shape into a CUDA graph and replayed.
+static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_mock,
+                                  const double *mom, double npix, int mode) {
+    const int nbins = ctx->cfg.hess_nx * ctx->cfg.hess_ny;
+    const size_t n_items = ctx->item_list.size();
+    CK(ctx->hess.ensure(sizeof(uint32_t) * nbins * n_sets));
+    CK(ctx->moments.ensure(sizeof(double) * 3 * n_sets));
+    CK(ctx->counters.ensure(sizeof(uint32_t) * 2 * n_sets));
+    CK(ctx->partials.ensure(sizeof(double) * 3 * n_items));
+    CK(ctx->part_begin.ensure(sizeof(uint32_t) * n_sets));
+    CK(ctx->part_count.ensure(sizeof(uint32_t) * n_sets));
+    CK(ctx->ll.ensure(sizeof(double) * n_sets));
+    CK(ctx->h_meta.ensure(sizeof(uint32_t) * 2 * n_sets + 16));
+    uint32_t *hb = ctx->h_meta.as<uint32_t>();
+    for (int s = 0; s < n_sets; ++s) {
+        hb[s] = ctx->descs[s].item_begin;
+        hb[n_sets + s] = ctx->descs[s].n_items;
+    }
+    CK(cudaMemcpyAsync(ctx->part_begin.p, hb, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->part_count.p, hb + n_sets, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaEventRecord(ctx->staged, ctx->st));
+    ctx->staged_pending = true;
+
+    const int B = ctx->model.n_bands;
+    const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
+    const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, kModeFused,
+                                        ctx->cfg.hess_nx, ctx->cfg.hess_ny);
+    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->block, smem));
+    const int grid = std::max(1, std::min<int>((int)n_items, per_sm * ctx->n_sm));
+    uint64_t mk[4];
+    std::memcpy(&mk[0], &mom[0], 8);
+    std::memcpy(&mk[1], &mom[1], 8);
+    std::memcpy(&mk[2], &mom[2], 8);
+    std::memcpy(&mk[3], &npix, 8);
+    const size_t key[12] = {(size_t)n_sets, n_items, (size_t)grid, (size_t)mode,
+                            (size_t)ctx->tables.p, (size_t)ctx->hess.p, (size_t)d_mock,
+                            (size_t)ctx->block * 1000003u + ctx->split * 1009u + ctx->chunk,
+                            mk[0], mk[1], mk[2], mk[3]};
+    if (ctx->gexec && std::memcmp(ctx->gkey, key, sizeof key) != 0) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    if (!ctx->gexec) {
+        DrawArgs a = base_draw_args(ctx);
+        a.hess = ctx->hess.as<uint32_t>();
+        a.counters = ctx->counters.as<uint32_t>();
+        a.item_moments = ctx->partials.as<double>();
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(ctx->hess.p, 0, sizeof(uint32_t) * nbins * n_sets, ctx->cap_st);
+        cudaMemsetAsync(ctx->counters.p, 0, sizeof(uint32_t) * 2 * n_sets, ctx->cap_st);
+        cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->cap_st);
+        launch_draw(a, B, kahan, kModeFused, grid, ctx->block, smem, ctx->cap_st);
+        launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
+                                ctx->part_count.as<uint32_t>(), n_sets, ctx->moments.as<double>(),
+                                ctx->cap_st);
+        launch_loglike(ctx->hess.as<uint32_t>(), ctx->moments.as<double>(), ctx->desc.as<SetDesc>(),
+                       n_sets, nbins, d_mock, mom[0], mom[1], mom[2], npix, mode,
+                       (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
+                       ctx->cap_st);
+        CK(cudaStreamEndCapture(ctx->cap_st, &g));
+        cudaError_t ec = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(ec);
+        std::memcpy(ctx->gkey, key, sizeof key);
+    }
+    {
+        KTimer t(ctx, PCMD_K_GRAPH, ctx->st);
+        CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+        t.done(ctx->st);
+    }
+    ctx->hess_ptr = ctx->hess.as<uint32_t>();
+    ctx->mom_ptr = ctx->moments.as<double>();
+    ctx->ctr_ptr = ctx->counters.as<uint32_t>();
+    ctx->have_hess = true;
+    ctx->have_images = false;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_evaluate(pcmd_ctx *ctx, const pcmd_params *h_params, int n_sets, const int *h_n_im,
+                          uint32_t first_set_id, const uint32_t *d_mock_hess,
+                          const double *h_mock_moments, double mock_n_pix, int mode, double *h_ll) {
+    if (!ctx) return PCMD_ERR_ARG;
+    pcmd_status rc = check_params(ctx, h_params, n_sets, h_n_im);
+    if (rc != PCMD_OK) return rc;
+    rc = check_mock(ctx, d_mock_hess, h_mock_moments, mock_n_pix, mode, h_ll);
+    if (rc != PCMD_OK) return rc;
+    if (!ctx->psf.empty()) {
+        rc = pcmd_simulate(ctx, h_params, n_sets, h_n_im, first_set_id, nullptr);
+        if (rc == PCMD_OK) rc = pcmd_hess(ctx, nullptr, nullptr, nullptr, nullptr);
+        if (rc == PCMD_OK) rc = pcmd_loglike(ctx, d_mock_hess, h_mock_moments, mock_n_pix, mode, h_ll);
+        return rc;
+    }
+    const int ppc = ctx->block / ctx->split;
+    rc = stage_sets(ctx, h_params, n_sets, h_n_im, first_set_id, true, ppc);
+    if (rc != PCMD_OK) return rc;
+    rc = evaluate_fused(ctx, n_sets, d_mock_hess, h_mock_moments, mock_n_pix, mode);
+    if (rc != PCMD_OK) return rc;
+    CK(cudaMemcpyAsync(ctx->h_ll.p, ctx->ll.p, sizeof(double) * n_sets, cudaMemcpyDeviceToHost, ctx->st));
+    rc = pcmd_sync(ctx);
+    std::memcpy(h_ll, ctx->h_ll.p, sizeof(double) * n_sets);
+    return rc;
+}
+
+pcmd_status pcmd_get_tables(pcmd_ctx *ctx, const pcmd_params *h_params, float *h_lam, float *h_flux,
+                            uint32_t *h_z0) {
+    if (!ctx || !h_params) return PCMD_ERR_ARG;
+    int one = 1;
+    pcmd_status rc = check_params(ctx, h_params, 1, &one);
+    if (rc != PCMD_OK) return rc;
+    std::vector<float> lam_h[2], flux;
+    ctx->model.lambdas(*h_params, lam_h);
+    ctx->model.fluxes(h_params->dmod, flux);
+    const size_t P = (size_t)ctx->model.n_points();
+    if (h_lam) {
+        std::memcpy(h_lam, lam_h[0].data(), P * 4);
+        std::memcpy(h_lam + P, lam_h[1].data(), P * 4);
+    }
+    if (h_flux) std::memcpy(h_flux, flux.data(), flux.size() * 4);
+    if (h_z0) {
+        uint32_t z[kInvCap];
+        for (int h = 0; h < 2; ++h)
+            for (size_t i = 0; i < P; ++i) {
+                const float l = lam_h[h][i];
+                if (!(l > 0.0f) || l >= kPtrsThreshold) h_z0[h * P + i] = 0xFFFFFFFFu;
+                else {
+                    inversion_thresholds(l, z, kInvCap);
+                    h_z0[h * P + i] = z[0];
+                }
+            }
+    }
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_counts(pcmd_ctx *ctx, const pcmd_params *h_params, int n_im, uint32_t set_id,
+                        uint32_t pix_begin, uint32_t n_pix, uint32_t *d_counts) {
+    if (!ctx || !d_counts) return PCMD_ERR_ARG;
+    pcmd_status rc = check_params(ctx, h_params, 1, &n_im);
+    if (rc != PCMD_OK) return rc;
+    const uint64_t npix = (uint64_t)n_im * n_im;
+    if (n_pix == 0 || pix_begin >= npix || pix_begin + (uint64_t)n_pix > npix)
+        return arg_error(ctx, "pixel range outside the image");
+    const int ppc = ctx->block / ctx->split;
+    rc = stage_sets(ctx, h_params, 1, &n_im, set_id, false, ppc);
+    if (rc != PCMD_OK) return rc;
+    // only the tiles that intersect the requested range
+    const uint32_t t0 = pix_begin / ppc, t1 = (pix_begin + n_pix - 1) / ppc;
+    std::vector<uint2> sub;
+    for (uint32_t t = t0; t <= t1; ++t) sub.push_back(make_uint2(0u, t));
+    CK(cudaEventSynchronize(ctx->staged));
+    ctx->staged_pending = false;
+    std::memcpy(ctx->h_items.p, sub.data(), sizeof(uint2) * sub.size());
+    for (size_t i = 0; i < sub.size(); ++i) ctx->h_order.as<uint32_t>()[i] = (uint32_t)i;
+    CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * sub.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * sub.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaEventRecord(ctx->staged, ctx->st));
+    ctx->staged_pending = true;
+    const size_t P = (size_t)ctx->model.n_points();
+    CK(cudaMemsetAsync(d_counts, 0, sizeof(uint32_t) * (size_t)n_pix * 2 * P, ctx->st));
+    DrawArgs a = base_draw_args(ctx);
+    a.n_items = (uint32_t)sub.size();
+    a.counts = d_counts;
+    a.count_pix0 = pix_begin;
+    a.count_npix = n_pix;
+    CK(ctx->image.ensure(sizeof(float) * ctx->model.n_bands * npix));
+    a.image = ctx->image.as<float>();
+    rc = launch_draw_mode(ctx, a, kModeCounts);
+    ctx->have_images = false;
+    ctx->have_hess = false;
+    return rc;
+}
+
+pcmd_status pcmd_bin_mags(pcmd_ctx *ctx, const float *d_mag, const float *d_colour,
+                          const uint8_t *d_valid, uint32_t n, uint32_t *d_hess, uint32_t *d_counters,
+                          double *d_moments) {
+    if (!ctx || !d_mag || !d_colour || !d_valid || !d_hess) return PCMD_ERR_ARG;
+    const int nbins = ctx->cfg.hess_nx * ctx->cfg.hess_ny;
+    CK(cudaMemsetAsync(d_hess, 0, sizeof(uint32_t) * nbins, ctx->st));
+    if (d_counters) CK(cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * 2, ctx->st));
+    if (d_moments) CK(cudaMemsetAsync(d_moments, 0, sizeof(double) * 3, ctx->st));
+    if (n == 0) return PCMD_OK;
+    const PixelConsts pc = pixel_consts(ctx);
+    CK(launch_bin_mags(d_mag, d_colour, d_valid, n, d_hess, d_counters, d_moments, pc,
+                       ctx->err.as<uint32_t>(), ctx->st));
+    return PCMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// draw_flux: Poisson star counts per pixel and isochrone point, per-band flux sums, dust
+// screen and (fused mode) noise, magnitudes and the Hess diagram.
+//
+// Section 2.1: every pixel receives n_i ~ Poisson(lambda_i) stars at every age-[Fe/H]-mass
+// point, lambda summing to Npix; fluxes are summed per band (panels B-D of Fig. 1), the dust
+// screen dims the stars behind it (Section 2.2 E1-E3) and distance is folded into the per-star
+// fluxes (D1/D2).  Section 2.4: the paper gives one GPU thread per pixel; here one thread per
+// pixel and split (a CTA's warps share a pixel tile and divide the isochrone points), with
+// the point tables streamed through shared memory by bulk copies.
+//
+// Draw word of inversion point i (lambda < 10) of half h at pixel p:
+//   x = hi16 << 16 | lo16, hi16 / lo16 the (i & 7)-th 16-bit slot of
+//   Philox(p, i >> 3, set, HI|h) / Philox(p, i >> 3, set, LO|h);  n = #{k : x > Z_k}.
+// The fast path only needs hi16: hi16 < Z_0 >> 16 gives n = 0 without the LO call, and a
+// certain hit with hi16 < Z_1 >> 16 gives n = 1.  Both are exact consequences of the rule.
+#include "common.cuh"
+
+namespace pcmd {
+
+__constant__ float c_stirlerr[16];
+
+cudaError_t upload_stirlerr(const float *tab16) {
+    return cudaMemcpyToSymbol(c_stirlerr, tab16, 16 * sizeof(float));
+}
+
+// stirlerr(k) = ln k! - (k ln k - k + ln(2 pi k) / 2): table below 16 (built in FP64 on the
+// host), FP32 Stirling series 1/(12k) - 1/(360k^3) + 1/(1260k^5) above (DLMF 5.11.1).
+__device__ __forceinline__ float stirlerr_dev(float kf) {
+    if (kf < 16.0f) return c_stirlerr[(int)kf];
+    const float r = __fdiv_rn(1.0f, kf);
+    const float r2 = __fmul_rn(r, r);
+    float t = __fmul_rn(r2, (float)(1.0 / 1260.0));
+    t = __fsub_rn((float)(1.0 / 360.0), t);
+    t = __fmul_rn(t, r2);
+    t = __fsub_rn((float)(1.0 / 12.0), t);
+    return __fmul_rn(t, r);
+}
+
+// log Poisson pmf in the deviance form -lambda phi((k - lambda)/lambda) - ln(2 pi k)/2 -
+// stirlerr(k) (Loader 2000), which does not cancel k ln(lambda) against ln k!.
+__device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
+    if (kf == 0.0f) return -lam;
+    const float x = __fdiv_rn(__fsub_rn(kf, lam), lam);
+    const float bd0 = __fmul_rn(lam, phi_dev(x));
+    const float st = stirlerr_dev(kf);
+    float t = ln_series(kf);
+    t = __fmul_rn(0.5f, t);
+    t = __fadd_rn(t, (float)0.91893853320467274178);
+    float r = -bd0;
+    r = __fsub_rn(r, t);
+    return __fsub_rn(r, st);
+}
+
+// Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Attempt `at` uses words
+// 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).
+__device__ __noinline__ uint32_t ptrs_draw(const PtrsRec &r, uint32_t pix, uint32_t set,
+                                           uint32_t half, uint32_t k0, uint32_t k1,
+                                           uint32_t *err) {
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t at = 0; at < kPtrsMaxAttempts; ++at) {
+        if ((at & 1u) == 0u) w = philox(pix, r.i, set, rng_tag(kKindPtrs, half, at >> 1), k0, k1);
+        const uint32_t wu = (at & 1u) ? w.z : w.x;
+        const uint32_t wv = (at & 1u) ? w.w : w.y;
+        const float U = __fsub_rn(uniform_of(wu), 0.5f);
+        const float V = uniform_of(wv);
+        const float us = __fsub_rn(0.5f, fabsf(U));
+        float t = __fdiv_rn(r.twoa, us);
+        t = __fadd_rn(t, r.b);
+        t = __fmul_rn(t, U);
+        t = __fadd_rn(t, r.lam);
+        t = __fadd_rn(t, 0.43f);
+        const float kf = floorf(t);
+        if (us >= 0.07f && V <= r.vr) return (uint32_t)kf;
+        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        if (kf > 1.0e9f) continue;
+        float q = __fmul_rn(us, us);
+        q = __fdiv_rn(r.a, q);
+        q = __fadd_rn(q, r.b);
+        float lhs = ln_series(V);
+        lhs = __fadd_rn(lhs, r.log_ia);
+        lhs = __fsub_rn(lhs, ln_series(q));
+        if (lhs <= log_pmf_dev(kf, r.lam)) return (uint32_t)kf;
+    }
+    atomicOr(err, kErrSampler);
+    return 0u;
+}
+
+// Per-pixel flux accumulators of the two dust halves; compensated (Kahan) when KAHAN.
+template <int B, bool KAHAN>
+struct Acc {
+    float s[2][B];
+    float c[2][B];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int b = 0; b < B; ++b) s[h][b] = c[h][b] = 0.0f;
+    }
+    template <int H>
+    __device__ __forceinline__ void add(float n, const float *f) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const float v = __fmul_rn(n, f[b]);
+            if (KAHAN) {
+                const float y = __fsub_rn(v, c[H][b]);
+                const float t = __fadd_rn(s[H][b], y);
+                c[H][b] = __fsub_rn(__fsub_rn(t, s[H][b]), y);
+                s[H][b] = t;
+            } else {
+                s[H][b] = __fadd_rn(s[H][b], v);
+            }
+        }
+    }
+    template <int H>
+    __device__ __forceinline__ float value(int b) const {
+        return KAHAN ? __fsub_rn(s[H][b], c[H][b]) : s[H][b];
+    }
+};
+
+__device__ __forceinline__ uint32_t maybe_mask(const uint4 &w, const uint4 &z) {
+    uint32_t m = 0;
+    m |= (uint32_t)((w.x & 0xFFFFu) >= (z.x & 0xFFFFu)) << 0;
+    m |= (uint32_t)((w.x >> 16) >= (z.x >> 16)) << 1;
+    m |= (uint32_t)((w.y & 0xFFFFu) >= (z.y & 0xFFFFu)) << 2;
+    m |= (uint32_t)((w.y >> 16) >= (z.y >> 16)) << 3;
+    m |= (uint32_t)((w.z & 0xFFFFu) >= (z.z & 0xFFFFu)) << 4;
+    m |= (uint32_t)((w.z >> 16) >= (z.z >> 16)) << 5;
+    m |= (uint32_t)((w.w & 0xFFFFu) >= (z.w & 0xFFFFu)) << 6;
+    m |= (uint32_t)((w.w >> 16) >= (z.w >> 16)) << 7;
+    return m;
+}
+
+struct ItemCtx {
+    uint32_t pix, set, npix;
+    bool active;
+    const SlowRec *slow[2];
+    const uint32_t *tail;
+};
+
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void hit_path(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
+                                         uint32_t gid, const uint4 &w, const uint4 &z0,
+                                         uint32_t m, Acc<B, KAHAN> &acc, uint32_t k0,
+                                         uint32_t k1) {
+    const uint4 z1 = *reinterpret_cast<const uint4 *>(r + 32);
+    const float *fl = reinterpret_cast<const float *>(r + 48);
+    uint4 wlo = make_uint4(0, 0, 0, 0);
+    bool have_lo = false;
+    do {
+        const uint32_t j = (uint32_t)(__ffs(m) - 1);
+        m &= m - 1u;
+        const uint32_t hi = slot16(w, j);
+        const uint32_t zc0 = slot16(z0, j), zc1 = slot16(z1, j);
+        uint32_t n;
+        if (hi > zc0 && hi < zc1) {
+            n = 1u;
+        } else {
+            if (!have_lo) {
+                wlo = philox(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), k0, k1);
+                have_lo = true;
+            }
+            const uint32_t x = (hi << 16) | slot16(wlo, j);
+            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + (gid * 8u + j));
+            if (x <= sr.x) {
+                n = 0u;
+            } else if (x <= sr.y) {
+                n = 1u;
+            } else {
+                n = 2u;
+                for (uint32_t t = 0; t < sr.w; ++t) {
+                    if (x > __ldg(ic.tail + sr.z + t)) ++n;
+                    else break;
+                }
+            }
+        }
+        if (n) {
+            acc.template add<H>((float)n, fl + j * B);
+            if (MODE == kModeCounts) {
+                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
+                             gid * 8u + j] = n;
+            }
+        }
+    } while (m);
+}
+
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
+                                              const uint8_t *cb, uint32_t cnt, int sidx,
+                                              Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
+    constexpr uint32_t rec = group_rec_bytes(B);
+    for (uint32_t g = (uint32_t)sidx; g < cnt; g += (uint32_t)a.split) {
+        const uint8_t *r = cb + g * rec;
+        const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
+        const uint4 z0 = *reinterpret_cast<const uint4 *>(r + 16);
+        const uint4 w = philox(ic.pix, gid, ic.set, rng_tag(kKindHi, H, 0), k0, k1);
+        const uint32_t m = maybe_mask(w, z0);
+        if (m != 0u && ic.active) hit_path<B, KAHAN, MODE, H>(a, ic, r, gid, w, z0, m, acc, k0, k1);
+    }
+}
+
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic,
+                                             const SetDesc &d, int sidx, Acc<B, KAHAN> &acc,
+                                             uint32_t k0, uint32_t k1) {
+    const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
+    for (uint32_t q = (uint32_t)sidx; q < d.n_ptrs[H]; q += (uint32_t)a.split) {
+        PtrsRec rec;
+        const uint4 *src = reinterpret_cast<const uint4 *>(pr + q);
+        uint4 *dst = reinterpret_cast<uint4 *>(&rec);
+        dst[0] = __ldg(src);
+        dst[1] = __ldg(src + 1);
+        dst[2] = __ldg(src + 2);
+        if (!ic.active) continue;
+        const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, k0, k1, a.err);
+        if (n) {
+            acc.template add<H>((float)n, rec.flux);
+            if (MODE == kModeCounts) {
+                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
+            }
+        }
+    }
+}
+
+// Dust screen factors of one pixel: E(B-V) = 10^log_ebv exp(sigma z), z ~ N(0, 1) by
+// Box-Muller from Philox(p, 0, set, DUST); factor_b = 10^(-0.4 R_b E).
+template <int B>
+__device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uint32_t k0,
+                                             uint32_t k1, float (&fac)[B]) {
+    float z = 0.0f;
+    if (d.dust_sigma != 0.0f) {
+        const uint4 w = philox(pix, 0u, d.set_id, rng_tag(kKindDust, 0, 0), k0, k1);
+        const float u1 = uniform_of(w.x), u2 = uniform_of(w.y);
+        z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+    const float e = expf(d.dust_a + d.dust_sigma * z);
+#pragma unroll
+    for (int b = 0; b < B; ++b) fac[b] = exp10f(d.dust_c[b] * e);
+}
+
+template <int B, bool KAHAN, int MODE>
+__global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr uint32_t rec = group_rec_bytes(B);
+    const uint32_t chunk = (uint32_t)a.chunk;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    volatile uint32_t *s_item = reinterpret_cast<volatile uint32_t *>(smem + 16);
+    uint32_t *s_ntouch = reinterpret_cast<uint32_t *>(smem + 20);
+    uint8_t *bufs = smem + 32;
+    float *red = reinterpret_cast<float *>(bufs + 2u * chunk * rec);
+    const int tid = threadIdx.x;
+    const int ppc = blockDim.x / a.split;
+    const int sidx = tid / ppc;
+    const int pl = tid - sidx * ppc;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(red + (size_t)blockDim.x * 2 * B);
+    const int nbins = a.pc.nx * a.pc.ny;
+    uint32_t *touched = hist + nbins;
+    double *wred = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(touched + ppc) + 7u) & ~uintptr_t(7));
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        *s_ntouch = 0u;
+    }
+    if (MODE == kModeFused)
+        for (int i = tid; i < nbins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    uint32_t parity = 0u;
+    uint32_t pending = 0u;   // bit b: buffer b has an issued, not yet awaited copy
+
+    for (uint32_t q = blockIdx.x;; q += gridDim.x) {
+        uint32_t pos;
+        if (a.queue) {
+            if (tid == 0) *s_item = atomicAdd(a.queue, 1u);
+            __syncthreads();
+            pos = *s_item;
+        } else {
+            pos = q;
+        }
+        if (pos >= a.n_items) break;
+        const uint32_t item = a.order ? __ldg(a.order + pos) : pos;
+        const uint2 it = a.items[item];
+        const SetDesc &d = a.desc[it.x];
+        ItemCtx ic;
+        ic.npix = d.n_im * d.n_im;
+        ic.pix = it.y * (uint32_t)ppc + (uint32_t)pl;
+        ic.active = ic.pix < ic.npix;
+        ic.set = d.set_id;
+        ic.slow[0] = reinterpret_cast<const SlowRec *>(a.tables + d.slow_off[0]);
+        ic.slow[1] = reinterpret_cast<const SlowRec *>(a.tables + d.slow_off[1]);
+        ic.tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
+        Acc<B, KAHAN> acc;
+        acc.init();
+
+        // ---- inversion points, streamed through shared memory chunk by chunk ----
+        const uint32_t ng0 = d.n_grp[0], ng1 = d.n_grp[1];
+        const uint32_t nc0 = (ng0 + chunk - 1) / chunk, nc1 = (ng1 + chunk - 1) / chunk;
+        const uint32_t nc = nc0 + nc1;
+        if (tid == 0 && nc > 0) {
+            const uint32_t cnt = min(chunk, nc0 > 0 ? ng0 : ng1);
+            const uint8_t *src = a.tables + (nc0 > 0 ? d.grp_off[0] : d.grp_off[1]);
+            mbar_expect_tx(&bars[0], cnt * rec);
+            bulk_g2s(bufs, src, cnt * rec, &bars[0]);
+            pending |= 1u;
+        }
+        for (uint32_t c = 0; c < nc; ++c) {
+            const uint32_t b = c & 1u;
+            if (tid == 0 && c + 1 < nc) {
+                const uint32_t cn = c + 1;
+                const uint32_t h = cn >= nc0 ? 1u : 0u;
+                const uint32_t first = (h ? cn - nc0 : cn) * chunk;
+                const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
+                const uint32_t bn = cn & 1u;
+                mbar_expect_tx(&bars[bn], cnt * rec);
+                bulk_g2s(bufs + bn * chunk * rec, a.tables + d.grp_off[h] + (uint64_t)first * rec,
+                         cnt * rec, &bars[bn]);
+                pending |= 1u << bn;
+            }
+            if (!mbar_wait(&bars[b], (parity >> b) & 1u, a.err)) mbar_wait(&bars[b], (parity >> b) & 1u, a.err);
+            parity ^= 1u << b;
+            pending &= ~(1u << b);
+            const uint32_t h = c >= nc0 ? 1u : 0u;
+            const uint32_t first = (h ? c - nc0 : c) * chunk;
+            const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
+            const uint8_t *cb = bufs + b * chunk * rec;
+            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, cb, cnt, sidx, acc, k0, k1);
+            else process_chunk<B, KAHAN, MODE, 1>(a, ic, cb, cnt, sidx, acc, k0, k1);
+            __syncthreads();
+        }
+
+        // ---- transformed-rejection points (lambda >= 10) ----
+        process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc, k0, k1);
+        process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc, k0, k1);
+
+        // ---- combine the splits of each pixel in a fixed order ----
+        float v0[B], v1[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            v0[b] = acc.template value<0>(b);
+            v1[b] = acc.template value<1>(b);
+        }
+        if (a.split > 1) {
+            float *my = red + (size_t)tid * 2 * B;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                my[b] = v0[b];
+                my[B + b] = v1[b];
+            }
+            __syncthreads();
+            if (sidx == 0) {
+                for (int s = 1; s < a.split; ++s) {
+                    const float *o = red + (size_t)(s * ppc + pl) * 2 * B;
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        v0[b] = __fadd_rn(v0[b], o[b]);
+                        v1[b] = __fadd_rn(v1[b], o[B + b]);
+                    }
+                }
+            }
+        }
+
+        // ---- epilogue: dust screen, then image store or the fused pixel stage ----
+        float F[B];
+        const bool own = sidx == 0 && ic.active;
+        if (own) {
+            if (d.dust_on) {
+                float fac[B];
+                dust_factors<B>(d, ic.pix, k0, k1, fac);
+#pragma unroll
+                for (int b = 0; b < B; ++b) F[b] = v0[b] + fac[b] * v1[b];
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) F[b] = __fadd_rn(v0[b], v1[b]);
+            }
+        }
+        if (MODE == kModeImage) {
+            if (own) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) a.image[d.img_off + (size_t)b * ic.npix + ic.pix] = F[b];
+            }
+        } else if (MODE == kModeFused) {
+            double cs = 0.0, ms = 0.0, nv = 0.0;
+            uint32_t novf = 0u, ninv = 0u;
+            if (sidx == 0) {
+                int bin = -1;
+                if (ic.active) {
+                    const PixelOut o = pixel_stage<B>(F, ic.pix, ic.set, a.pc);
+                    if (o.valid) {
+                        cs = (double)__fsub_rn(o.col, a.pc.c_lo);
+                        ms = (double)__fsub_rn(o.mag, a.pc.m_lo);
+                        nv = 1.0;
+                        bin = o.bin;
+                        if (bin < 0) novf = 1u;
+                    } else {
+                        ninv = 1u;
+                    }
+                }
+                hist_add_warp(hist, touched, s_ntouch, bin, (uint32_t)ppc);
+            }
+            // block reduction of the item's moments and counters
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                ms += __shfl_xor_sync(0xffffffffu, ms, o);
+                nv += __shfl_xor_sync(0xffffffffu, nv, o);
+                novf += __shfl_xor_sync(0xffffffffu, novf, o);
+                ninv += __shfl_xor_sync(0xffffffffu, ninv, o);
+            }
+            const int wid = tid >> 5, lane = tid & 31;
+            if (lane == 0) {
+                wred[wid * 5 + 0] = cs;
+                wred[wid * 5 + 1] = ms;
+                wred[wid * 5 + 2] = nv;
+                wred[wid * 5 + 3] = (double)novf;
+                wred[wid * 5 + 4] = (double)ninv;
+            }
+            __syncthreads();
+            const uint32_t nbins_u = (uint32_t)nbins;
+            const uint32_t ntouch = min(*s_ntouch, (uint32_t)ppc);
+            uint32_t *gh = a.hess + (size_t)it.x * nbins_u;
+            for (uint32_t t = tid; t < ntouch; t += blockDim.x) {
+                const uint32_t bin = touched[t];
+                const uint32_t v = hist[bin];
+                hist[bin] = 0u;
+                if (v) atomicAdd(gh + bin, v);
+            }
+            if (tid == 0) {
+                double t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    t0 += wred[w * 5 + 0];
+                    t1 += wred[w * 5 + 1];
+                    t2 += wred[w * 5 + 2];
+                    t3 += wred[w * 5 + 3];
+                    t4 += wred[w * 5 + 4];
+                }
+                a.item_moments[(size_t)item * 3 + 0] = t0 + t2 * (double)a.pc.c_lo;
+                a.item_moments[(size_t)item * 3 + 1] = t1 + t2 * (double)a.pc.m_lo;
+                a.item_moments[(size_t)item * 3 + 2] = t2;
+                if (t3 > 0.0) atomicAdd(a.counters + (size_t)it.x * 2 + 0, (uint32_t)t3);
+                if (t4 > 0.0) atomicAdd(a.counters + (size_t)it.x * 2 + 1, (uint32_t)t4);
+            }
+            __syncthreads();
+            if (tid == 0) *s_ntouch = 0u;
+        }
+        __syncthreads();
+        if (!a.queue) break;
+    }
+    // a copy can only be outstanding here after a timed-out wait: wait for it once more
+    if (tid == 0) {
+        for (uint32_t b = 0; b < 2; ++b)
+            if (pending & (1u << b)) mbar_wait(&bars[b], (parity >> b) & 1u, a.err);
+    }
+}
+
+size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx, int ny) {
+    size_t s = 32 + 2 * (size_t)chunk * group_rec_bytes(nb) + (size_t)block * 2 * nb * 4;
+    if (mode == kModeFused) {
+        s += (size_t)nx * ny * 4 + (size_t)(block / split) * 4;
+        s = (s + 7) & ~size_t(7);
+        s += (size_t)(block / 32) * 5 * 8 + 8;
+    }
+    return s;
+}
+
+// Opt in to the dynamic shared memory of each instantiation once per process (before any
+// stream capture: the first call of every configuration goes through draw_max_blocks_per_sm).
+template <int B, bool KAHAN, int MODE>
+static cudaError_t configure_t(size_t smem) {
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(draw_kernel<B, KAHAN, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    return cudaSuccess;
+}
+
+template <int B, bool KAHAN, int MODE>
+static cudaError_t launch_t(const DrawArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
+    cudaError_t e = configure_t<B, KAHAN, MODE>(smem);
+    if (e != cudaSuccess) return e;
+    draw_kernel<B, KAHAN, MODE><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int B, bool KAHAN, int MODE>
+static int occupancy_t(int block, size_t smem) {
+    if (configure_t<B, KAHAN, MODE>(smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, draw_kernel<B, KAHAN, MODE>, block, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <int B, bool KAHAN>
+static int occupancy_m(int mode, int block, size_t smem) {
+    switch (mode) {
+        case kModeImage: return occupancy_t<B, KAHAN, kModeImage>(block, smem);
+        case kModeCounts: return occupancy_t<B, KAHAN, kModeCounts>(block, smem);
+        default: return occupancy_t<B, KAHAN, kModeFused>(block, smem);
+    }
+}
+
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int block, size_t smem) {
+    switch (nb) {
+        case 2: return kahan ? occupancy_m<2, true>(mode, block, smem) : occupancy_m<2, false>(mode, block, smem);
+        case 3: return kahan ? occupancy_m<3, true>(mode, block, smem) : occupancy_m<3, false>(mode, block, smem);
+        default: return kahan ? occupancy_m<4, true>(mode, block, smem) : occupancy_m<4, false>(mode, block, smem);
+    }
+}
+
+template <int B, bool KAHAN>
+static cudaError_t launch_m(const DrawArgs &a, int mode, int grid, int block, size_t smem,
+                            cudaStream_t st) {
+    switch (mode) {
+        case kModeImage: return launch_t<B, KAHAN, kModeImage>(a, grid, block, smem, st);
+        case kModeCounts: return launch_t<B, KAHAN, kModeCounts>(a, grid, block, smem, st);
+        default: return launch_t<B, KAHAN, kModeFused>(a, grid, block, smem, st);
+    }
+}
+
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, int grid, int block,
+                        size_t smem, cudaStream_t st) {
+    switch (n_bands) {
+        case 2: return kahan ? launch_m<2, true>(a, mode, grid, block, smem, st)
+                             : launch_m<2, false>(a, mode, grid, block, smem, st);
+        case 3: return kahan ? launch_m<3, true>(a, mode, grid, block, smem, st)
+                             : launch_m<3, false>(a, mode, grid, block, smem, st);
+        default: return kahan ? launch_m<4, true>(a, mode, grid, block, smem, st)
+                              : launch_m<4, false>(a, mode, grid, block, smem, st);
+    }
+}
+
+}  // namespace pcmd

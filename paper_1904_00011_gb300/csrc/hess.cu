@@ -1,0 +1,278 @@
+// psf_noise_mag_hess: periodic PSF convolution from a shared-memory tile with halo, sky and
+// photon noise, magnitudes and colour, and a Hess diagram privatised in shared memory
+// (Section 2.1 panels E-F, Section 2.5).  Persistent over 32x32 output tiles of one image per
+// blockIdx.y; each CTA flushes its histogram once and writes one moments partial.
+#include "common.cuh"
+
+namespace pcmd {
+
+constexpr int kTile = 32;
+constexpr int kHessThreads = 256;
+
+struct PsfW {
+    float w[kMaxBands][625];   // 25x25 weights per band (compile-time indexed: constant bank)
+};
+
+template <int B, int KS>
+__device__ __forceinline__ float conv_pixel(const float *tile_b, int hx, int ty, int tx,
+                                            const float *w, int ks_rt) {
+    float acc = 0.0f;
+    if (KS > 0) {
+        constexpr int R = KS / 2;
+#pragma unroll
+        for (int u = 0; u < KS; ++u) {
+            const float *row = tile_b + (ty + 2 * R - u) * hx + tx + 2 * R;
+#pragma unroll
+            for (int v = 0; v < KS; ++v) acc = fmaf(w[u * KS + v], row[-v], acc);
+        }
+    } else {
+        const int R = ks_rt / 2;
+        for (int u = 0; u < ks_rt; ++u) {
+            const float *row = tile_b + (ty + 2 * R - u) * hx + tx + 2 * R;
+            for (int v = 0; v < ks_rt; ++v) acc = fmaf(w[u * ks_rt + v], row[-v], acc);
+        }
+    }
+    return acc;
+}
+
+// KS: 0 = no PSF, 25 = 25x25 weights from the kernel parameter, -1 = any odd size from smem.
+template <int B, int KS>
+__global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constant__ HessArgs a,
+                                                            const __grid_constant__ PsfW pw) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int set = blockIdx.y;
+    const SetDesc &d = a.desc[set];
+    const int N = (int)d.n_im;
+    const uint32_t npix = (uint32_t)N * (uint32_t)N;
+    const int ks = KS > 0 ? KS : (KS == 0 ? 0 : a.psf_size);
+    const int R = ks / 2;
+    const int hx = kTile + 2 * R, hy = kTile + 2 * R;
+    const int nbins = a.pc.nx * a.pc.ny;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    float *tile = reinterpret_cast<float *>(hist + nbins);
+    float *wsm = tile + (KS != 0 ? B * hx * hy : 0);
+    double *wred = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(wsm + (KS < 0 ? B * ks * ks : 0)) + 7u) & ~uintptr_t(7));
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nbins; i += kHessThreads) hist[i] = 0u;
+    if (KS < 0)
+        for (int i = tid; i < B * ks * ks; i += kHessThreads) wsm[i] = a.psf[i];
+    __syncthreads();
+
+    const float *img = a.image + d.img_off;
+    float *pout = a.pixels ? a.pixels + a.pix_off[set] : nullptr;
+    const int tiles_x = (N + kTile - 1) / kTile;
+    const int n_tiles = tiles_x * tiles_x;
+    double cs = 0.0, ms = 0.0, nv = 0.0;
+    uint32_t novf = 0u, ninv = 0u;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int y0 = (t / tiles_x) * kTile, x0 = (t % tiles_x) * kTile;
+        if (KS != 0) {
+            for (int i = tid; i < hx * hy; i += kHessThreads) {
+                const int ty = i / hx, tx = i - ty * hx;
+                int gy = (y0 - R + ty) % N;
+                gy += gy < 0 ? N : 0;
+                int gx = (x0 - R + tx) % N;
+                gx += gx < 0 ? N : 0;
+                const size_t src = (size_t)gy * N + gx;
+#pragma unroll
+                for (int b = 0; b < B; ++b) tile[b * hx * hy + i] = __ldg(img + (size_t)b * npix + src);
+            }
+            __syncthreads();
+        }
+        const int tx = tid & 31;
+        for (int ty = tid >> 5; ty < kTile; ty += kHessThreads / 32) {
+            const int y = y0 + ty, x = x0 + tx;
+            const bool in = y < N && x < N;
+            int bin = -1;
+            if (in) {
+                const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
+                float F[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    if (KS == 0) F[b] = __ldg(img + (size_t)b * npix + p);
+                    else if (KS > 0) F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, pw.w[b], ks);
+                    else F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, wsm + b * ks * ks, ks);
+                }
+                const PixelOut o = pixel_stage<B>(F, p, d.set_id, a.pc);
+                if (o.valid) {
+                    cs += (double)__fsub_rn(o.col, a.pc.c_lo);
+                    ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
+                    nv += 1.0;
+                    bin = o.bin;
+                    if (bin < 0) ++novf;
+                } else {
+                    ++ninv;
+                }
+                if (pout) {
+#pragma unroll
+                    for (int b = 0; b < B; ++b) pout[(size_t)b * npix + p] = F[b];
+                    pout[(size_t)B * npix + p] = o.valid ? o.mag : __int_as_float(0x7fc00000);
+                    pout[(size_t)(B + 1) * npix + p] = o.valid ? o.col : __int_as_float(0x7fc00000);
+                }
+            }
+            hist_add_warp(hist, nullptr, nullptr, bin, 0u);
+        }
+        if (KS != 0) __syncthreads();
+    }
+    __syncthreads();
+    uint32_t *gh = a.hess + (size_t)set * nbins;
+    for (int i = tid; i < nbins; i += kHessThreads) {
+        const uint32_t v = hist[i];
+        if (v) atomicAdd(gh + i, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        ms += __shfl_xor_sync(0xffffffffu, ms, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        novf += __shfl_xor_sync(0xffffffffu, novf, o);
+        ninv += __shfl_xor_sync(0xffffffffu, ninv, o);
+    }
+    const int wid = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        wred[wid * 3 + 0] = cs;
+        wred[wid * 3 + 1] = ms;
+        wred[wid * 3 + 2] = nv;
+        if (novf) atomicAdd(a.counters + (size_t)set * 2 + 0, novf);
+        if (ninv) atomicAdd(a.counters + (size_t)set * 2 + 1, ninv);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < kHessThreads / 32; ++w) {
+            t0 += wred[w * 3 + 0];
+            t1 += wred[w * 3 + 1];
+            t2 += wred[w * 3 + 2];
+        }
+        double *out = a.cta_moments + ((size_t)set * a.ctas_per_set + blockIdx.x) * 3;
+        out[0] = t0 + t2 * (double)a.pc.c_lo;
+        out[1] = t1 + t2 * (double)a.pc.m_lo;
+        out[2] = t2;
+    }
+}
+
+size_t hess_smem_bytes(int nb, int psf_size, int nx, int ny) {
+    const int R = psf_size / 2;
+    const int h = kTile + 2 * R;
+    size_t s = (size_t)nx * ny * 4;
+    if (psf_size > 0) s += (size_t)nb * h * h * 4;
+    if (psf_size > 0 && psf_size != 25) s += (size_t)nb * psf_size * psf_size * 4;
+    s = (s + 7) & ~size_t(7);
+    s += (kHessThreads / 32) * 3 * 8;
+    return s;
+}
+
+template <int B, int KS>
+static cudaError_t launch_hess_t(const HessArgs &a, const PsfW &w, size_t smem, cudaStream_t st) {
+    static size_t configured = 0;
+    auto k = hess_kernel<B, KS>;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    dim3 grid(a.ctas_per_set, a.n_sets);
+    k<<<grid, kHessThreads, smem, st>>>(a, w);
+    return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t launch_hess_b(const HessArgs &a, const PsfW &w, size_t smem, cudaStream_t st) {
+    if (!a.psf || a.psf_size == 0) return launch_hess_t<B, 0>(a, w, smem, st);
+    if (a.psf_size == 25) return launch_hess_t<B, 25>(a, w, smem, st);
+    return launch_hess_t<B, -1>(a, w, smem, st);
+}
+
+// The 25x25 weights travel as a kernel parameter (constant bank, compile-time offsets);
+// psf25_host is the context's host copy [kMaxBands][625] (or nullptr).
+cudaError_t launch_hess(const HessArgs &a, const float *psf25_host, cudaStream_t st) {
+    const size_t smem = hess_smem_bytes(a.n_bands, a.psf ? a.psf_size : 0, a.pc.nx, a.pc.ny);
+    PsfW w;
+    for (int b = 0; b < kMaxBands; ++b)
+        for (int i = 0; i < 625; ++i) w.w[b][i] = psf25_host ? psf25_host[b * 625 + i] : 0.0f;
+    switch (a.n_bands) {
+        case 2: return launch_hess_b<2>(a, w, smem, st);
+        case 3: return launch_hess_b<3>(a, w, smem, st);
+        default: return launch_hess_b<4>(a, w, smem, st);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Binning of given FP32 (magnitude, colour) pairs with the same rule (parity tests).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bin_mags_kernel(const float *mag, const float *col,
+                                                       const uint8_t *valid, uint32_t n,
+                                                       uint32_t *hess, uint32_t *counters,
+                                                       double *moments, PixelConsts pc) {
+    extern __shared__ uint32_t shist[];
+    const int nbins = pc.nx * pc.ny;
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) shist[i] = 0u;
+    __syncthreads();
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        int bin = -1;
+        if (i < n) {
+            if (valid[i]) {
+                bin = hess_bin(mag[i], col[i], pc);
+                if (moments) {
+                    atomicAdd(moments + 0, (double)col[i]);
+                    atomicAdd(moments + 1, (double)mag[i]);
+                    atomicAdd(moments + 2, 1.0);
+                }
+                if (bin < 0 && counters) atomicAdd(counters + 0, 1u);
+            } else if (counters) {
+                atomicAdd(counters + 1, 1u);
+            }
+        }
+        hist_add_warp(shist, nullptr, nullptr, bin, 0u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+        if (shist[i]) atomicAdd(hess + i, shist[i]);
+}
+
+cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *valid, uint32_t n,
+                            uint32_t *hess, uint32_t *counters, double *moments,
+                            const PixelConsts &pc, uint32_t *err, cudaStream_t st) {
+    (void)err;
+    const size_t smem = (size_t)pc.nx * pc.ny * 4;
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(bin_mags_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int grid = (int)((n + 255) / 256);
+    if (grid > 1024) grid = 1024;
+    if (grid < 1) grid = 1;
+    bin_mags_kernel<<<grid, 256, smem, st>>>(mag, col, valid, n, hess, counters, moments, pc);
+    return cudaGetLastError();
+}
+
+// One thread per set sums its partials in index order: deterministic moments.
+__global__ void moments_finalize_kernel(const double *partials, const uint32_t *begin,
+                                        const uint32_t *count, int n_sets, double *moments) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sets) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const double *p = partials + (size_t)begin[s] * 3;
+    for (uint32_t i = 0; i < count[s]; ++i) {
+        a0 += p[i * 3 + 0];
+        a1 += p[i * 3 + 1];
+        a2 += p[i * 3 + 2];
+    }
+    moments[s * 3 + 0] = a0;
+    moments[s * 3 + 1] = a1;
+    moments[s * 3 + 2] = a2;
+}
+
+cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part_begin,
+                                    const uint32_t *part_count, int n_sets, double *moments,
+                                    cudaStream_t st) {
+    moments_finalize_kernel<<<(n_sets + 127) / 128, 128, 0, st>>>(partials, part_begin, part_count,
+                                                                 n_sets, moments);
+    return cudaGetLastError();
+}
+
+}  // namespace pcmd

@@ -1,0 +1,131 @@
+// Internal layouts shared by the host table builder and the kernels of libpcmd.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace pcmd {
+
+constexpr int kMaxBands = 4;
+constexpr int kGroup = 8;                 // isochrone points per Philox HI/LO call
+constexpr float kPtrsThreshold = 10.0f;   // inversion below, transformed rejection at/above
+constexpr int kInvCap = 64;               // inversion counts are capped at 64 (lambda < 10)
+constexpr uint32_t kPtrsMaxAttempts = 1024u;
+
+// RNG stream kinds (tag = kind << 28 | half << 27 | sub)
+enum : uint32_t { kKindHi = 1u, kKindLo = 2u, kKindPtrs = 3u, kKindDust = 4u, kKindNoise = 5u };
+
+// device error bits
+enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
+
+// Fast-path record of 8 consecutive isochrone points of one dust half (staged in shared memory
+// by bulk copies).  Size 48 + 32 * B bytes (a multiple of 16).
+//   u32 gid              group index (points 8*gid .. 8*gid+7)
+//   u32 pad[3]
+//   u16 zc0[8]           Z_0 >> 16 per slot: hi16 >= zc0 means "maybe non-zero"
+//   u16 zc1[8]           Z_1 >> 16 per slot: a certain hit with hi16 < zc1 has n = 1
+//   f32 flux[8][B]       electrons per star of each slot
+__host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 48u + 32u * (uint32_t)nb; }
+
+// Slow-path record per point and half (global memory): full 32-bit thresholds.
+struct SlowRec {
+    uint32_t z0, z1;        // n > k  <=>  x > Z_k
+    uint32_t tail_off;      // index of Z_2 in the tail array
+    uint32_t tail_len;      // number of Z_k, k >= 2, below 0xFFFFFFFF
+};
+
+// Transformed-rejection record (lambda >= 10), 48 bytes.
+struct PtrsRec {
+    uint32_t i;             // canonical point index
+    float lam, b, a, twoa, vr, log_ia;
+    float flux[kMaxBands];
+    uint32_t pad;
+};
+static_assert(sizeof(PtrsRec) == 48, "PtrsRec layout");
+
+// Per-set descriptor (device memory).  Offsets are bytes from the start of the table buffer.
+struct __align__(16) SetDesc {
+    uint64_t grp_off[2];    // group records of half 0 / 1
+    uint64_t slow_off[2];   // SlowRec[P] of half 0 / 1
+    uint64_t tail_off;      // uint32 tail thresholds
+    uint64_t ptrs_off[2];   // PtrsRec lists
+    uint64_t img_off;       // float offset of the raw image [B][n][n]
+    uint32_t n_grp[2], n_ptrs[2];
+    uint32_t n_im, set_id;
+    uint32_t item_begin, n_items;   // work items (pixel tiles) of this set
+    float dust_a;           // ln(10) * log_ebv
+    float dust_sigma;
+    float dust_c[kMaxBands];  // -0.4 R_b: factor_b = 10^(dust_c[b] * E)
+    uint32_t dust_on, pad0;
+};
+
+// Constants of the pixel stage (noise, magnitudes, Hess binning).
+struct PixelConsts {
+    float sky[kMaxBands];
+    float t[kMaxBands];        // exposure times
+    float zp[kMaxBands];       // zero-points, FP32 part
+    float zp_lo[kMaxBands];    // zero-points minus their FP32 part
+    float c_lo, m_lo, inv_w;   // Hess axes (FP32 bin rule)
+    int nx, ny;
+    int noise;
+    uint64_t seed;
+};
+
+struct DrawArgs {
+    const uint8_t *tables;      // table buffer
+    const SetDesc *desc;        // [n_sets]
+    const uint2 *items;         // (set index, tile) per work item, grouped by set
+    const uint32_t *order;      // queue position -> item (longest first); nullptr = identity
+    uint32_t n_items;
+    uint32_t *queue;            // persistent work counter (nullptr = one item per CTA)
+    uint64_t seed;
+    float *image;               // raw images (IMAGE mode)
+    uint32_t *counts;           // COUNTS mode output [n_pix][2][P]
+    uint32_t count_pix0, count_npix, n_points;
+    uint32_t *err;              // device error word
+    int chunk;                  // groups per staged chunk
+    int split;                  // warps-groups sharing one pixel
+    // FUSED mode (no PSF): histogram outputs
+    uint32_t *hess;             // [n_sets][ny][nx]
+    uint32_t *counters;         // [n_sets][2]
+    double *item_moments;       // [n_items][3]
+    PixelConsts pc;
+};
+
+// PSF / noise / magnitude / Hess stage over raw images.
+struct HessArgs {
+    const float *image;         // raw images
+    const SetDesc *desc;        // for n_im, set_id, img_off
+    int n_sets, n_bands;
+    const float *psf;           // device [B][S][S] or nullptr
+    int psf_size;
+    uint32_t *hess;             // [n_sets][ny][nx]
+    uint32_t *counters;         // [n_sets][2]
+    double *cta_moments;        // [n_sets][ctas_per_set][3]
+    int ctas_per_set;
+    float *pixels;              // optional [n_sets][B+2][n^2] (packed like the images, B+2 planes)
+    const uint64_t *pix_off;    // float offsets of each set's pixel output
+    PixelConsts pc;
+};
+
+// launchers (implemented in the .cu files)
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, int grid,
+                        int block, size_t smem, cudaStream_t st);
+size_t draw_smem_bytes(int n_bands, int chunk, int block, int split, int mode, int nx, int ny);
+enum { kModeImage = 0, kModeCounts = 1, kModeFused = 2 };
+
+cudaError_t launch_hess(const HessArgs &a, const float *psf25_host, cudaStream_t st);
+size_t hess_smem_bytes(int n_bands, int psf_size, int nx, int ny);
+cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *valid, uint32_t n,
+                            uint32_t *hess, uint32_t *counters, double *moments,
+                            const PixelConsts &pc, uint32_t *err, cudaStream_t st);
+// sums per-CTA / per-item partial moments of each set, in a fixed order, into moments[s][3]
+cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part_begin,
+                                    const uint32_t *part_count, int n_sets, double *moments,
+                                    cudaStream_t st);
+cudaError_t launch_loglike(const uint32_t *hess, const double *moments, const SetDesc *desc,
+                           int n_sets, int nbins, const uint32_t *mock, double mock_sc,
+                           double mock_sm, double mock_nv, double mock_npix, int mode,
+                           int sqrtsum, double *ll, cudaStream_t st);
+cudaError_t upload_stirlerr(const float *tab16);
+
+}  // namespace pcmd
