@@ -34,6 +34,7 @@ WORKLOAD = ("plain full model: 256x256, 2 bands, 7 SFH x 7 [Fe/H] x 300 masses (
             "log10 Npix 2, log-normal dust F_dust 0.5, 25x25 Moffat PSF, sky + photon noise, "
             "100x100 Hess, Eq. 2-4 likelihood")
 METRIC = "model pixels/s (plain full model, one likelihood evaluation per step)"
+# Each step evaluates a new parameter point (a sampler-like random walk) with a new RNG set id.
 PEAK_ISSUE_PER_SM_CLK = 128          # 4 schedulers x 32 lanes: thread-instructions per clock
 OPS_PER_INV_DRAW = 6.0               # 1/8 Philox4x32-10 block (40 instr) + 16-bit compare
 OPS_PER_PTRS_DRAW = 60.0             # 1/2 Philox block + ~40 FP32 ops of the squeeze test
@@ -220,8 +221,18 @@ def run_gb300(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     base_id = rank * 10_000_000
 
+    # a sampler-like sequence of parameter points: small seeded steps around the mock's values
+    rng = np.random.default_rng(1234 + rank)
+    p0 = w.params[0]
+
+    def proposal():
+        return [W.Params(log_sfh=p0.log_sfh + rng.normal(0, 0.05, size=p0.log_sfh.size),
+                         feh_mean=p0.feh_mean + rng.normal(0, 0.02), feh_sigma=p0.feh_sigma,
+                         log_ebv=p0.log_ebv + rng.normal(0, 0.02), dust_sigma=p0.dust_sigma,
+                         dmod=p0.dmod + rng.normal(0, 0.02))]
+
     for i in range(args.warmup):
-        sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode, first_set_id=base_id + i)
+        sim.evaluate(proposal(), [n], mock_hess, mock_mom, npix, mode, first_set_id=base_id + i)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -232,10 +243,11 @@ def run_gb300(args, world, rank, local):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     lls = []
+    props = [proposal() for _ in range(args.steps)]
     for i in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (outside the interval)
         ev0[i].record(stream)
-        ll = sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode,
+        ll = sim.evaluate(props[i], [n], mock_hess, mock_mom, npix, mode,
                           first_set_id=base_id + args.warmup + i)
         ev1[i].record(stream)
         lls.append(float(ll[0]))
@@ -251,7 +263,7 @@ def run_gb300(args, world, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mock_hess.copy_(mock_host, non_blocking=True)
-        ll = sim.evaluate(w.params, [n], mock_hess, mock_mom, npix, mode,
+        ll = sim.evaluate(proposal(), [n], mock_hess, mock_mom, npix, mode,
                           first_set_id=base_id + 5_000_000 + i)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     clk = clocks.stop()

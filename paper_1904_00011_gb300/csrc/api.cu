@@ -81,7 +81,8 @@ struct pcmd_ctx {
     HostBuf h_tables, h_desc, h_items, h_order, h_meta, h_ll;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
-    std::vector<uint8_t> tab;
+    std::vector<SetTables> sets;
+    size_t tab_bytes = 0;
     std::vector<SetDesc> descs;
     std::vector<SetStats> stats;
     std::vector<uint2> item_list;
@@ -184,15 +185,46 @@ static pcmd_status check_params(pcmd_ctx *ctx, const pcmd_params *p, int n_sets,
 static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, const int *n_im,
                               uint32_t first_set_id, bool cost_sorted, int ppc) {
     const int B = ctx->model.n_bands;
-    ctx->tab.clear();
     ctx->descs.assign(n_sets, SetDesc());
     ctx->stats.assign(n_sets, SetStats());
     ctx->item_list.clear();
+    if ((int)ctx->sets.size() < n_sets) ctx->sets.resize(n_sets);
+    auto one = [&](int s) {
+        std::memset(&ctx->sets[s].d, 0, sizeof(SetDesc));
+        build_set_tables(ctx->model, p[s], ctx->sets[s], n_sets == 1);
+    };
+    if (n_sets > 1) parallel_for(n_sets, one);
+    else one(0);
+    std::vector<size_t> base(n_sets);
+    size_t total = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        base[s] = total;
+        total += (ctx->sets[s].bytes + 15) & ~size_t(15);
+    }
+    total = std::max<size_t>(total, 16);
+    if (ctx->staged_pending) {
+        CK(cudaEventSynchronize(ctx->staged));
+        ctx->staged_pending = false;
+    }
+    CK(ctx->h_tables.ensure(total));
+    {
+        uint8_t *dst = ctx->h_tables.as<uint8_t>();
+        auto em = [&](int s) { emit_set_tables(ctx->sets[s], dst + base[s]); };
+        if (n_sets > 1) parallel_for(n_sets, em);
+        else em(0);
+    }
+    ctx->tab_bytes = total;
     uint64_t img_off = 0;
     for (int s = 0; s < n_sets; ++s) {
         SetDesc &d = ctx->descs[s];
-        std::memset(&d, 0, sizeof d);
-        build_set_tables(ctx->model, p[s], ctx->tab, d, ctx->stats[s]);
+        d = ctx->sets[s].d;
+        ctx->stats[s] = ctx->sets[s].st;
+        for (int h = 0; h < 2; ++h) {
+            d.grp_off[h] += base[s];
+            d.slow_off[h] += base[s];
+            d.ptrs_off[h] += base[s];
+        }
+        d.tail_off += base[s];
         d.n_im = (uint32_t)n_im[s];
         d.set_id = first_set_id + (uint32_t)s;
         d.img_off = img_off;
@@ -202,7 +234,6 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         d.n_items = (npix + ppc - 1) / ppc;
         for (uint32_t t = 0; t < d.n_items; ++t) ctx->item_list.push_back(make_uint2((uint32_t)s, t));
     }
-    if (ctx->tab.empty()) ctx->tab.resize(16, 0);
     const size_t n_items = ctx->item_list.size();
     ctx->order_list.resize(n_items);
     std::iota(ctx->order_list.begin(), ctx->order_list.end(), 0u);
@@ -212,23 +243,17 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
                    ctx->stats[ctx->item_list[b].x].cost_per_pixel;
         });
     }
-    if (ctx->staged_pending) {
-        CK(cudaEventSynchronize(ctx->staged));
-        ctx->staged_pending = false;
-    }
-    CK(ctx->h_tables.ensure(ctx->tab.size()));
     CK(ctx->h_desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
-    CK(ctx->tables.ensure(ctx->tab.size()));
+    CK(ctx->tables.ensure(ctx->tab_bytes));
     CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->items.ensure(sizeof(uint2) * n_items));
     CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
-    std::memcpy(ctx->h_tables.p, ctx->tab.data(), ctx->tab.size());
     std::memcpy(ctx->h_desc.p, ctx->descs.data(), sizeof(SetDesc) * n_sets);
     std::memcpy(ctx->h_items.p, ctx->item_list.data(), sizeof(uint2) * n_items);
     std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
-    CK(cudaMemcpyAsync(ctx->tables.p, ctx->h_tables.p, ctx->tab.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tables.p, ctx->h_tables.p, ctx->tab_bytes, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
@@ -324,6 +349,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
         m.r_ext[b] = b < c.n_bands ? c.r_ext[b] : 0.0;
     }
     m.build_imf();
+    m.build_base_flux();
     ctx->cfg.feh_grid = nullptr;
     ctx->cfg.mass = nullptr;
     ctx->cfg.abs_mag = nullptr;

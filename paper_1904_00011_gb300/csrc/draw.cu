@@ -117,16 +117,18 @@ struct Acc {
     }
 };
 
-__device__ __forceinline__ uint32_t maybe_mask(const uint4 &w, const uint4 &z) {
+// Per-slot "maybe non-zero" bits of one HI call against the pre-shifted coarse thresholds:
+// odd slots compare the word itself, even slots the word shifted left by 16.
+__device__ __forceinline__ uint32_t maybe_mask(const uint4 &w, const uint4 &za, const uint4 &zb) {
     uint32_t m = 0;
-    m |= (uint32_t)((w.x & 0xFFFFu) >= (z.x & 0xFFFFu)) << 0;
-    m |= (uint32_t)((w.x >> 16) >= (z.x >> 16)) << 1;
-    m |= (uint32_t)((w.y & 0xFFFFu) >= (z.y & 0xFFFFu)) << 2;
-    m |= (uint32_t)((w.y >> 16) >= (z.y >> 16)) << 3;
-    m |= (uint32_t)((w.z & 0xFFFFu) >= (z.z & 0xFFFFu)) << 4;
-    m |= (uint32_t)((w.z >> 16) >= (z.z >> 16)) << 5;
-    m |= (uint32_t)((w.w & 0xFFFFu) >= (z.w & 0xFFFFu)) << 6;
-    m |= (uint32_t)((w.w >> 16) >= (z.w >> 16)) << 7;
+    m |= (uint32_t)((w.x << 16) >= za.x) << 0;
+    m |= (uint32_t)(w.x >= za.y) << 1;
+    m |= (uint32_t)((w.y << 16) >= za.z) << 2;
+    m |= (uint32_t)(w.y >= za.w) << 3;
+    m |= (uint32_t)((w.z << 16) >= zb.x) << 4;
+    m |= (uint32_t)(w.z >= zb.y) << 5;
+    m |= (uint32_t)((w.w << 16) >= zb.z) << 6;
+    m |= (uint32_t)(w.w >= zb.w) << 7;
     return m;
 }
 
@@ -137,28 +139,28 @@ struct ItemCtx {
     const uint32_t *tail;
 };
 
+constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
+
+// Resolve the queued maybe-hits of this thread: entry = g << 19 | slot << 16 | hi16, g the
+// group's index in the staged chunk.  n = 1 when hi16 is above Z_0 >> 16 and below Z_1 >> 16;
+// otherwise the LO call completes the 32-bit word and the full thresholds decide.
 template <int B, bool KAHAN, int MODE, int H>
-__device__ __forceinline__ void hit_path(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
-                                         uint32_t gid, const uint4 &w, const uint4 &z0,
-                                         uint32_t m, Acc<B, KAHAN> &acc, uint32_t k0,
-                                         uint32_t k1) {
-    const uint4 z1 = *reinterpret_cast<const uint4 *>(r + 32);
-    const float *fl = reinterpret_cast<const float *>(r + 48);
-    uint4 wlo = make_uint4(0, 0, 0, 0);
-    bool have_lo = false;
-    do {
-        const uint32_t j = (uint32_t)(__ffs(m) - 1);
-        m &= m - 1u;
-        const uint32_t hi = slot16(w, j);
-        const uint32_t zc0 = slot16(z0, j), zc1 = slot16(z1, j);
+__device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic,
+                                            const uint8_t *cb, const uint32_t *queue, int qn,
+                                            Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
+    constexpr uint32_t rec = group_rec_bytes(B);
+    for (int q = 0; q < qn; ++q) {
+        const uint32_t e = queue[q * blockDim.x + threadIdx.x];
+        const uint32_t g = e >> 19, j = (e >> 16) & 7u, hi = e & 0xFFFFu;
+        const uint8_t *r = cb + g * rec;
+        const uint32_t zc0 = *reinterpret_cast<const uint32_t *>(r + kRecZs + 4 * j) >> 16;
+        const uint32_t zc1 = *reinterpret_cast<const uint16_t *>(r + kRecZc1 + 2 * j);
         uint32_t n;
         if (hi > zc0 && hi < zc1) {
             n = 1u;
         } else {
-            if (!have_lo) {
-                wlo = philox(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), k0, k1);
-                have_lo = true;
-            }
+            const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
+            const uint4 wlo = philox(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), k0, k1);
             const uint32_t x = (hi << 16) | slot16(wlo, j);
             const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + (gid * 8u + j));
             if (x <= sr.x) {
@@ -174,29 +176,46 @@ __device__ __forceinline__ void hit_path(const DrawArgs &a, const ItemCtx &ic, c
             }
         }
         if (n) {
-            acc.template add<H>((float)n, fl + j * B);
+            acc.template add<H>((float)n, reinterpret_cast<const float *>(r + kRecFlux) + j * B);
             if (MODE == kModeCounts) {
+                const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
                 if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
-                             gid * 8u + j] = n;
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * 8u + j] = n;
             }
         }
-    } while (m);
+    }
 }
 
+// One staged chunk of groups: the HI call of every (pixel, group), a compare per slot, and the
+// rare maybe-hits pushed to the thread's queue, drained warp-wide when any lane is nearly full
+// and at the end of the chunk (instead of a warp-divergent branch per group).
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
                                               const uint8_t *cb, uint32_t cnt, int sidx,
-                                              Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
+                                              uint32_t *queue, Acc<B, KAHAN> &acc, uint32_t k0,
+                                              uint32_t k1) {
     constexpr uint32_t rec = group_rec_bytes(B);
+    int qn = 0;
     for (uint32_t g = (uint32_t)sidx; g < cnt; g += (uint32_t)a.split) {
         const uint8_t *r = cb + g * rec;
         const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
-        const uint4 z0 = *reinterpret_cast<const uint4 *>(r + 16);
+        const uint4 za = *reinterpret_cast<const uint4 *>(r + kRecZs);
+        const uint4 zb = *reinterpret_cast<const uint4 *>(r + kRecZs + 16);
         const uint4 w = philox(ic.pix, gid, ic.set, rng_tag(kKindHi, H, 0), k0, k1);
-        const uint32_t m = maybe_mask(w, z0);
-        if (m != 0u && ic.active) hit_path<B, KAHAN, MODE, H>(a, ic, r, gid, w, z0, m, acc, k0, k1);
+        uint32_t m = maybe_mask(w, za, zb);
+        if (!ic.active) m = 0u;
+        while (m) {
+            const uint32_t j = (uint32_t)(__ffs(m) - 1);
+            m &= m - 1u;
+            queue[qn * blockDim.x + threadIdx.x] = (g << 19) | (j << 16) | slot16(w, j);
+            ++qn;
+        }
+        if (__any_sync(0xffffffffu, qn > kQueueCap - 8)) {
+            drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
+            qn = 0;
+        }
     }
+    if (__any_sync(0xffffffffu, qn > 0)) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
 }
 
 template <int B, bool KAHAN, int MODE, int H>
@@ -248,7 +267,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
     volatile uint32_t *s_item = reinterpret_cast<volatile uint32_t *>(smem + 16);
     uint32_t *s_ntouch = reinterpret_cast<uint32_t *>(smem + 20);
     uint8_t *bufs = smem + 32;
-    float *red = reinterpret_cast<float *>(bufs + 2u * chunk * rec);
+    uint32_t *queue = reinterpret_cast<uint32_t *>(bufs + 2u * chunk * rec);
+    float *red = reinterpret_cast<float *>(queue + (size_t)kQueueCap * blockDim.x);
     const int tid = threadIdx.x;
     const int ppc = blockDim.x / a.split;
     const int sidx = tid / ppc;
@@ -327,8 +347,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             const uint32_t first = (h ? c - nc0 : c) * chunk;
             const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
             const uint8_t *cb = bufs + b * chunk * rec;
-            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, cb, cnt, sidx, acc, k0, k1);
-            else process_chunk<B, KAHAN, MODE, 1>(a, ic, cb, cnt, sidx, acc, k0, k1);
+            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, cb, cnt, sidx, queue, acc, k0, k1);
+            else process_chunk<B, KAHAN, MODE, 1>(a, ic, cb, cnt, sidx, queue, acc, k0, k1);
             __syncthreads();
         }
 
@@ -457,7 +477,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
 }
 
 size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx, int ny) {
-    size_t s = 32 + 2 * (size_t)chunk * group_rec_bytes(nb) + (size_t)block * 2 * nb * 4;
+    size_t s = 32 + 2 * (size_t)chunk * group_rec_bytes(nb) + (size_t)kQueueCap * block * 4 +
+               (size_t)block * 2 * nb * 4;
     if (mode == kModeFused) {
         s += (size_t)nx * ny * 4 + (size_t)(block / split) * 4;
         s = (s + 7) & ~size_t(7);

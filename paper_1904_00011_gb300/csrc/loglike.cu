@@ -9,29 +9,36 @@
 
 namespace pcmd {
 
-__global__ void __launch_bounds__(256) loglike_kernel(const uint32_t *hess, const double *moments,
-                                                      const SetDesc *desc, int nbins,
-                                                      const uint32_t *mock, double mock_sc,
-                                                      double mock_sm, double mock_nv,
-                                                      double mock_npix, int mode, int sqrtsum,
-                                                      double *ll) {
-    __shared__ double wsum[8];
+// Per-bin terms in FP32 where they are well conditioned (sigma^2 = max(d^2 + m^2, 4) needs no
+// square root; the fraction difference is formed in FP64), every accumulation in FP64.
+__global__ void __launch_bounds__(1024) loglike_kernel(const uint32_t *hess, const double *moments,
+                                                       const SetDesc *desc, int nbins,
+                                                       const uint32_t *mock, double mock_sc,
+                                                       double mock_sm, double mock_nv,
+                                                       double mock_npix, int mode, int sqrtsum,
+                                                       double *ll) {
+    __shared__ double wsum[32];
     const int s = blockIdx.x;
     const double n_m = (double)desc[s].n_im * (double)desc[s].n_im;
     const double n_d = mock_npix;
+    const double inv_nd = 1.0 / n_d, inv_nm = 1.0 / n_m, ratio = n_d / n_m;
     const uint32_t *m = hess + (size_t)s * nbins;
     double acc = 0.0;
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
-        const double di = (double)mock[i], mi = (double)m[i];
+        const uint32_t du = __ldg(mock + i), mu = __ldg(m + i);
         if (mode == 1) {
-            const double mh = fmax(mi, 0.5) * (n_d / n_m);
-            acc += di * log(mh) - mh - lgamma(di + 1.0);
+            const double mh = fmax((double)mu, 0.5) * ratio;
+            acc -= mh;
+            if (du) {
+                const double di = (double)du;
+                acc += di * log(mh) - lgamma(di + 1.0);
+            }
         } else {
-            if (di == 0.0 && mi == 0.0) continue;
-            double sig = sqrtsum ? sqrt(di + mi) : sqrt(di * di + mi * mi);
-            sig = fmax(sig, 2.0);
-            const double g = di / n_d - mi / n_m;
-            acc += -(g * g) / (2.0 * sig * sig);
+            if ((du | mu) == 0u) continue;
+            const float df = (float)du, mf = (float)mu;
+            const float sig2 = fmaxf(sqrtsum ? df + mf : df * df + mf * mf, 4.0f);
+            const double g = (double)du * inv_nd - (double)mu * inv_nm;
+            acc -= (double)(__fdiv_rn((float)(g * g), 2.0f * sig2));
         }
     }
 #pragma unroll
@@ -60,7 +67,7 @@ cudaError_t launch_loglike(const uint32_t *hess, const double *moments, const Se
                            int n_sets, int nbins, const uint32_t *mock, double mock_sc,
                            double mock_sm, double mock_nv, double mock_npix, int mode,
                            int sqrtsum, double *ll, cudaStream_t st) {
-    loglike_kernel<<<n_sets, 256, 0, st>>>(hess, moments, desc, nbins, mock, mock_sc, mock_sm,
+    loglike_kernel<<<n_sets, n_sets >= 152 ? 256 : 1024, 0, st>>>(hess, moments, desc, nbins, mock, mock_sc, mock_sm,
                                            mock_nv, mock_npix, mode, sqrtsum, ll);
     return cudaGetLastError();
 }

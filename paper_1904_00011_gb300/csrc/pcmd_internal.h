@@ -18,13 +18,15 @@ enum : uint32_t { kKindHi = 1u, kKindLo = 2u, kKindPtrs = 3u, kKindDust = 4u, kK
 enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
 
 // Fast-path record of 8 consecutive isochrone points of one dust half (staged in shared memory
-// by bulk copies).  Size 48 + 32 * B bytes (a multiple of 16).
+// by bulk copies).  Size 64 + 32 * B bytes (a multiple of 16).
 //   u32 gid              group index (points 8*gid .. 8*gid+7)
 //   u32 pad[3]
-//   u16 zc0[8]           Z_0 >> 16 per slot: hi16 >= zc0 means "maybe non-zero"
+//   u32 zs[8]            (Z_0 >> 16) << 16 per slot: slot j "may be non-zero" when
+//                        hi16 >= Z_0 >> 16, i.e. w >= zs (odd j) or (w << 16) >= zs (even j)
 //   u16 zc1[8]           Z_1 >> 16 per slot: a certain hit with hi16 < zc1 has n = 1
 //   f32 flux[8][B]       electrons per star of each slot
-__host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 48u + 32u * (uint32_t)nb; }
+__host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 32u * (uint32_t)nb; }
+constexpr uint32_t kRecZs = 16, kRecZc1 = 48, kRecFlux = 64;
 
 // Slow-path record per point and half (global memory): full 32-bit thresholds.
 struct SlowRec {
@@ -82,7 +84,7 @@ struct DrawArgs {
     uint32_t *counts;           // COUNTS mode output [n_pix][2][P]
     uint32_t count_pix0, count_npix, n_points;
     uint32_t *err;              // device error word
-    int chunk;                  // groups per staged chunk
+    int chunk;                  // groups per staged chunk (<= 256)
     int split;                  // warps-groups sharing one pixel
     // FUSED mode (no PSF): histogram outputs
     uint32_t *hess;             // [n_sets][ny][nx]

@@ -13,8 +13,13 @@
 // word x gives n > k iff x > Z_k = ceil(F_k 2^32 - 1/2) - 1 (saturating at 2^32 - 1).
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
+#include <mutex>
+#include <thread>
 
 namespace pcmd {
 
@@ -108,23 +113,34 @@ void Model::lambdas(const pcmd_params &p, std::vector<float> (&lam_h)[2]) const 
     }
 }
 
-void Model::fluxes(double dmod, std::vector<float> &flux) const {
+// Electrons per star: t_b 10^(-0.4 (M_b + dmod - ZP_b)) = [t_b 10^(-0.4 (M_b - ZP_b))] 10^(-0.4 dmod);
+// the bracket is computed once per context (base_flux), the distance factor once per model.
+void Model::build_base_flux() {
     const size_t P = (size_t)n_points();
-    flux.assign(P * n_bands, 0.0f);
+    base_flux.assign(P * n_bands, 0.0);
     for (size_t i = 0; i < P; ++i)
         for (int b = 0; b < n_bands; ++b) {
-            double s = abs_mag[i * n_bands + b] + dmod;
-            s = s - zeropoint[b];
+            double s = abs_mag[i * n_bands + b] - zeropoint[b];
             s = -0.4 * s;
-            const double f = std::pow(10.0, s);
-            flux[i * n_bands + b] = (float)(exptime[b] * f);
+            base_flux[i * n_bands + b] = exptime[b] * std::pow(10.0, s);
         }
 }
 
+void Model::fluxes(double dmod, std::vector<float> &flux) const {
+    const size_t n = base_flux.size();
+    flux.resize(n);
+    const double f = std::pow(10.0, -0.4 * dmod);
+    for (size_t i = 0; i < n; ++i) flux[i] = (float)(base_flux[i] * f);
+}
+
+// Z = ceil(F 2^32 - 1/2) - 1 with F 2^32 - 1/2 exact in FP64 and non-negative (F >= e^-10):
+// the ceiling is the truncation plus one unless the value is already an integer.
 uint32_t threshold_of(double F) {
-    const double T = std::ceil(std::ldexp(F, 32) - 0.5);
-    if (T >= 4294967296.0) return 0xFFFFFFFFu;
-    return (uint32_t)(T - 1.0);
+    const double y = F * 4294967296.0 - 0.5;
+    if (y >= 4294967295.0) return 0xFFFFFFFFu;   // T = ceil(y) >= 2^32
+    const uint64_t t = (uint64_t)y;
+    const uint64_t T = t + (y > (double)t ? 1u : 0u);
+    return (uint32_t)(T - 1u);
 }
 
 int inversion_thresholds(float lam_f, uint32_t *z, int cap) {
@@ -172,101 +188,212 @@ void stirlerr_table(float out[16]) {
     }
 }
 
-// Device table of one model, appended to `buf` (16-byte aligned sections).
-void build_set_tables(const Model &m, const pcmd_params &p, std::vector<uint8_t> &buf,
-                      SetDesc &d, SetStats &st) {
-    std::vector<float> lam_h[2];
-    std::vector<float> flux;
-    m.lambdas(p, lam_h);
-    m.fluxes(p.dmod, flux);
+// ---------------------------------------------------------------------------------------
+// Worker pool: run(n, f) calls f(0..n-1) on the pool's threads and the caller.
+// ---------------------------------------------------------------------------------------
+class Pool {
+public:
+    explicit Pool(int n_workers) {
+        for (int t = 0; t < n_workers; ++t) th_.emplace_back([this] { loop(); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    int size() const { return (int)th_.size() + 1; }
+    void run(int n, const std::function<void(int)> &f) {
+        if (n <= 1 || th_.empty()) {
+            for (int i = 0; i < n; ++i) f(i);
+            return;
+        }
+        std::unique_lock<std::mutex> lk(mu_);
+        job_ = &f;
+        n_ = n;
+        next_ = 0;
+        left_ = n;
+        ++gen_;
+        lk.unlock();
+        cv_.notify_all();
+        work();
+        lk.lock();
+        done_.wait(lk, [this] { return left_ == 0; });
+        job_ = nullptr;
+    }
+
+private:
+    void work() {
+        while (true) {
+            int i;
+            const std::function<void(int)> *f;
+            {
+                std::lock_guard<std::mutex> g(mu_);
+                if (!job_ || next_ >= n_) return;
+                i = next_++;
+                f = job_;
+            }
+            (*f)(i);
+            std::lock_guard<std::mutex> g(mu_);
+            if (--left_ == 0) done_.notify_all();
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        while (true) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || (gen_ != seen && job_ && next_ < n_); });
+                if (stop_) return;
+                seen = gen_;
+            }
+            work();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)> *job_ = nullptr;
+    int n_ = 0, next_ = 0, left_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+static Pool &pool() {
+    static Pool p([] {
+        const unsigned hc = std::thread::hardware_concurrency();
+        return (int)std::min(15u, hc > 1 ? hc - 1 : 0u);
+    }());
+    return p;
+}
+
+void parallel_for(int n, const std::function<void(int)> &f) { pool().run(n, f); }
+
+static void build_part(const Model &m, const std::vector<float> &lam, const std::vector<float> &flux,
+                       uint32_t g0, uint32_t g1, SlowRec *slow, Part &out) {
+    const int B = m.n_bands;
+    const uint32_t P = (uint32_t)m.n_points();
+    const uint32_t rec = group_rec_bytes(B);
+    uint32_t z[kInvCap];
+    out.grp.clear();
+    out.ptrs.clear();
+    out.tail.clear();
+    out.grp.reserve((size_t)(g1 - g0) * rec);
+    for (uint32_t g = g0; g < g1; ++g) {
+        uint16_t zc0[8], zc1[8];
+        float fl[8][kMaxBands];
+        bool active = false;
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t i = g * 8 + j;
+            zc0[j] = 0xFFFFu;
+            zc1[j] = 0xFFFFu;
+            for (int b = 0; b < kMaxBands; ++b) fl[j][b] = 0.0f;
+            SlowRec &sr = slow[(size_t)g * 8 + j];
+            sr = SlowRec{0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u};
+            if (i >= P) continue;
+            for (int b = 0; b < B; ++b) fl[j][b] = flux[(size_t)i * B + b];
+            const float l = lam[i];
+            if (!(l > 0.0f)) continue;
+            if (l >= kPtrsThreshold) {
+                PtrsRec r;
+                std::memset(&r, 0, sizeof r);
+                r.i = i;
+                ptrs_constants(l, r);
+                for (int b = 0; b < B; ++b) r.flux[b] = flux[(size_t)i * B + b];
+                out.ptrs.push_back(r);
+                continue;
+            }
+            const int nz = inversion_thresholds(l, z, kInvCap);
+            if (z[0] == 0xFFFFFFFFu) continue;
+            sr.z0 = z[0];
+            sr.z1 = nz > 1 ? z[1] : 0xFFFFFFFFu;
+            sr.tail_off = (uint32_t)out.tail.size();   // local; rebased when parts are joined
+            for (int k = 2; k < nz; ++k) {
+                if (z[k] == 0xFFFFFFFFu) break;
+                out.tail.push_back(z[k]);
+                sr.tail_len++;
+            }
+            zc0[j] = (uint16_t)(sr.z0 >> 16);
+            zc1[j] = (uint16_t)(sr.z1 >> 16);
+            active = true;
+        }
+        if (!active) continue;
+        const size_t o = out.grp.size();
+        out.grp.resize(o + rec, 0);
+        uint8_t *r = out.grp.data() + o;
+        uint32_t zs[8];
+        for (uint32_t j = 0; j < 8; ++j) zs[j] = (uint32_t)zc0[j] << 16;
+        std::memcpy(r, &g, 4);
+        std::memcpy(r + kRecZs, zs, 32);
+        std::memcpy(r + kRecZc1, zc1, 16);
+        for (uint32_t j = 0; j < 8; ++j) std::memcpy(r + kRecFlux + j * B * 4, fl[j], (size_t)B * 4);
+    }
+}
+
+// Tables of one model, built over the worker pool when `parallel` is set (large grids).
+// Offsets in `t.d` are relative to the start of the model's table; emit_set_tables writes it.
+void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool parallel) {
+    m.lambdas(p, t.lam_h);
+    m.fluxes(p.dmod, t.flux);
     const int B = m.n_bands;
     const uint32_t P = (uint32_t)m.n_points();
     const uint32_t G = (P + 7) / 8;
     const uint32_t rec = group_rec_bytes(B);
-    const size_t base = align16(buf.size());
-
-    std::vector<uint8_t> grp[2];
-    std::vector<SlowRec> slow[2];
-    std::vector<PtrsRec> ptrs[2];
-    std::vector<uint32_t> tail;
-    uint32_t z[kInvCap];
-    st = SetStats();
+    int n_parts = 1;
+    if (parallel && G >= 256) n_parts = std::min<int>(pool().size() * 2, (int)(G / 64));
+    t.n_parts = n_parts;
+    t.G = G;
+    t.rec = rec;
     for (int h = 0; h < 2; ++h) {
-        slow[h].assign((size_t)G * 8, SlowRec{0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u});
-        for (uint32_t g = 0; g < G; ++g) {
-            uint16_t zc0[8], zc1[8];
-            float fl[8][kMaxBands];
-            bool active = false;
-            for (uint32_t j = 0; j < 8; ++j) {
-                const uint32_t i = g * 8 + j;
-                zc0[j] = 0xFFFFu;
-                zc1[j] = 0xFFFFu;
-                for (int b = 0; b < kMaxBands; ++b) fl[j][b] = 0.0f;
-                if (i >= P) continue;
-                for (int b = 0; b < B; ++b) fl[j][b] = flux[(size_t)i * B + b];
-                const float lam = lam_h[h][i];
-                if (!(lam > 0.0f)) continue;
-                if (lam >= kPtrsThreshold) {
-                    PtrsRec r;
-                    std::memset(&r, 0, sizeof r);
-                    r.i = i;
-                    ptrs_constants(lam, r);
-                    for (int b = 0; b < B; ++b) r.flux[b] = flux[(size_t)i * B + b];
-                    ptrs[h].push_back(r);
-                    continue;
-                }
-                const int nz = inversion_thresholds(lam, z, kInvCap);
-                if (z[0] == 0xFFFFFFFFu) continue;
-                SlowRec &s = slow[h][i];
-                s.z0 = z[0];
-                s.z1 = nz > 1 ? z[1] : 0xFFFFFFFFu;
-                s.tail_off = (uint32_t)tail.size();
-                s.tail_len = 0;
-                for (int k = 2; k < nz; ++k) {
-                    if (z[k] == 0xFFFFFFFFu) break;
-                    tail.push_back(z[k]);
-                    s.tail_len++;
-                }
-                zc0[j] = (uint16_t)(s.z0 >> 16);
-                zc1[j] = (uint16_t)(s.z1 >> 16);
-                active = true;
-            }
-            if (!active) continue;
-            const size_t o = grp[h].size();
-            grp[h].resize(o + rec, 0);
-            uint8_t *r = grp[h].data() + o;
-            std::memcpy(r, &g, 4);
-            std::memcpy(r + 16, zc0, 16);
-            std::memcpy(r + 32, zc1, 16);
-            for (uint32_t j = 0; j < 8; ++j) std::memcpy(r + 48 + j * B * 4, fl[j], (size_t)B * 4);
-        }
-        st.n_inv_groups[h] = (uint32_t)(grp[h].size() / rec);
-        st.n_ptrs[h] = (uint32_t)ptrs[h].size();
+        t.slow[h].resize((size_t)G * 8);
+        t.parts[h].resize(n_parts);
     }
-    if (tail.empty()) tail.push_back(0xFFFFFFFFu);
+    auto task = [&](int q) {
+        const int h = q / n_parts, k = q % n_parts;
+        const uint32_t g0 = (uint32_t)((uint64_t)G * k / n_parts);
+        const uint32_t g1 = (uint32_t)((uint64_t)G * (k + 1) / n_parts);
+        build_part(m, t.lam_h[h], t.flux, g0, g1, t.slow[h].data(), t.parts[h][k]);
+    };
+    if (n_parts > 1) parallel_for(2 * n_parts, task);
+    else for (int q = 0; q < 2; ++q) task(q);
 
-    size_t off = base;
+    SetStats &st = t.st;
+    SetDesc &d = t.d;
+    st = SetStats();
+    t.tail_total = 0;
+    for (int h = 0; h < 2; ++h) {
+        size_t ng = 0, np = 0;
+        for (int k = 0; k < n_parts; ++k) {
+            const uint32_t g0 = (uint32_t)((uint64_t)G * k / n_parts);
+            const uint32_t g1 = (uint32_t)((uint64_t)G * (k + 1) / n_parts);
+            const uint32_t base = (uint32_t)t.tail_total;
+            if (base)
+                for (size_t i = (size_t)g0 * 8; i < (size_t)g1 * 8; ++i)
+                    if (t.slow[h][i].tail_len) t.slow[h][i].tail_off += base;
+            t.tail_total += t.parts[h][k].tail.size();
+            ng += t.parts[h][k].grp.size() / rec;
+            np += t.parts[h][k].ptrs.size();
+        }
+        st.n_inv_groups[h] = (uint32_t)ng;
+        st.n_ptrs[h] = (uint32_t)np;
+    }
+    size_t off = 0;
     auto place = [&](size_t bytes) {
         const size_t o = off;
         off = align16(off + bytes);
         return o;
     };
     for (int h = 0; h < 2; ++h) {
-        d.grp_off[h] = place(grp[h].size());
-        d.slow_off[h] = place(slow[h].size() * sizeof(SlowRec));
-        d.ptrs_off[h] = place(ptrs[h].size() * sizeof(PtrsRec));
+        d.grp_off[h] = place((size_t)st.n_inv_groups[h] * rec);
+        d.slow_off[h] = place(t.slow[h].size() * sizeof(SlowRec));
+        d.ptrs_off[h] = place((size_t)st.n_ptrs[h] * sizeof(PtrsRec));
         d.n_grp[h] = st.n_inv_groups[h];
         d.n_ptrs[h] = st.n_ptrs[h];
     }
-    d.tail_off = place(tail.size() * 4);
-    buf.resize(off, 0);
-    for (int h = 0; h < 2; ++h) {
-        if (!grp[h].empty()) std::memcpy(buf.data() + d.grp_off[h], grp[h].data(), grp[h].size());
-        std::memcpy(buf.data() + d.slow_off[h], slow[h].data(), slow[h].size() * sizeof(SlowRec));
-        if (!ptrs[h].empty())
-            std::memcpy(buf.data() + d.ptrs_off[h], ptrs[h].data(), ptrs[h].size() * sizeof(PtrsRec));
-    }
-    std::memcpy(buf.data() + d.tail_off, tail.data(), tail.size() * 4);
+    d.tail_off = place(std::max<size_t>(t.tail_total, 1) * 4);
+    t.bytes = off;
 
     // dust screen of this model (Section 2.2): E = 10^log_ebv exp(sigma z)
     d.dust_on = m.dust ? 1u : 0u;
@@ -275,6 +402,31 @@ void build_set_tables(const Model &m, const pcmd_params &p, std::vector<uint8_t>
     for (int b = 0; b < kMaxBands; ++b) d.dust_c[b] = b < B ? (float)(-0.4 * m.r_ext[b]) : 0.0f;
     st.cost_per_pixel = 60.0 * (st.n_inv_groups[0] + st.n_inv_groups[1]) +
                         180.0 * (st.n_ptrs[0] + st.n_ptrs[1]) + 200.0;
+}
+
+// Write the model's table (t.bytes bytes) at dst.
+void emit_set_tables(const SetTables &t, uint8_t *dst) {
+    const SetDesc &d = t.d;
+    for (int h = 0; h < 2; ++h) {
+        size_t go = d.grp_off[h], po = d.ptrs_off[h];
+        for (int k = 0; k < t.n_parts; ++k) {
+            const Part &pt = t.parts[h][k];
+            if (!pt.grp.empty()) std::memcpy(dst + go, pt.grp.data(), pt.grp.size());
+            go += pt.grp.size();
+            if (!pt.ptrs.empty()) std::memcpy(dst + po, pt.ptrs.data(), pt.ptrs.size() * sizeof(PtrsRec));
+            po += pt.ptrs.size() * sizeof(PtrsRec);
+        }
+        std::memcpy(dst + d.slow_off[h], t.slow[h].data(), t.slow[h].size() * sizeof(SlowRec));
+    }
+    uint32_t *tail = reinterpret_cast<uint32_t *>(dst + d.tail_off);
+    size_t o = 0;
+    for (int h = 0; h < 2; ++h)
+        for (int k = 0; k < t.n_parts; ++k) {
+            const Part &pt = t.parts[h][k];
+            if (!pt.tail.empty()) std::memcpy(tail + o, pt.tail.data(), pt.tail.size() * 4);
+            o += pt.tail.size();
+        }
+    if (o == 0) tail[0] = 0xFFFFFFFFu;
 }
 
 }  // namespace pcmd

@@ -1,6 +1,7 @@
 // Host-side model and table builder of libpcmd.
 #pragma once
 #include <stdint.h>
+#include <functional>
 #include <vector>
 
 #include "../../include/pcmd.h"
@@ -13,6 +14,7 @@ struct Model {
     int n_bands = 2, n_ages = 1, n_feh = 1, n_mass = 1;
     std::vector<double> feh, mass, abs_mag;
     std::vector<double> imf;   // [n_ages][n_feh][n_mass], each isochrone sums to 1
+    std::vector<double> base_flux;  // [P][n_bands] electrons per star at distance modulus 0
     double imf_slope = 2.35, mdf_cut = 0.01, f_dust = 0.5;
     double exptime[kMaxBands] = {1, 1, 1, 1}, zeropoint[kMaxBands] = {0, 0, 0, 0};
     double r_ext[kMaxBands] = {0, 0, 0, 0};
@@ -20,6 +22,7 @@ struct Model {
 
     int n_points() const { return n_ages * n_feh * n_mass; }
     void build_imf();
+    void build_base_flux();
     void mdf_weights(double mu, double sigma, std::vector<double> &w) const;
     void lambdas(const pcmd_params &p, std::vector<float> (&lam_h)[2]) const;
     void fluxes(double dmod, std::vector<float> &flux) const;
@@ -35,7 +38,28 @@ uint32_t threshold_of(double F);
 int inversion_thresholds(float lam, uint32_t *z, int cap);
 void ptrs_constants(float lam, PtrsRec &r);
 void stirlerr_table(float out[16]);
-void build_set_tables(const Model &m, const pcmd_params &p, std::vector<uint8_t> &buf,
-                      SetDesc &d, SetStats &st);
+// Group records, transformed-rejection records and tail thresholds of a range of groups.
+struct Part {
+    std::vector<uint8_t> grp;
+    std::vector<PtrsRec> ptrs;
+    std::vector<uint32_t> tail;
+};
+
+// Host form of one model's device table.
+struct SetTables {
+    std::vector<float> lam_h[2], flux;
+    std::vector<SlowRec> slow[2];
+    std::vector<Part> parts[2];
+    int n_parts = 1;
+    uint32_t G = 0, rec = 0;
+    size_t tail_total = 0;
+    size_t bytes = 0;       // size of the emitted table
+    SetDesc d;              // offsets relative to the table start
+    SetStats st;
+};
+
+void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool parallel);
+void emit_set_tables(const SetTables &t, uint8_t *dst);
+void parallel_for(int n, const std::function<void(int)> &f);
 
 }  // namespace pcmd

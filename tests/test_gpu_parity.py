@@ -51,7 +51,10 @@ def test_tables_match_oracle(name):
     lam, flux, z0 = s.tables(w.params[0])
     lam_o, flux_o, _ = O.tables(w)
     assert np.array_equal(lam, lam_o)                       # FP32 means bit-exact
-    assert np.array_equal(flux, flux_o.astype(np.float32))  # FP32 rounding of the FP64 fluxes
+    # FP32 rounding of the FP64 fluxes; the library applies distance as one factor, so the FP64
+    # values may differ in the last bit and the FP32 table by at most one unit in the last place
+    f32 = flux_o.astype(np.float32)
+    assert np.all(np.abs(flux.view(np.int32) - f32.view(np.int32)) <= 1)
     rng = np.random.default_rng(0)
     for h in range(2):
         idx = np.nonzero((lam[h] > 0) & (lam[h] < 10))[0]
