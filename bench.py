@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", type=int, default=1, help="also time the batched path")
+    ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     return ap.parse_args()
 
 
@@ -221,6 +222,13 @@ def run_gb300(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     base_id = rank * 10_000_000
 
+    from paper_1904_00011_gb300 import autotune
+    if args.launch:
+        b_, s_, c_ = (int(v) for v in args.launch.split(","))
+        sim.set_launch(b_, s_, c_)
+        tuned = {"block": b_, "split": s_, "chunk": c_, "sweep": None}
+    else:
+        tuned = autotune.tune(sim, w.params, [n], use_cache=False)
     # a sampler-like sequence of parameter points: small seeded steps around the mock's values
     rng = np.random.default_rng(1234 + rank)
     p0 = w.params[0]
@@ -302,7 +310,8 @@ def run_gb300(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n_im": n, "points": w.iso.n_points,
                    "draw_entries_per_pixel": n_inv + n_ptrs, "ptrs_entries_per_pixel": n_ptrs,
                    "l2": "flushed between timed steps (256 MB write outside the timed interval)",
-                   "launch": {"block": 256, "split": 4, "chunk": 64}},
+                   "launch": {k: tuned[k] for k in ("block", "split", "chunk")},
+                   "autotune_sweep_ms": tuned.get("sweep")},
         "loglike_evals_per_s": evals,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "draw_kernel<2,false,IMAGE>",
@@ -340,6 +349,11 @@ def run_batched(sim_plain, P, W, torch):
     torch.cuda.synchronize()
     mock = h[0].clone()
     mom = m[0].cpu().numpy().copy()
+    from paper_1904_00011_gb300 import autotune
+    tuned = autotune.tune(sim, w.params, w.n_ims, fused=True, reps=1, use_cache=False,
+                          candidates=[(256, 4, 64), (256, 2, 64), (256, 1, 64), (256, 8, 64),
+                                      (128, 1, 64), (128, 2, 64)],
+                          mock=(mock, mom, 256 * 256, W.LL_POISSON))
     for i in range(2):
         sim.evaluate(w.params, w.n_ims, mock, mom, 256 * 256, W.LL_POISSON, first_set_id=i * 1000)
     torch.cuda.synchronize()
@@ -357,7 +371,8 @@ def run_batched(sim_plain, P, W, torch):
     return {"workload": "512 sets, images 128..512 (step 16), log10 Npix U[1,6], dmod U[22,26], "
                         "log E(B-V) U[-1,0], 200-point isochrone, Poisson likelihood",
             "evals_per_s": w.n_sets / step, "model_pixels_per_s": pix / step, "ms_per_batch": 1e3 * step,
-            "graph_ms_per_batch": kt["graph"][0] / max(1, kt["graph"][1])}
+            "graph_ms_per_batch": kt["graph"][0] / max(1, kt["graph"][1]),
+            "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
 
 
 def main():

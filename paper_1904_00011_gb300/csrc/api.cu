@@ -274,6 +274,10 @@ static DrawArgs base_draw_args(pcmd_ctx *ctx) {
     a.n_items = (uint32_t)ctx->item_list.size();
     a.queue = ctx->queue.as<uint32_t>();
     a.seed = ctx->cfg.seed;
+    for (int r = 0; r < 10; ++r) {
+        a.rk0[r] = (uint32_t)ctx->cfg.seed + (uint32_t)r * 0x9E3779B9u;
+        a.rk1[r] = (uint32_t)(ctx->cfg.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
     a.err = ctx->err.as<uint32_t>();
     a.chunk = ctx->chunk;
     a.split = ctx->split;

@@ -11,7 +11,7 @@ namespace pcmd {
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011): 10 rounds of two 32x32->64 multiplies
 // with the Weyl key schedule.  Counter (pixel, index, set, tag), key = 64-bit seed.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+__host__ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -27,6 +27,128 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
         k1 += 0xBB67AE85u;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+// Philox of counters (c0, c1 = varying index, c2, c3) with c0, c2, c3 and the key fixed: the
+// parts of rounds 1-3 that do not depend on c1 are computed once (PhiloxPrefix), leaving one
+// XOR in round 1, one multiply in rounds 2 and 3 and seven full rounds per call.
+struct PhiloxPrefix {
+    uint32_t x0;        // round 1: hi(M1 c2) ^ k0                   (c1 enters by XOR)
+    uint32_t n3;        // round 1: lo(M0 c0)
+    uint32_t m0, m1;    // round 2 outputs 0 and 1 (independent of c1)
+    uint32_t hp0, o3;   // round 3: hi and lo of M0 m0
+    uint32_t k0, k1;
+};
+
+__host__ __device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t c0, uint32_t c2, uint32_t c3,
+                                                             uint32_t k0, uint32_t k1) {
+    PhiloxPrefix f;
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    f.x0 = (uint32_t)(p1 >> 32) ^ k0;
+    const uint32_t n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    f.n3 = (uint32_t)p0;
+    const uint64_t q1 = (uint64_t)0xCD9E8D57u * (uint64_t)n2;
+    f.m0 = (uint32_t)(q1 >> 32) ^ n1 ^ (k0 + 0x9E3779B9u);
+    f.m1 = (uint32_t)q1;
+    const uint64_t r0 = (uint64_t)0xD2511F53u * (uint64_t)f.m0;
+    f.hp0 = (uint32_t)(r0 >> 32);
+    f.o3 = (uint32_t)r0;
+    f.k0 = k0;
+    f.k1 = k1;
+    return f;
+}
+
+__host__ __device__ __forceinline__ uint4 philox_from_prefix(const PhiloxPrefix &f, uint32_t c1) {
+    const uint32_t n0 = f.x0 ^ c1;
+    const uint64_t q0 = (uint64_t)0xD2511F53u * (uint64_t)n0;
+    const uint32_t m2 = (uint32_t)(q0 >> 32) ^ f.n3 ^ (f.k1 + 0xBB67AE85u);
+    const uint32_t m3 = (uint32_t)q0;
+    const uint64_t r1 = (uint64_t)0xCD9E8D57u * (uint64_t)m2;
+    uint32_t c0 = (uint32_t)(r1 >> 32) ^ f.m1 ^ (f.k0 + 2u * 0x9E3779B9u);
+    uint32_t cc1 = (uint32_t)r1;
+    uint32_t c2 = f.hp0 ^ m3 ^ (f.k1 + 2u * 0xBB67AE85u);
+    uint32_t c3 = f.o3;
+    uint32_t k0 = f.k0 + 3u * 0x9E3779B9u, k1 = f.k1 + 3u * 0xBB67AE85u;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        const uint32_t a0 = (uint32_t)(p1 >> 32) ^ cc1 ^ k0;
+        const uint32_t a2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        cc1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = a0;
+        c2 = a2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, cc1, c2, c3);
+}
+
+// Full Philox4x32-10 with the round keys read from arrays.
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t *rk0, const uint32_t *rk1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// The same with the ten round keys of each key word read from arrays (kernel parameters:
+// constant-bank operands of the XORs, nothing recomputed per call).
+__device__ __forceinline__ PhiloxPrefix philox_prefix_rk(uint32_t c0, uint32_t c2, uint32_t c3,
+                                                         const uint32_t *rk0, const uint32_t *rk1) {
+    PhiloxPrefix f;
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    f.x0 = (uint32_t)(p1 >> 32) ^ rk0[0];
+    const uint32_t n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[0];
+    f.n3 = (uint32_t)p0;
+    const uint64_t q1 = (uint64_t)0xCD9E8D57u * (uint64_t)n2;
+    f.m0 = (uint32_t)(q1 >> 32) ^ n1 ^ rk0[1];
+    f.m1 = (uint32_t)q1;
+    const uint64_t r0 = (uint64_t)0xD2511F53u * (uint64_t)f.m0;
+    f.hp0 = (uint32_t)(r0 >> 32);
+    f.o3 = (uint32_t)r0;
+    f.k0 = rk0[0];
+    f.k1 = rk1[0];
+    return f;
+}
+
+__device__ __forceinline__ uint4 philox_from_prefix_rk(const PhiloxPrefix &f, uint32_t c1,
+                                                       const uint32_t *rk0, const uint32_t *rk1) {
+    const uint32_t n0 = f.x0 ^ c1;
+    const uint64_t q0 = (uint64_t)0xD2511F53u * (uint64_t)n0;
+    const uint32_t m2 = (uint32_t)(q0 >> 32) ^ f.n3 ^ rk1[1];
+    const uint32_t m3 = (uint32_t)q0;
+    const uint64_t r1 = (uint64_t)0xCD9E8D57u * (uint64_t)m2;
+    uint32_t c0 = (uint32_t)(r1 >> 32) ^ f.m1 ^ rk0[2];
+    uint32_t cc1 = (uint32_t)r1;
+    uint32_t c2 = f.hp0 ^ m3 ^ rk1[2];
+    uint32_t c3 = f.o3;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        const uint32_t a0 = (uint32_t)(p1 >> 32) ^ cc1 ^ rk0[r];
+        const uint32_t a2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        cc1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = a0;
+        c2 = a2;
+    }
+    return make_uint4(c0, cc1, c2, c3);
 }
 
 __device__ __forceinline__ uint32_t rng_tag(uint32_t kind, uint32_t half, uint32_t sub) {

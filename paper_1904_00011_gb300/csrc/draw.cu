@@ -54,11 +54,11 @@ __device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
 // Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Attempt `at` uses words
 // 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).
 __device__ __noinline__ uint32_t ptrs_draw(const PtrsRec &r, uint32_t pix, uint32_t set,
-                                           uint32_t half, uint32_t k0, uint32_t k1,
-                                           uint32_t *err) {
+                                           uint32_t half, const uint32_t *rk0,
+                                           const uint32_t *rk1, uint32_t *err) {
     uint4 w = make_uint4(0, 0, 0, 0);
     for (uint32_t at = 0; at < kPtrsMaxAttempts; ++at) {
-        if ((at & 1u) == 0u) w = philox(pix, r.i, set, rng_tag(kKindPtrs, half, at >> 1), k0, k1);
+        if ((at & 1u) == 0u) w = philox_rk(pix, r.i, set, rng_tag(kKindPtrs, half, at >> 1), rk0, rk1);
         const uint32_t wu = (at & 1u) ? w.z : w.x;
         const uint32_t wv = (at & 1u) ? w.w : w.y;
         const float U = __fsub_rn(uniform_of(wu), 0.5f);
@@ -160,7 +160,7 @@ __device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic
             n = 1u;
         } else {
             const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
-            const uint4 wlo = philox(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), k0, k1);
+            const uint4 wlo = philox_rk(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
             const uint32_t x = (hi << 16) | slot16(wlo, j);
             const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + (gid * 8u + j));
             if (x <= sr.x) {
@@ -186,36 +186,38 @@ __device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic
     }
 }
 
-// One staged chunk of groups: the HI call of every (pixel, group), a compare per slot, and the
-// rare maybe-hits pushed to the thread's queue, drained warp-wide when any lane is nearly full
-// and at the end of the chunk (instead of a warp-divergent branch per group).
+// One staged chunk of groups: the HI call of every (pixel, group) from the pixel's Philox
+// prefix, one compare per slot OR-ed into "any maybe-hit", and the rare maybe-hits pushed to the
+// thread's queue; a thread drains its own queue when it is nearly full and at the chunk's end.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
-                                              const uint8_t *cb, uint32_t cnt, int sidx,
-                                              uint32_t *queue, Acc<B, KAHAN> &acc, uint32_t k0,
-                                              uint32_t k1) {
+                                              const PhiloxPrefix &pf, const uint8_t *cb,
+                                              uint32_t cnt, int sidx, uint32_t *queue,
+                                              Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
     constexpr uint32_t rec = group_rec_bytes(B);
     int qn = 0;
+#pragma unroll 2
     for (uint32_t g = (uint32_t)sidx; g < cnt; g += (uint32_t)a.split) {
         const uint8_t *r = cb + g * rec;
         const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
         const uint4 za = *reinterpret_cast<const uint4 *>(r + kRecZs);
         const uint4 zb = *reinterpret_cast<const uint4 *>(r + kRecZs + 16);
-        const uint4 w = philox(ic.pix, gid, ic.set, rng_tag(kKindHi, H, 0), k0, k1);
+        const uint4 w = philox_from_prefix_rk(pf, gid, a.rk0, a.rk1);
         uint32_t m = maybe_mask(w, za, zb);
-        if (!ic.active) m = 0u;
-        while (m) {
-            const uint32_t j = (uint32_t)(__ffs(m) - 1);
-            m &= m - 1u;
-            queue[qn * blockDim.x + threadIdx.x] = (g << 19) | (j << 16) | slot16(w, j);
-            ++qn;
-        }
-        if (__any_sync(0xffffffffu, qn > kQueueCap - 8)) {
-            drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
-            qn = 0;
+        if (m) {
+            do {
+                const uint32_t j = (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                queue[qn * blockDim.x + threadIdx.x] = (g << 19) | (j << 16) | slot16(w, j);
+                ++qn;
+            } while (m);
+            if (qn > kQueueCap - 8) {
+                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
+                qn = 0;
+            }
         }
     }
-    if (__any_sync(0xffffffffu, qn > 0)) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
+    if (qn) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
 }
 
 template <int B, bool KAHAN, int MODE, int H>
@@ -231,7 +233,7 @@ __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &i
         dst[1] = __ldg(src + 1);
         dst[2] = __ldg(src + 2);
         if (!ic.active) continue;
-        const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, k0, k1, a.err);
+        const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
         if (n) {
             acc.template add<H>((float)n, rec.flux);
             if (MODE == kModeCounts) {
@@ -315,6 +317,9 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
         ic.tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
         Acc<B, KAHAN> acc;
         acc.init();
+        const PhiloxPrefix pf[2] = {
+            philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 0, 0), a.rk0, a.rk1),
+            philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 1, 0), a.rk0, a.rk1)};
 
         // ---- inversion points, streamed through shared memory chunk by chunk ----
         const uint32_t ng0 = d.n_grp[0], ng1 = d.n_grp[1];
@@ -347,8 +352,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             const uint32_t first = (h ? c - nc0 : c) * chunk;
             const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
             const uint8_t *cb = bufs + b * chunk * rec;
-            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, cb, cnt, sidx, queue, acc, k0, k1);
-            else process_chunk<B, KAHAN, MODE, 1>(a, ic, cb, cnt, sidx, queue, acc, k0, k1);
+            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, pf[0], cb, cnt, sidx, queue, acc, k0, k1);
+            else process_chunk<B, KAHAN, MODE, 1>(a, ic, pf[1], cb, cnt, sidx, queue, acc, k0, k1);
             __syncthreads();
         }
 

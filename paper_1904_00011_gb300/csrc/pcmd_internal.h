@@ -80,6 +80,7 @@ struct DrawArgs {
     uint32_t n_items;
     uint32_t *queue;            // persistent work counter (nullptr = one item per CTA)
     uint64_t seed;
+    uint32_t rk0[10], rk1[10];  // Philox round keys: seed words + r * Weyl constants
     float *image;               // raw images (IMAGE mode)
     uint32_t *counts;           // COUNTS mode output [n_pix][2][P]
     uint32_t count_pix0, count_npix, n_points;
