@@ -200,6 +200,51 @@ pcmd_status pcmd_bin_mags(pcmd_ctx *ctx, const float *d_mag, const float *d_colo
                           const uint8_t *d_valid, uint32_t n, uint32_t *d_hess,
                           uint32_t *d_counters, double *d_moments);
 
+/* --------------------------------------------------------------------------------------- */
+/* Allocation-free Hess stage.                                                              */
+/* --------------------------------------------------------------------------------------- */
+
+/* Largest image edge pcmd_hess_noalloc accepts. */
+#define PCMD_NOALLOC_MAX_IM 8192
+
+/* Pixel-stage settings for pcmd_hess_noalloc (host struct, read during the call). */
+typedef struct {
+    int n_bands;                       /* 2..PCMD_MAX_BANDS; band 0 = magnitude axis */
+    double exptime[PCMD_MAX_BANDS];    /* seconds */
+    double zeropoint[PCMD_MAX_BANDS];  /* magnitude giving 1 e-/s */
+    double sky[PCMD_MAX_BANDS];        /* sky electrons per pixel */
+    int noise;                         /* nonzero: add sky + photon noise */
+    uint64_t seed;                     /* Philox key of the noise draws */
+    uint32_t set_id;                   /* RNG set id of the image */
+    const float *psf;                  /* HOST [n_bands][psf_size][psf_size] or NULL = no PSF */
+    int psf_size;                      /* odd, <= 25 */
+    int hess_nx, hess_ny;              /* bins in colour and magnitude (nx * ny <= 40000) */
+    double hess_c_lo, hess_m_lo, hess_width;
+} pcmd_pixel_config;
+
+/* The paper has no counterpart: this entry point exists for callers that may not allocate GPU
+ * memory -- for example code running inside a host application whose memory pool already owns
+ * the whole device, or a latency-sensitive loop where cudaMalloc / cudaFree would synchronise the
+ * device and stall other streams.  It does what pcmd_hess does for one image (periodic PSF
+ * convolution, sky and photon noise, magnitudes, Hess diagram, moments) without a context and
+ * without allocating: its working memory is one fixed array of about 34 KB that the library keeps
+ * on every device it runs on until the process exits.
+ *  cfg        pixel-stage settings (host)
+ *  d_image    [n_bands][n_im][n_im] raw fluxes (device, e.g. from pcmd_simulate)
+ *  n_im       image edge, 1..PCMD_NOALLOC_MAX_IM; larger images return PCMD_ERR_ARG
+ *  d_hess     [hess_ny][hess_nx] uint32 output (device, cleared by the call)
+ *  d_moments  [3] double output: sum of colour, sum of magnitude, valid pixels (device)
+ *  d_counters [2] uint32 output: valid pixels outside the grid, invalid pixels (device)
+ *  stream     cudaStream_t to run on (NULL = legacy default stream)
+ * Results equal pcmd_hess's for the same image, settings and set id.  Asynchronous.
+ * The first call on each device looks up the array's device address (make that first call
+ * before capturing a stream).  All calls on a device share the array: calls that overlap on the
+ * GPU (different streams without ordering between them) race and corrupt each other's moments;
+ * order them on one stream or with events. */
+pcmd_status pcmd_hess_noalloc(const pcmd_pixel_config *cfg, const float *d_image, int n_im,
+                              uint32_t *d_hess, double *d_moments, uint32_t *d_counters,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

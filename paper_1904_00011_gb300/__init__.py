@@ -60,6 +60,15 @@ class pcmd_params(ctypes.Structure):
                 ("dust_sigma", ctypes.c_double), ("dmod", ctypes.c_double)]
 
 
+class pcmd_pixel_config(ctypes.Structure):
+    _fields_ = [("n_bands", ctypes.c_int), ("exptime", ctypes.c_double * PCMD_MAX_BANDS),
+                ("zeropoint", ctypes.c_double * PCMD_MAX_BANDS), ("sky", ctypes.c_double * PCMD_MAX_BANDS),
+                ("noise", ctypes.c_int), ("seed", ctypes.c_uint64), ("set_id", ctypes.c_uint32),
+                ("psf", ctypes.POINTER(ctypes.c_float)), ("psf_size", ctypes.c_int),
+                ("hess_nx", ctypes.c_int), ("hess_ny", ctypes.c_int), ("hess_c_lo", ctypes.c_double),
+                ("hess_m_lo", ctypes.c_double), ("hess_width", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -91,10 +100,12 @@ def lib():
         L.pcmd_counts.argtypes = [vp, parp, i, u32, u32, u32, vp]
         L.pcmd_bin_mags.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
         L.pcmd_profile.argtypes = [vp, i]
+        L.pcmd_hess_noalloc.argtypes = [ctypes.POINTER(pcmd_pixel_config), vp, i, vp, vp, vp, vp]
         L.pcmd_kernel_times.argtypes = [vp, dp, ip]
         for name in ["pcmd_create", "pcmd_simulate", "pcmd_hess", "pcmd_loglike", "pcmd_evaluate",
                      "pcmd_sync", "pcmd_n_points", "pcmd_set_launch", "pcmd_get_tables",
-                     "pcmd_counts", "pcmd_bin_mags", "pcmd_profile", "pcmd_kernel_times"]:
+                     "pcmd_counts", "pcmd_bin_mags", "pcmd_profile", "pcmd_kernel_times",
+                     "pcmd_hess_noalloc"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -171,6 +182,14 @@ def pcmd_evaluate(ctx, params, n_sets, n_im, first_set_id, d_mock_hess, mock_mom
 
 def pcmd_sync(ctx) -> None:
     _check(lib().pcmd_sync(ctx), "pcmd_sync", ctx)
+
+
+def pcmd_hess_noalloc(cfg: pcmd_pixel_config, d_image, n_im: int, d_hess, d_moments, d_counters,
+                      stream=None) -> None:
+    """The Hess stage of one image without a context and without any device allocation (see
+    include/pcmd.h); all arguments are device pointers except ``cfg``."""
+    _check(lib().pcmd_hess_noalloc(ctypes.byref(cfg), d_image, n_im, d_hess, d_moments, d_counters,
+                                   stream), "pcmd_hess_noalloc")
 
 
 KERNEL_KINDS = ["draw", "hess", "finalize", "loglike", "graph", "gemm", "other", "spare"]
