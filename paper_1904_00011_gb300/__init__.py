@@ -101,11 +101,12 @@ def lib():
         L.pcmd_bin_mags.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
         L.pcmd_profile.argtypes = [vp, i]
         L.pcmd_hess_noalloc.argtypes = [ctypes.POINTER(pcmd_pixel_config), vp, i, vp, vp, vp, vp]
+        L.pcmd_gemm_bf16.argtypes = [vp, i, vp, i, vp, i, vp, vp, i, i, i, i, vp, vp]
         L.pcmd_kernel_times.argtypes = [vp, dp, ip]
         for name in ["pcmd_create", "pcmd_simulate", "pcmd_hess", "pcmd_loglike", "pcmd_evaluate",
                      "pcmd_sync", "pcmd_n_points", "pcmd_set_launch", "pcmd_get_tables",
                      "pcmd_counts", "pcmd_bin_mags", "pcmd_profile", "pcmd_kernel_times",
-                     "pcmd_hess_noalloc"]:
+                     "pcmd_hess_noalloc", "pcmd_gemm_bf16"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -190,6 +191,32 @@ def pcmd_hess_noalloc(cfg: pcmd_pixel_config, d_image, n_im: int, d_hess, d_mome
     include/pcmd.h); all arguments are device pointers except ``cfg``."""
     _check(lib().pcmd_hess_noalloc(ctypes.byref(cfg), d_image, n_im, d_hess, d_moments, d_counters,
                                    stream), "pcmd_hess_noalloc")
+
+
+PCMD_GEMM_F32, PCMD_GEMM_BIAS_F32, PCMD_GEMM_BIAS_GELU_BF16, PCMD_GEMM_BIAS_BF16 = 0, 1, 2, 3
+
+
+def pcmd_gemm_bf16(d_a, lda, d_b, ldb, d_c, ldc, d_bias, d_aux, m, n, k, epilogue, d_err,
+                   stream=None) -> None:
+    _check(lib().pcmd_gemm_bf16(d_a, lda, d_b, ldb, d_c, ldc, d_bias, d_aux, m, n, k, epilogue,
+                                d_err, stream), "pcmd_gemm_bf16")
+
+
+def gemm(a, b, bias=None, epilogue=PCMD_GEMM_F32, err=None):
+    """C = epilogue(a @ b.T) for BF16 CUDA tensors a [m, k], b [n, k] (row strides multiples of
+    8 elements); returns (C, aux)."""
+    import torch
+    m, k = a.shape
+    n = b.shape[0]
+    bf16_out = epilogue in (PCMD_GEMM_BIAS_GELU_BF16, PCMD_GEMM_BIAS_BF16)
+    c = torch.empty((m, n), dtype=torch.bfloat16 if bf16_out else torch.float32, device=a.device)
+    aux = torch.empty_like(c) if epilogue == PCMD_GEMM_BIAS_GELU_BF16 else None
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    pcmd_gemm_bf16(a.data_ptr(), a.stride(0), b.data_ptr(), b.stride(0), c.data_ptr(), c.stride(0),
+                   _ptr(bias), _ptr(aux), m, n, k, epilogue, err.data_ptr(),
+                   torch.cuda.current_stream().cuda_stream)
+    return c, aux
 
 
 KERNEL_KINDS = ["draw", "hess", "finalize", "loglike", "graph", "gemm", "other", "spare"]

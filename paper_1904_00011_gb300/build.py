@@ -15,7 +15,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["api.cu", "draw.cu", "hess.cu", "loglike.cu", "noalloc.cu", "mlp.cu"]  # missing ones skipped
+CU_SOURCES = ["api.cu", "draw.cu", "hess.cu", "loglike.cu", "noalloc.cu", "mlp.cu", "mlp_gemm.cu"]  # missing ones skipped
 CPP_SOURCES = ["tables.cpp"]
 HEADERS = ["common.cuh", "pcmd_internal.h", "tables.h", "mlp_internal.h"]
 

@@ -1,0 +1,302 @@
+// BF16 GEMM on the fifth-generation tensor cores: C = epilogue(A[M,K] . B[N,K]^T), FP32
+// accumulation in tensor memory.
+//
+// One CTA (4 warps) computes a 128 x BN tile.  Warp 0 (one lane) streams 128x64 / BNx64 K-major
+// tiles of A and B into a 4-stage shared-memory ring with TMA (128-byte swizzle); warp 1 (one lane)
+// issues tcgen05.mma (M=128, N=BN, K=16 per instruction) from shared-memory descriptors and
+// commits each stage back to the producer; warp 2 allocates the TMEM accumulator.  After the last
+// K block the four warps read their 32 TMEM lanes (rows) with tcgen05.ld, apply the epilogue and
+// store.  Every mbarrier wait is bounded in wall time; a wait that runs out latches an error and
+// the CTA still frees its tensor memory before it exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "mlp_internal.h"
+
+namespace pcmd {
+
+constexpr int kGemmBM = 128;
+constexpr int kGemmBK = 64;          // 64 BF16 = 128 bytes: one swizzle row
+constexpr int kGemmStages = 4;
+
+// ---- tcgen05 / TMA primitives (inline PTX) -------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
+// 8-row swizzle atoms 1024 bytes apart (stride byte offset), start address >> 4.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                       // leading byte offset (unused for this layout)
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;  // stride byte offset
+    d |= (uint64_t)1u << 46;                       // descriptor version
+    d |= (uint64_t)2u << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu_f(float x) {
+    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+
+template <int BN>
+struct GemmLayout {
+    static constexpr uint32_t a_bytes = kGemmBM * kGemmBK * 2;
+    static constexpr uint32_t b_bytes = BN * kGemmBK * 2;
+    static constexpr uint32_t stage_bytes = a_bytes + b_bytes;
+    static constexpr size_t smem = 1024 + kGemmStages * (size_t)stage_bytes + 256;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tm_a,
+                                                           const __grid_constant__ CUtensorMap tm_b,
+                                                           const GemmArgs g) {
+    using L = GemmLayout<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    uint8_t *tiles = base;
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + kGemmStages * L::stage_bytes);
+    uint64_t *empty = full + kGemmStages;
+    uint64_t *accum = empty + kGemmStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0u;
+        fence_mbar_init();
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, BN < 32 ? 32 : BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * BN;
+    const int nk = (g.k + kGemmBK - 1) / kGemmBK;
+    constexpr uint32_t idesc = idesc_bf16(kGemmBM, BN);
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk && !*abort_flag; ++kb) {
+            const int s = kb % kGemmStages;
+            if (kb >= kGemmStages) {
+                if (!mbar_wait(&empty[s], ((kb / kGemmStages) - 1) & 1, g.err)) {
+                    *abort_flag = 1u;
+                    break;
+                }
+            }
+            uint8_t *sa = tiles + s * L::stage_bytes;
+            uint8_t *sb = sa + L::a_bytes;
+            mbar_expect_tx(&full[s], L::stage_bytes);
+            tma_load_2d(sa, &tm_a, kb * kGemmBK, m0, &full[s]);
+            tma_load_2d(sb, &tm_b, kb * kGemmBK, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % kGemmStages;
+            if (!mbar_wait(&full[s], (kb / kGemmStages) & 1, g.err)) {
+                *abort_flag = 1u;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(tiles + s * L::stage_bytes);
+            const uint32_t sb = sa + L::a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                const uint64_t bd = smem_desc_sw128(sb + kk * 32);
+                umma_bf16(taddr, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(accum);
+        else mbar_arrive_local(accum);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+    const bool have = __all_sync(0xffffffffu, mbar_wait(accum, 0, g.err) && !*abort_flag);
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (have) {
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+            uint32_t r[16];
+            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), r);
+            const int col0 = n0 + c * 16;
+            if (row >= g.m || col0 >= g.n) continue;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            const bool full16 = col0 + 16 <= g.n;
+            if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
+                float *out = reinterpret_cast<float *>(g.c) + (size_t)row * g.ldc + col0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (EPI == kEpiBiasF32 && col0 + j < g.n) v[j] += g.bias[col0 + j];
+                }
+                if (full16 && ((g.ldc & 3) == 0)) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+                    for (int j = 0; j < 16; ++j)
+                        if (col0 + j < g.n) out[j] = v[j];
+                }
+            } else {
+                __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.c) + (size_t)row * g.ldc + col0;
+                __nv_bfloat16 *aux = EPI == kEpiBiasGeluBf16
+                                         ? reinterpret_cast<__nv_bfloat16 *>(g.aux) + (size_t)row * g.ldc + col0
+                                         : nullptr;
+                for (int j = 0; j < 16; ++j) {
+                    if (col0 + j >= g.n) break;
+                    const float z = v[j] + g.bias[col0 + j];
+                    if (EPI == kEpiBiasGeluBf16) {
+                        aux[j] = __float2bfloat16_rn(z);
+                        out[j] = __float2bfloat16_rn(gelu_f(z));
+                    } else {
+                        out[j] = __float2bfloat16_rn(z);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(taddr, BN < 32 ? 32 : BN);
+}
+
+// ---- host side --------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map of a row-major [rows][ld] matrix with `cols` valid columns, box 64 x box_rows.
+static bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int EPI>
+static cudaError_t launch_t(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g,
+                            cudaStream_t st) {
+    using L = GemmLayout<BN>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((g.n + BN - 1) / BN, (g.m + kGemmBM - 1) / kGemmBM);
+    gemm_bf16_kernel<BN, EPI><<<grid, 128, L::smem, st>>>(ta, tb, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_bf16(const void *a, int lda, const void *b, int ldb, const GemmArgs &g,
+                             int epilogue, cudaStream_t st) {
+    if (g.m <= 0 || g.n <= 0 || g.k <= 0 || (lda & 7) || (ldb & 7) || lda < g.k || ldb < g.k ||
+        ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
+        return cudaErrorInvalidValue;
+    constexpr int BN = 128;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, a, g.m, g.k, lda, kGemmBM) || !make_map(&tb, b, g.n, g.k, ldb, BN))
+        return cudaErrorInvalidValue;
+    switch (epilogue) {
+        case kEpiF32: return launch_t<BN, kEpiF32>(ta, tb, g, st);
+        case kEpiBiasF32: return launch_t<BN, kEpiBiasF32>(ta, tb, g, st);
+        case kEpiBiasGeluBf16: return launch_t<BN, kEpiBiasGeluBf16>(ta, tb, g, st);
+        case kEpiBiasBf16: return launch_t<BN, kEpiBiasBf16>(ta, tb, g, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pcmd
