@@ -38,6 +38,57 @@ pcmd_status pcmd_gemm_bf16(const void *d_a, int lda, const void *d_b, int ldb, v
                            const float *d_bias, void *d_aux, int m, int n, int k, int epilogue,
                            uint32_t *d_err, void *stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* The surrogate network: an MLP dims[0] -> dims[1] -> ... -> dims[n_layers] with GELU on the */
+/* hidden layers and a linear FP32 output, BF16 weights and activations, FP32 master weights  */
+/* and Adam.  Inputs are the raw model parameters, normalised in a kernel to [-1, 1] over the */
+/* box [in_lo, in_hi]; targets are ln(1 + m) of Hess counts m.                                 */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct pcmd_mlp pcmd_mlp;
+
+/* Create a network on the current device.  h_dims [n_layers + 1]: multiples of 8, dims[0] <= 64
+ * is the padded input width; n_in <= dims[0] raw inputs with box h_in_lo / h_in_hi [n_in];
+ * max_batch a multiple of 8.  Weights: LeCun-normal from a Mersenne twister seeded with `seed`,
+ * biases zero.  All work runs on `stream`.  *out is NULL on error. */
+pcmd_status pcmd_mlp_create(const int *h_dims, int n_layers, int n_in, const float *h_in_lo,
+                            const float *h_in_hi, int max_batch, uint64_t seed, void *stream,
+                            pcmd_mlp **out);
+void pcmd_mlp_destroy(pcmd_mlp *mlp);
+const char *pcmd_mlp_last_error(const pcmd_mlp *mlp);
+
+/* Forward pass of B rows (B a multiple of 8, <= max_batch): theta [B][n_in] FP32, on the device
+ * when on_device != 0 else on the host; d_out [B][dims[n_layers]] FP32 (may be NULL: the output
+ * stays inside the network, see pcmd_mlp_output).  Asynchronous. */
+pcmd_status pcmd_mlp_forward(pcmd_mlp *mlp, const float *theta, int on_device, int B, float *d_out);
+
+/* Device pointer of the last forward output [B][dims[n_layers]] FP32 (owned by the network). */
+const float *pcmd_mlp_output(const pcmd_mlp *mlp);
+
+/* Training targets of the next step: ln(1 + m) of the Hess counts d_hess [B][dims[n_layers]]
+ * (uint32, device), or given FP32 targets d_y.  Asynchronous. */
+pcmd_status pcmd_mlp_targets(pcmd_mlp *mlp, const uint32_t *d_hess, int B);
+pcmd_status pcmd_mlp_set_targets(pcmd_mlp *mlp, const float *d_y, int B);
+
+/* One step: forward on theta (as in pcmd_mlp_forward), loss sum (yhat - y)^2 / (2B), backward
+ * through every layer with tensor-core GEMMs, and (update != 0) an Adam step with learning rate
+ * lr (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Asynchronous. */
+pcmd_status pcmd_mlp_train_step(pcmd_mlp *mlp, const float *theta, int on_device, int B, float lr,
+                                int update);
+
+/* Loss of the last step (host); synchronises and reports a latched GEMM error. */
+pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss);
+
+/* Poisson log-likelihood (the alternative of Section 2.5) of the last forward pass's B
+ * predicted diagrams against data counts d_data_hess [dims[n_layers]]: predicted counts
+ * max(expm1(yhat), 1/2) * ratio with ratio = data pixels / model pixels.  h_ll [B]; synchronises. */
+pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double ratio,
+                             double *h_ll);
+
+/* Host copies of layer l's FP32 weights [dims[l+1]][dims[l]], bias, and the last step's gradients
+ * (any pointer may be NULL); set_layer replaces weights and bias.  Synchronous. */
+pcmd_status pcmd_mlp_get_layer(pcmd_mlp *mlp, int l, float *h_w, float *h_b, float *h_gw, float *h_gb);
+pcmd_status pcmd_mlp_set_layer(pcmd_mlp *mlp, int l, const float *h_w, const float *h_b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,53 @@
+"""Pins of the FP64 surrogate-network reference: gradients against central finite differences,
+GELU against its closed-form limits."""
+import numpy as np
+
+from oracle import mlp as M
+
+
+def _net(seed, dims):
+    rng = np.random.default_rng(seed)
+    Ws = [rng.normal(0, 1 / np.sqrt(dims[l]), size=(dims[l + 1], dims[l])) for l in range(len(dims) - 1)]
+    bs = [rng.normal(0, 0.1, size=dims[l + 1]) for l in range(len(dims) - 1)]
+    return Ws, bs
+
+
+def test_gelu_limits():
+    assert M.gelu(0.0) == 0.0
+    assert abs(M.gelu(8.0) - 8.0) < 1e-12 and abs(M.gelu(-8.0)) < 1e-12
+    assert abs(M.gelu(1.0) - 0.8413447460685429) < 1e-15      # Phi(1)
+    z = np.linspace(-4, 4, 41)
+    fd = (M.gelu(z + 1e-6) - M.gelu(z - 1e-6)) / 2e-6
+    assert np.allclose(M.gelu_grad(z), fd, atol=1e-8)
+
+
+def test_gradients_match_finite_differences():
+    dims = [5, 7, 6, 4]
+    Ws, bs = _net(1, dims)
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(9, dims[0]))
+    y = rng.normal(size=(9, dims[-1]))
+    loss, gW, gb = M.loss_and_grads(Ws, bs, x, y)
+    h = 1e-6
+    for l in range(len(Ws)):
+        for (i, j) in [(0, 0), (dims[l + 1] - 1, dims[l] - 1), (1, 2)]:
+            Wp = [w.copy() for w in Ws]
+            Wm = [w.copy() for w in Ws]
+            Wp[l][i, j] += h
+            Wm[l][i, j] -= h
+            fd = (M.loss_and_grads(Wp, bs, x, y)[0] - M.loss_and_grads(Wm, bs, x, y)[0]) / (2 * h)
+            assert abs(fd - gW[l][i, j]) < 1e-7 * max(1.0, abs(fd))
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[l][0] += h
+        bm[l][0] -= h
+        fd = (M.loss_and_grads(Ws, bp, x, y)[0] - M.loss_and_grads(Ws, bm, x, y)[0]) / (2 * h)
+        assert abs(fd - gb[l][0]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_adam_first_step_moves_by_lr():
+    w, m, v = np.ones(3), np.zeros(3), np.zeros(3)
+    g = np.array([0.5, -2.0, 1e-3])
+    w2, m2, v2 = M.adam(w, m, v, g, 1, 0.01)
+    # with bias correction the first step is lr * sign(g) (up to eps)
+    assert np.allclose(w2, w - 0.01 * np.sign(g), atol=1e-6)
