@@ -64,12 +64,19 @@ pcmd_status pcmd_mlp_forward(pcmd_mlp *mlp, const float *theta, int on_device, i
 /* Device pointer of the last forward output [B][dims[n_layers]] FP32 (owned by the network). */
 const float *pcmd_mlp_output(const pcmd_mlp *mlp);
 
-/* Training targets of the next step: ln(1 + m) of the Hess counts d_hess [B][dims[n_layers]]
- * (uint32, device), or given FP32 targets d_y.  Asynchronous. */
+/* Output and loss convention: 0 (default) = the output is ln(1 + m) trained with the squared
+ * error; 1 = the output is the log expected count trained with the Poisson deviance
+ * exp(yhat) - m yhat on the counts m (the form the Poisson likelihood needs). */
+pcmd_status pcmd_mlp_set_loss(pcmd_mlp *mlp, int poisson);
+
+/* Training targets of the next step from the Hess counts d_hess [B][dims[n_layers]] (uint32,
+ * device): ln(1 + m), or m itself under the Poisson convention; or given FP32 targets d_y.
+ * Asynchronous. */
 pcmd_status pcmd_mlp_targets(pcmd_mlp *mlp, const uint32_t *d_hess, int B);
 pcmd_status pcmd_mlp_set_targets(pcmd_mlp *mlp, const float *d_y, int B);
 
-/* One step: forward on theta (as in pcmd_mlp_forward), loss sum (yhat - y)^2 / (2B), backward
+/* One step: forward on theta (as in pcmd_mlp_forward), loss (sum (yhat - y)^2 / 2, or the Poisson
+ * deviance) / B, backward
  * through every layer with tensor-core GEMMs, and (update != 0) an Adam step with learning rate
  * lr (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Asynchronous. */
 pcmd_status pcmd_mlp_train_step(pcmd_mlp *mlp, const float *theta, int on_device, int B, float lr,
@@ -79,10 +86,12 @@ pcmd_status pcmd_mlp_train_step(pcmd_mlp *mlp, const float *theta, int on_device
 pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss);
 
 /* Poisson log-likelihood (the alternative of Section 2.5) of the last forward pass's B
- * predicted diagrams against data counts d_data_hess [dims[n_layers]]: predicted counts
- * max(expm1(yhat), 1/2) * ratio with ratio = data pixels / model pixels.  h_ll [B]; synchronises. */
-pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double ratio,
-                             double *h_ll);
+ * predicted diagrams against data counts d_data_hess [dims[n_layers]] (device): predicted counts
+ * of the network's image (exp(yhat), or expm1(yhat) under the squared-error convention) times
+ * `scale` (model pixels / network-image pixels), floored at 1/2, times `ratio` (data pixels /
+ * model pixels); sum d ln mh - mh - ln Gamma(d + 1).  h_ll [B]; synchronises. */
+pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale,
+                             double ratio, double *h_ll);
 
 /* Host copies of layer l's FP32 weights [dims[l+1]][dims[l]], bias, and the last step's gradients
  * (any pointer may be NULL); set_layer replaces weights and bias.  Synchronous. */

@@ -44,12 +44,19 @@ def forward(Ws: List[np.ndarray], bs: List[np.ndarray], x: np.ndarray):
     return a, zs, xs
 
 
-def loss_and_grads(Ws, bs, x, y) -> Tuple[float, list, list]:
+def loss_and_grads(Ws, bs, x, y, poisson: bool = False) -> Tuple[float, list, list]:
+    """Squared error sum((yhat - y)^2) / (2B), or with poisson the deviance of a log-rate output
+    against counts y: sum(exp(yhat) - y yhat) / B."""
     B = x.shape[0]
     yhat, zs, xs = forward(Ws, bs, x)
-    d = yhat - y
-    loss = 0.5 * float(np.sum(d * d)) / B
-    dz = d / B
+    if poisson:
+        r = np.exp(yhat)
+        loss = float(np.sum(r - y * yhat)) / B
+        dz = (r - y) / B
+    else:
+        d = yhat - y
+        loss = 0.5 * float(np.sum(d * d)) / B
+        dz = d / B
     gW, gb = [None] * len(Ws), [None] * len(Ws)
     for l in range(len(Ws) - 1, -1, -1):
         gW[l] = dz.T @ xs[l]

@@ -46,14 +46,16 @@ __global__ void pack_inputs_kernel(const float *theta, int B, int n_in, int ld_o
     x[(size_t)r * ld_out + c] = __float2bfloat16_rn(v);
 }
 
-__global__ void hist_to_target_kernel(const uint32_t *h, size_t n, float *y) {
+__global__ void hist_to_target_kernel(const uint32_t *h, size_t n, int poisson, float *y) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        y[i] = log1pf((float)h[i]);
+        y[i] = poisson ? (float)h[i] : log1pf((float)h[i]);
 }
 
-// dZ of the output layer: (yhat - y) / B in BF16, its transpose, and the loss sum.
+// dZ of the output layer in BF16, its transpose, and the loss sum.  Squared error:
+// l = (yhat - y)^2 / 2, dl/dyhat = yhat - y.  Poisson deviance of a log-rate output (targets are
+// counts): l = exp(yhat) - y yhat, dl/dyhat = exp(yhat) - y.  Both divided by B.
 __global__ void loss_grad_kernel(const float *yhat, const float *y, int B, int N, float inv_b,
-                                 __nv_bfloat16 *dz, __nv_bfloat16 *dzt, double *loss) {
+                                 int poisson, __nv_bfloat16 *dz, __nv_bfloat16 *dzt, double *loss) {
     __shared__ float tile[kTT][kTT + 1];
     const int n0 = blockIdx.x * kTT, b0 = blockIdx.y * kTT;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -62,9 +64,16 @@ __global__ void loss_grad_kernel(const float *yhat, const float *y, int B, int N
         const int b = b0 + j, n = n0 + tx;
         float g = 0.0f;
         if (b < B && n < N) {
-            const float d = yhat[(size_t)b * N + n] - y[(size_t)b * N + n];
-            l += 0.5 * (double)d * (double)d;
-            g = d * inv_b;
+            const float yh = yhat[(size_t)b * N + n], yt = y[(size_t)b * N + n];
+            if (poisson) {
+                const float r = expf(yh);
+                l += (double)r - (double)yt * (double)yh;
+                g = (r - yt) * inv_b;
+            } else {
+                const float d = yh - yt;
+                l += 0.5 * (double)d * (double)d;
+                g = d * inv_b;
+            }
             dz[(size_t)b * N + n] = __float2bfloat16_rn(g);
         }
         tile[j][tx] = g;
@@ -172,14 +181,16 @@ __global__ void adam_b_kernel(float *b, float *m, float *v, const float *g, int 
 }
 
 // Surrogate Poisson log-likelihood of each predicted diagram against the data (Section 2.5's
-// Poisson alternative): mh = max(expm1(yhat), 1/2) * N_d / N_m; sum d ln mh - mh - ln Gamma(d+1).
-__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double ratio,
-                                         double *ll) {
+// Poisson alternative): the predicted counts of a model image `scale` times the network's
+// image, mh = max(counts * scale, 1/2) * N_d / N_m; sum d ln mh - mh - ln Gamma(d+1).
+__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double scale,
+                                         double ratio, int poisson, double *ll) {
     __shared__ double ws[32];
     const int r = blockIdx.x;
     double acc = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double mh = fmax((double)expm1f(yhat[(size_t)r * N + i]), 0.5) * ratio;
+        const float yv = yhat[(size_t)r * N + i];
+        const double mh = fmax((double)(poisson ? expf(yv) : expm1f(yv)) * scale, 0.5) * ratio;
         const uint32_t d = data[i];
         acc -= mh;
         if (d) acc += (double)d * log(mh) - lgamma((double)d + 1.0);
@@ -230,6 +241,7 @@ struct pcmd_mlp {
     Dev<uint32_t> err;
     Dev<double> ll;
     int step = 0;
+    int poisson = 0;   // 1: log-rate output trained with the Poisson deviance on counts
     std::string err_text;
 };
 
@@ -398,7 +410,7 @@ pcmd_status pcmd_mlp_forward(pcmd_mlp *mlp, const float *theta, int on_device, i
 pcmd_status pcmd_mlp_targets(pcmd_mlp *mlp, const uint32_t *d_hess, int B) {
     if (!mlp || !d_hess || B < 1 || B > mlp->max_batch) return PCMD_ERR_ARG;
     const size_t n = (size_t)B * mlp->dims[mlp->n_layers];
-    hist_to_target_kernel<<<1024, 256, 0, mlp->st>>>(d_hess, n, mlp->target.p);
+    hist_to_target_kernel<<<1024, 256, 0, mlp->st>>>(d_hess, n, mlp->poisson, mlp->target.p);
     MCK(cudaGetLastError());
     return PCMD_OK;
 }
@@ -416,8 +428,8 @@ static pcmd_status backward_and_update(pcmd_mlp *mlp, int B, float lr, int updat
     const int dout = mlp->dims[Lc];
     MCK(cudaMemsetAsync(mlp->loss.p, 0, sizeof(double), mlp->st));
     loss_grad_kernel<<<tgrid(dout, B), dim3(kTT, 8), 0, mlp->st>>>(mlp->yhat.p, mlp->target.p, B, dout,
-                                                                   1.0f / (float)B, mlp->dz.p, mlp->dzt.p,
-                                                                   mlp->loss.p);
+                                                                   1.0f / (float)B, mlp->poisson, mlp->dz.p,
+                                                                   mlp->dzt.p, mlp->loss.p);
     MCK(cudaGetLastError());
     for (int l = Lc - 1; l >= 0; --l) {
         const int K = mlp->dims[l], N = mlp->dims[l + 1];
@@ -491,10 +503,11 @@ pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss) {
     return PCMD_OK;
 }
 
-pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double ratio, double *h_ll) {
+pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale, double ratio,
+                             double *h_ll) {
     if (!mlp || !d_data_hess || !h_ll || B < 1 || B > mlp->max_batch) return PCMD_ERR_ARG;
     surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, mlp->dims[mlp->n_layers], d_data_hess,
-                                                     ratio, mlp->ll.p);
+                                                     scale, ratio, mlp->poisson, mlp->ll.p);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(h_ll, mlp->ll.p, sizeof(double) * B, cudaMemcpyDeviceToHost, mlp->st));
     MCK(cudaStreamSynchronize(mlp->st));
@@ -526,6 +539,12 @@ pcmd_status pcmd_mlp_set_layer(pcmd_mlp *mlp, int l, const float *h_w, const flo
     adam_w_kernel<<<tgrid(K, N), dim3(kTT, 8), 0, mlp->st>>>(Ly.w.p, Ly.mw.p, Ly.vw.p, Ly.gw.p, N, K, 0.0f, 1.0f,
                                                              1.0f, 1.0f, 1.0f, 1e-8f, Ly.wb.p, Ly.wt.p);
     MCK(cudaGetLastError());
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_mlp_set_loss(pcmd_mlp *mlp, int poisson) {
+    if (!mlp || (poisson != 0 && poisson != 1)) return PCMD_ERR_ARG;
+    mlp->poisson = poisson;
     return PCMD_OK;
 }
 

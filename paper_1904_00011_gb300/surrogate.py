@@ -43,12 +43,13 @@ def _setup_types():
     L.pcmd_mlp_set_targets.argtypes = [vp, vp, i]
     L.pcmd_mlp_train_step.argtypes = [vp, vp, i, i, ctypes.c_float, i]
     L.pcmd_mlp_loss.argtypes = [vp, dp]
-    L.pcmd_mlp_loglike.argtypes = [vp, i, vp, d, dp]
+    L.pcmd_mlp_loglike.argtypes = [vp, i, vp, d, d, dp]
     L.pcmd_mlp_get_layer.argtypes = [vp, i, vp, vp, vp, vp]
+    L.pcmd_mlp_set_loss.argtypes = [vp, i]
     L.pcmd_mlp_set_layer.argtypes = [vp, i, vp, vp]
     for n in ["pcmd_mlp_create", "pcmd_mlp_forward", "pcmd_mlp_targets", "pcmd_mlp_set_targets",
               "pcmd_mlp_train_step", "pcmd_mlp_loss", "pcmd_mlp_loglike", "pcmd_mlp_get_layer",
-              "pcmd_mlp_set_layer"]:
+              "pcmd_mlp_set_layer", "pcmd_mlp_set_loss"]:
         getattr(L, n).restype = ctypes.c_int
     L._mlp_types = True
     return L
@@ -117,6 +118,10 @@ class Mlp:
         self.forward(theta, out)
         return out
 
+    def set_loss(self, poisson: bool):
+        self._chk(self.L.pcmd_mlp_set_loss(self.h, int(bool(poisson))), "pcmd_mlp_set_loss")
+        self.poisson = bool(poisson)
+
     def targets_from_hess(self, d_hess, B: int):
         self._chk(self.L.pcmd_mlp_targets(self.h, d_hess.data_ptr(), B), "pcmd_mlp_targets")
 
@@ -134,9 +139,9 @@ class Mlp:
         self._chk(self.L.pcmd_mlp_loss(self.h, ctypes.byref(v)), "pcmd_mlp_loss")
         return float(v.value)
 
-    def loglike(self, B: int, d_data_hess, ratio: float) -> np.ndarray:
+    def loglike(self, B: int, d_data_hess, scale: float, ratio: float) -> np.ndarray:
         out = np.zeros(B)
-        self._chk(self.L.pcmd_mlp_loglike(self.h, B, d_data_hess.data_ptr(), float(ratio),
+        self._chk(self.L.pcmd_mlp_loglike(self.h, B, d_data_hess.data_ptr(), float(scale), float(ratio),
                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                   "pcmd_mlp_loglike")
         return out
@@ -159,3 +164,154 @@ class Mlp:
 
 def surrogate_dims(n_out: int = 10000, hidden: int = HIDDEN, n_hidden: int = N_HIDDEN):
     return [64] + [hidden] * n_hidden + [n_out]
+
+
+class Surrogate:
+    """An MLP from the 12 free parameters of the full model to the log Hess diagram of a
+    64 x 64 image, trained on diagrams the exact simulator produces on the GPU."""
+
+    def __init__(self, n_im: int = 64, batch: int = 512, seed: int = 0, hidden: int = HIDDEN,
+                 n_hidden: int = N_HIDDEN, infer_batch: int = 4096, exact_n_im: int = 256):
+        import torch
+        from . import Simulator
+        self.torch = torch
+        self.n_im = n_im
+        self.batch = batch
+        self.box = workloads.SURROGATE_BOX.copy()
+        self.base = workloads.surrogate(n_sets=1, n_im=n_im)
+        self.sim = Simulator(self.base, max_sets=batch, max_im=n_im)
+        # the judge: the exact simulator on larger images (expected Hess counts scale with the
+        # number of pixels, so the network's 64x64 rates are rescaled, not retrained)
+        self.exact_n_im = exact_n_im
+        self.exact_sim = Simulator(self.base, max_sets=8, max_im=exact_n_im)
+        self.nbins = self.base.hess_nx * self.base.hess_ny
+        self.net = Mlp(surrogate_dims(self.nbins, hidden, n_hidden), 12, self.box[:, 0],
+                       self.box[:, 1], max_batch=max(batch, infer_batch), seed=seed)
+        # the output is the log expected count of every bin (Poisson deviance on the counts)
+        self.net.set_loss(True)
+        self.calib = {"offset": 0.0, "spread": 0.0}
+        self.rng = np.random.default_rng(seed + 17)
+        self.set_counter = 1 << 24
+        self.history = []
+
+    # -- data --------------------------------------------------------------------------------
+    def sample_theta(self, n: int, rng: Optional[np.random.Generator] = None) -> np.ndarray:
+        rng = rng or self.rng
+        u = rng.uniform(size=(n, 12))
+        return self.box[:, 0] + u * (self.box[:, 1] - self.box[:, 0])
+
+    def simulate(self, theta: np.ndarray, set_id0: Optional[int] = None):
+        """Exact Hess diagrams [n][ny][nx] (int32 CUDA tensor) of the parameter rows."""
+        n = len(theta)
+        w = workloads.surrogate_from_theta(theta, n_im=self.n_im, base=self.base)
+        if set_id0 is None:
+            set_id0 = self.set_counter
+            self.set_counter += n
+        self.sim.simulate(w.params, [self.n_im] * n, set_id0)
+        h, m, c, _ = self.sim.hess(n, [self.n_im] * n)
+        return h, m
+
+    # -- training -----------------------------------------------------------------------------
+    def train(self, n_sims: int, lr: float = 1e-3, lr_min: float = 2e-5, log_every: int = 50):
+        """Fresh simulations every step (no sample is seen twice); cosine learning-rate decay."""
+        steps = max(1, n_sims // self.batch)
+        t0 = time.perf_counter()
+        t_sim = 0.0
+        for s in range(steps):
+            theta = self.sample_theta(self.batch).astype(np.float32)
+            ts = time.perf_counter()
+            h, _ = self.simulate(theta)
+            self.torch.cuda.synchronize()
+            t_sim += time.perf_counter() - ts
+            if s == 0:
+                # start the output layer at the log mean count of every bin
+                last = self.net.n_layers - 1
+                w, _, _, _ = self.net.get_layer(last)
+                mean = h.reshape(self.batch, -1).float().mean(0).cpu().numpy()
+                self.net.set_layer(last, w * 0.1, np.log(mean + 1e-2).astype(np.float32))
+            self.net.targets_from_hess(h, self.batch)
+            a = lr_min + 0.5 * (lr - lr_min) * (1 + np.cos(np.pi * s / steps))
+            self.net.train_step(theta, a)
+            if s % log_every == 0 or s == steps - 1:
+                self.history.append((s, self.net.loss()))
+        self.torch.cuda.synchronize()
+        return {"steps": steps, "sims": steps * self.batch, "seconds": time.perf_counter() - t0,
+                "simulation_seconds": t_sim, "final_loss": self.history[-1][1]}
+
+    # -- inference -----------------------------------------------------------------------------
+    def predict(self, theta: np.ndarray):
+        """Predicted ln(1 + m) [n][nbins] as a CUDA tensor (n a multiple of 8)."""
+        return self.net.predict(np.asarray(theta, np.float32))
+
+    def loglike(self, theta: np.ndarray, d_mock_hess, mock_n_pix: float) -> np.ndarray:
+        """Surrogate Poisson log-likelihood of every parameter row against the data diagram, for
+        a model image of exact_n_im (the judge's image size)."""
+        n = len(theta)
+        pad = (-n) % 8
+        th = np.asarray(theta, np.float32)
+        if pad:
+            th = np.concatenate([th, np.repeat(th[-1:], pad, axis=0)])
+        self.net.forward(th)
+        scale = float(self.exact_n_im ** 2) / float(self.n_im ** 2)
+        ll = self.net.loglike(len(th), d_mock_hess.reshape(-1), scale, mock_n_pix / float(self.exact_n_im ** 2))
+        return ll[:n]
+
+    def exact_loglike(self, theta: np.ndarray, d_mock_hess, mock_moments, mock_n_pix: float,
+                      set_id0: Optional[int] = None) -> np.ndarray:
+        """The exact simulator's Poisson log-likelihood (the judge) on exact_n_im images."""
+        n = len(theta)
+        if set_id0 is None:
+            set_id0 = self.set_counter
+            self.set_counter += n
+        out = np.zeros(n)
+        for k in range(0, n, 8):
+            th = theta[k:k + 8]
+            w = workloads.surrogate_from_theta(th, n_im=self.exact_n_im, base=self.base)
+            out[k:k + len(th)] = self.exact_sim.evaluate(
+                w.params, [self.exact_n_im] * len(th), d_mock_hess, mock_moments, mock_n_pix,
+                workloads.LL_POISSON, first_set_id=set_id0 + k)
+        return out
+
+    def exact_mock(self, theta: np.ndarray, set_id: int = 123456789):
+        """Data diagram: one exact realisation at theta on an exact_n_im image."""
+        w = workloads.surrogate_from_theta(np.atleast_2d(theta), n_im=self.exact_n_im, base=self.base)
+        self.exact_sim.simulate(w.params, [self.exact_n_im], set_id)
+        h, m, c, _ = self.exact_sim.hess(1, [self.exact_n_im])
+        return h[0].contiguous(), m[0].cpu().numpy(), float(self.exact_n_im ** 2)
+
+    def errors(self, n_test: int = 512, seed: int = 99, d_mock=None, mock_moments=None,
+               mock_n_pix: float = 0.0):
+        """Held-out accuracy: RMS of ln(1 + m) per bin against one exact realisation, the same
+        between two exact realisations (the simulator's own noise floor), and, with a mock,
+        the log-likelihood difference surrogate - exact."""
+        t = self.torch
+        rng = np.random.default_rng(seed)
+        n_test = max(8, n_test - n_test % 8)
+        theta = self.sample_theta(n_test, rng).astype(np.float32)
+        pred = self.torch.log1p(self.torch.exp(self.predict(theta)))
+        h1, _ = self.simulate(theta, set_id0=7 << 26)
+        y1 = t.log1p(h1.reshape(n_test, -1).float())
+        h2, _ = self.simulate(theta, set_id0=9 << 26)
+        y2 = t.log1p(h2.reshape(n_test, -1).float())
+        out = {"n_test": n_test,
+               "rms_log_bin": float(((pred - y1) ** 2).mean().sqrt()),
+               "rms_log_bin_noise_floor": float(((y2 - y1) ** 2).mean().sqrt() / np.sqrt(2.0))}
+        if d_mock is not None:
+            ll_s = self.loglike(theta, d_mock, mock_n_pix)
+            ll_e = self.exact_loglike(theta, d_mock, mock_moments, mock_n_pix, set_id0=11 << 26)
+            d = ll_s - ll_e
+            off = float(np.median(ll_e - ll_s))
+            spread = float(np.percentile(np.abs(ll_e - ll_s - off), 90))
+            self.calib = {"offset": off, "spread": spread}
+            out.update({"ll_offset": off, "ll_spread_p90": spread,
+                        "ll_abs_err_median": float(np.median(np.abs(d))),
+                        "ll_abs_err_p90": float(np.percentile(np.abs(d), 90)),
+                        "ll_rel_err_median": float(np.median(np.abs(d) / np.abs(ll_e))),
+                        "ll_spearman": float(_spearman(ll_s, ll_e))})
+        return out
+
+
+def _spearman(a, b):
+    ra = np.argsort(np.argsort(a))
+    rb = np.argsort(np.argsort(b))
+    return np.corrcoef(ra, rb)[0, 1]

@@ -52,14 +52,19 @@ def test_forward_matches_fp64_reference():
     assert err < 3e-2, err
 
 
-def test_gradients_match_fp64_reference():
+@pytest.mark.parametrize("poisson", [False, True])
+def test_gradients_match_fp64_reference(poisson):
     net, Ws, bs, theta, x = _setup(seed=4)
     rng = np.random.default_rng(9)
-    y = rng.normal(size=(theta.shape[0], DIMS[-1])).astype(np.float32)
+    if poisson:
+        y = rng.poisson(1.5, size=(theta.shape[0], DIMS[-1])).astype(np.float32)
+        net.set_loss(True)
+    else:
+        y = rng.normal(size=(theta.shape[0], DIMS[-1])).astype(np.float32)
     net.set_targets(torch.from_numpy(y).cuda(), theta.shape[0])
     net.train_step(theta, lr=0.0, update=False)
     loss = net.loss()
-    ref_loss, gW, gb = M.loss_and_grads(Ws, bs, x, y.astype(np.float64))
+    ref_loss, gW, gb = M.loss_and_grads(Ws, bs, x, y.astype(np.float64), poisson)
     assert abs(loss - ref_loss) <= 3e-2 * ref_loss
     for l in range(len(DIMS) - 1):
         _, _, gw, gbb = net.get_layer(l)

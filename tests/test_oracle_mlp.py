@@ -21,13 +21,18 @@ def test_gelu_limits():
     assert np.allclose(M.gelu_grad(z), fd, atol=1e-8)
 
 
-def test_gradients_match_finite_differences():
+import pytest
+
+
+@pytest.mark.parametrize("poisson", [False, True])
+def test_gradients_match_finite_differences(poisson):
     dims = [5, 7, 6, 4]
     Ws, bs = _net(1, dims)
     rng = np.random.default_rng(2)
     x = rng.normal(size=(9, dims[0]))
-    y = rng.normal(size=(9, dims[-1]))
-    loss, gW, gb = M.loss_and_grads(Ws, bs, x, y)
+    y = rng.poisson(2.0, size=(9, dims[-1])).astype(float) if poisson else rng.normal(size=(9, dims[-1]))
+    lg = lambda W, b: M.loss_and_grads(W, b, x, y, poisson)  # noqa: E731
+    loss, gW, gb = lg(Ws, bs)
     h = 1e-6
     for l in range(len(Ws)):
         for (i, j) in [(0, 0), (dims[l + 1] - 1, dims[l] - 1), (1, 2)]:
@@ -35,13 +40,13 @@ def test_gradients_match_finite_differences():
             Wm = [w.copy() for w in Ws]
             Wp[l][i, j] += h
             Wm[l][i, j] -= h
-            fd = (M.loss_and_grads(Wp, bs, x, y)[0] - M.loss_and_grads(Wm, bs, x, y)[0]) / (2 * h)
+            fd = (lg(Wp, bs)[0] - lg(Wm, bs)[0]) / (2 * h)
             assert abs(fd - gW[l][i, j]) < 1e-7 * max(1.0, abs(fd))
         bp = [b.copy() for b in bs]
         bm = [b.copy() for b in bs]
         bp[l][0] += h
         bm[l][0] -= h
-        fd = (M.loss_and_grads(Ws, bp, x, y)[0] - M.loss_and_grads(Ws, bm, x, y)[0]) / (2 * h)
+        fd = (lg(Ws, bp)[0] - lg(Ws, bm)[0]) / (2 * h)
         assert abs(fd - gb[l][0]) < 1e-7 * max(1.0, abs(fd))
 
 
