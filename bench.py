@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", type=int, default=1, help="also time the batched path")
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
+    ap.add_argument("--surrogate-sims", type=int, default=262144,
+                    help="simulations the surrogate is trained on in the extras")
     return ap.parse_args()
 
 
@@ -285,6 +287,8 @@ def run_gb300(args, world, rank, local):
     extras = {}
     if args.extras and rank == 0:
         extras["batched"] = run_batched(sim, P, W, torch)
+        extras["large_npix"] = run_large(P, W, torch)
+        extras["surrogate"] = run_surrogate(torch, n_sims=args.surrogate_sims)
 
     if rank != 0:
         if world > 1:
@@ -297,6 +301,8 @@ def run_gb300(args, world, rank, local):
     per_launch = ops * npix
     avg_draw_s = (draw_ms / max(draw_n, 1)) / 1e3
     peak = 152 * PEAK_ISSUE_PER_SM_CLK * 2070e6 / 1e12   # Tinstr/s at the maximum SM clock
+    # (MEASURED_PEAKS.json holds copy bandwidth and cuBLAS BF16 only; the issue-slot peak is
+    # derived from the SM count and the maximum clock)
     achieved = per_launch / avg_draw_s / 1e12
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -373,6 +379,94 @@ def run_batched(sim_plain, P, W, torch):
             "evals_per_s": w.n_sets / step, "model_pixels_per_s": pix / step, "ms_per_batch": 1e3 * step,
             "graph_ms_per_batch": kt["graph"][0] / max(1, kt["graph"][1]),
             "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
+
+
+def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3):
+    """Large-Npix regime: 1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix 6,
+    transformed rejection dominant, Kahan sums; full evaluation (PSF path) per step."""
+    w = W.large(log_npix=log_npix)
+    n = w.n_im
+    sim = P.Simulator(w, max_sets=1)
+    sim.simulate(w.params, [n], 2_000_000)
+    h, m, c, _ = sim.hess(1, [n])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=1)
+    sim.profile(True)
+    t0 = time.perf_counter()
+    for i in range(reps):
+        sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=10 + i)
+    dt = (time.perf_counter() - t0) / reps
+    kt = sim.kernel_times()
+    sim.profile(False)
+    lam, _, _ = sim.tables(w.params[0])
+    inv = int(((lam > 0) & (lam < 10)).sum())
+    ptrs = int((lam >= 10).sum())
+    draw_ms = kt["draw"][0] / max(1, kt["draw"][1])
+    return {"workload": "1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
+                        "dust, 25x25 PSF, noise, Kahan sums" % log_npix,
+            "model_pixels_per_s": n * n / dt, "evals_per_s": 1.0 / dt, "ms_per_eval": 1e3 * dt,
+            "draw_ms": draw_ms, "hess_ms": kt["hess"][0] / max(1, kt["hess"][1]),
+            "entries_per_pixel": inv + ptrs, "ptrs_entries_per_pixel": ptrs,
+            "draws_per_s": (inv + ptrs) * n * n / (draw_ms / 1e3)}
+
+
+def run_surrogate(torch, n_sims: int = 262144, infer_batch: int = 4096, reps: int = 10):
+    """Surrogate: train on fresh simulations, report held-out accuracy against the exact
+    simulator, inference throughput (tensor-core GEMMs) and the nested-sampling pre-screen gain."""
+    from paper_1904_00011_gb300.surrogate import Surrogate
+    from paper_1904_00011_gb300.sampler import nested_sampling
+    S = Surrogate(batch=512, seed=0, infer_batch=infer_batch)
+    info = S.train(n_sims=n_sims)
+    d_mock, mom, npix = S.exact_mock(S.box.mean(axis=1).astype(np.float32))
+    err = S.errors(n_test=512, seed=43, d_mock=d_mock, mock_moments=mom, mock_n_pix=npix)
+    # inference: forward + likelihood of infer_batch parameter points
+    th = S.sample_theta(infer_batch, np.random.default_rng(7)).astype(np.float32)
+    th_d = torch.from_numpy(th).cuda()
+    st = torch.cuda.current_stream()
+    S.net.forward(th_d)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        S.net.forward(th_d)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        S.loglike(th, d_mock, npix)
+    ll_s = (time.perf_counter() - t0) / reps
+    dims = S.net.dims
+    flop = 2.0 * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1)) * infer_batch
+    tflops = flop / (fwd_ms / 1e3) / 1e12
+    peak = _measured_peak("bf16_tflops", 1900.0)
+    # pre-screen gain in a short nested-sampling run
+    offset, margin = err["ll_offset"], 2.0 * err["ll_spread_p90"]
+    exact = lambda t: S.exact_loglike(t, d_mock, mom, npix)  # noqa: E731
+    sur = lambda t: S.loglike(t, d_mock, npix) + offset  # noqa: E731
+    prior = lambda k, rng: S.sample_theta(k, rng).astype(np.float32)  # noqa: E731
+    plain = nested_sampling(exact, prior, n_live=32, n_iter=96, seed=3)
+    fast = nested_sampling(exact, prior, n_live=32, n_iter=96, seed=3, surrogate_ll=sur, margin=margin)
+    return {"workload": "12 parameters -> 100x100 log expected Hess counts (64x64 image, full "
+                        "physics), MLP 64(12)-4x1024 GELU-10000, BF16 weights, FP32 accumulation",
+            "train": info, "errors": err,
+            "evals_per_s": infer_batch / ll_s, "forward_ms_batch": fwd_ms, "batch": infer_batch,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "kernel": "gemm_bf16_kernel (5 layers)"},
+            "prescreen": {"exact_calls_per_replacement_plain": plain.exact_calls_per_replacement,
+                          "exact_calls_per_replacement_surrogate": fast.exact_calls_per_replacement,
+                          "gain": plain.exact_calls_per_replacement / max(1e-9, fast.exact_calls_per_replacement),
+                          "l_min_final_plain": plain.l_min_final, "l_min_final_surrogate": fast.l_min_final,
+                          "judge": "exact simulator, 256x256 images, Poisson likelihood"}}
+
+
+def _measured_peak(key: str, fallback: float) -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, ValueError, KeyError):
+        return fallback
 
 
 def main():
