@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     ap.add_argument("--surrogate-sims", type=int, default=262144,
                     help="simulations the surrogate is trained on in the extras")
+    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate"],
+                    help="run one extra section alone and print its JSON (profiling runs)")
+    ap.add_argument("--large-n-im", type=int, default=1024, help="image edge of the large-Npix line")
     return ap.parse_args()
 
 
@@ -287,7 +290,7 @@ def run_gb300(args, world, rank, local):
     extras = {}
     if args.extras and rank == 0:
         extras["batched"] = run_batched(sim, P, W, torch)
-        extras["large_npix"] = run_large(P, W, torch)
+        extras["large_npix"] = run_large(P, W, torch, n_im=args.large_n_im)
         extras["surrogate"] = run_surrogate(torch, n_sims=args.surrogate_sims)
 
     if rank != 0:
@@ -381,10 +384,10 @@ def run_batched(sim_plain, P, W, torch):
             "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
 
 
-def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3):
+def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 1024):
     """Large-Npix regime: 1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix 6,
     transformed rejection dominant, Kahan sums; full evaluation (PSF path) per step."""
-    w = W.large(log_npix=log_npix)
+    w = W.large(log_npix=log_npix, n_im=n_im)
     n = w.n_im
     sim = P.Simulator(w, max_sets=1)
     sim.simulate(w.params, [n], 2_000_000)
@@ -403,8 +406,8 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3):
     inv = int(((lam > 0) & (lam < 10)).sum())
     ptrs = int((lam >= 10).sum())
     draw_ms = kt["draw"][0] / max(1, kt["draw"][1])
-    return {"workload": "1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
-                        "dust, 25x25 PSF, noise, Kahan sums" % log_npix,
+    return {"workload": "%dx%d, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
+                        "dust, 25x25 PSF, noise, Kahan sums" % (n, n, log_npix),
             "model_pixels_per_s": n * n / dt, "evals_per_s": 1.0 / dt, "ms_per_eval": 1e3 * dt,
             "draw_ms": draw_ms, "hess_ms": kt["hess"][0] / max(1, kt["hess"][1]),
             "entries_per_pixel": inv + ptrs, "ptrs_entries_per_pixel": ptrs,
@@ -474,6 +477,21 @@ def main():
     world, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.only:
+        import torch
+        import paper_1904_00011_gb300 as P
+        from paper_1904_00011_gb300 import build as B
+        from paper_1904_00011_gb300 import workloads as W
+        B.build()
+        torch.cuda.set_device(local)
+        if args.only == "large":
+            out = run_large(P, W, torch, n_im=args.large_n_im)
+        elif args.only == "batched":
+            out = run_batched(None, P, W, torch)
+        else:
+            out = run_surrogate(torch, n_sims=args.surrogate_sims)
+        print(json.dumps({"section": args.only, **out}), flush=True)
         return
     run_gb300(args, world, rank, local)
 

@@ -221,6 +221,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         ctx->stats[s] = ctx->sets[s].st;
         for (int h = 0; h < 2; ++h) {
             d.grp_off[h] += base[s];
+            d.dense_off[h] += base[s];
             d.slow_off[h] += base[s];
             d.ptrs_off[h] += base[s];
         }

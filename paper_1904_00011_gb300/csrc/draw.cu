@@ -52,34 +52,55 @@ __device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
 }
 
 // Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Attempt `at` uses words
-// 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).
-__device__ __noinline__ uint32_t ptrs_draw(const PtrsRec &r, uint32_t pix, uint32_t set,
-                                           uint32_t half, const uint32_t *rk0,
-                                           const uint32_t *rk1, uint32_t *err) {
+// 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).  The cheap part of an attempt decides
+// the squeeze acceptance and the quick rejections; the rest takes the log-form test.
+struct PtrsTry {
+    float kf, us, V;
+    int status;   // 0 accept, 1 reject, 2 needs the log test
+};
+
+__device__ __forceinline__ PtrsTry ptrs_cheap(const PtrsRec &r, uint32_t wu, uint32_t wv) {
+    PtrsTry t;
+    const float U = __fsub_rn(uniform_of(wu), 0.5f);
+    t.V = uniform_of(wv);
+    t.us = __fsub_rn(0.5f, fabsf(U));
+    float x = __fdiv_rn(r.twoa, t.us);
+    x = __fadd_rn(x, r.b);
+    x = __fmul_rn(x, U);
+    x = __fadd_rn(x, r.lam);
+    x = __fadd_rn(x, 0.43f);
+    t.kf = floorf(x);
+    if (t.us >= 0.07f && t.V <= r.vr) t.status = 0;
+    else if (t.kf < 0.0f || (t.us < 0.013f && t.V > t.us) || t.kf > 1.0e9f) t.status = 1;
+    else t.status = 2;
+    return t;
+}
+
+__device__ __forceinline__ bool ptrs_log_accept(const PtrsRec &r, const PtrsTry &t) {
+    float q = __fmul_rn(t.us, t.us);
+    q = __fdiv_rn(r.a, q);
+    q = __fadd_rn(q, r.b);
+    float lhs = ln_series(t.V);
+    lhs = __fadd_rn(lhs, r.log_ia);
+    lhs = __fsub_rn(lhs, ln_series(q));
+    return lhs <= log_pmf_dev(t.kf, r.lam);
+}
+
+__device__ __forceinline__ uint4 ptrs_words(const PtrsRec &r, uint32_t pix, uint32_t set, uint32_t half,
+                                            uint32_t at, const uint32_t *rk0, const uint32_t *rk1) {
+    return philox_rk(pix, r.i, set, rng_tag(kKindPtrs, half, at >> 1), rk0, rk1);
+}
+
+// The attempt loop of one draw; out of line, so that the caller's registers stay its own.
+__device__ __noinline__ uint32_t ptrs_draw(const PtrsRec &r, uint32_t pix, uint32_t set, uint32_t half,
+                                           const uint32_t *rk0, const uint32_t *rk1, uint32_t *err) {
     uint4 w = make_uint4(0, 0, 0, 0);
     for (uint32_t at = 0; at < kPtrsMaxAttempts; ++at) {
-        if ((at & 1u) == 0u) w = philox_rk(pix, r.i, set, rng_tag(kKindPtrs, half, at >> 1), rk0, rk1);
-        const uint32_t wu = (at & 1u) ? w.z : w.x;
-        const uint32_t wv = (at & 1u) ? w.w : w.y;
-        const float U = __fsub_rn(uniform_of(wu), 0.5f);
-        const float V = uniform_of(wv);
-        const float us = __fsub_rn(0.5f, fabsf(U));
-        float t = __fdiv_rn(r.twoa, us);
-        t = __fadd_rn(t, r.b);
-        t = __fmul_rn(t, U);
-        t = __fadd_rn(t, r.lam);
-        t = __fadd_rn(t, 0.43f);
-        const float kf = floorf(t);
-        if (us >= 0.07f && V <= r.vr) return (uint32_t)kf;
-        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
-        if (kf > 1.0e9f) continue;
-        float q = __fmul_rn(us, us);
-        q = __fdiv_rn(r.a, q);
-        q = __fadd_rn(q, r.b);
-        float lhs = ln_series(V);
-        lhs = __fadd_rn(lhs, r.log_ia);
-        lhs = __fsub_rn(lhs, ln_series(q));
-        if (lhs <= log_pmf_dev(kf, r.lam)) return (uint32_t)kf;
+        if ((at & 1u) == 0u) w = ptrs_words(r, pix, set, half, at, rk0, rk1);
+        const PtrsTry t = ptrs_cheap(r, (at & 1u) ? w.z : w.x, (at & 1u) ? w.w : w.y);
+        if (t.status == 0) return (uint32_t)t.kf;
+        if (t.status == 1) continue;
+        if (ptrs_log_accept(r, t)) return (uint32_t)t.kf;
     }
     atomicOr(err, kErrSampler);
     return 0u;
@@ -144,41 +165,58 @@ constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
 // Resolve the queued maybe-hits of this thread: entry = g << 19 | slot << 16 | hi16, g the
 // group's index in the staged chunk.  n = 1 when hi16 is above Z_0 >> 16 and below Z_1 >> 16;
 // otherwise the LO call completes the 32-bit word and the full thresholds decide.
+// n = #{k : x > Z_k} from the slow record of a slot: Z_0, Z_1 in the record, Z_2.. in the tail
+// (saturated beyond its length).  The search starts at the record's start index k_s (near
+// lambda) and walks up or down; the count equals the linear scan's.
+__device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint4 &sr, const uint32_t *tail) {
+    if (x <= sr.x) return 0u;
+    if (x <= sr.y) return 1u;
+    const uint32_t len = sr.w & 0xFFFFu;
+    uint32_t ks = sr.w >> 16;                       // 2 <= ks <= len + 1
+    if (ks < 2u) ks = 2u;
+    auto z = [&](uint32_t k) { return k - 2u < len ? __ldg(tail + sr.z + (k - 2u)) : 0xFFFFFFFFu; };
+    uint32_t k = ks;
+    if (x > z(k)) {
+        do { ++k; } while (k - 2u < len && x > z(k));
+        return k;                                   // first k with x <= Z_k
+    }
+    while (k > 2u && x <= z(k - 1u)) --k;
+    return k;
+}
+
+// Resolve the queued maybe-hits of this thread: entry = g << 19 | slot << 16 | hi16, g the
+// group's index in the staged chunk.  n = 1 when hi16 is above Z_0 >> 16 and below Z_1 >> 16;
+// otherwise the LO call of the group completes the 32-bit word (kept for the following entries
+// of the same group) and the full thresholds decide.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic,
                                             const uint8_t *cb, const uint32_t *queue, int qn,
-                                            Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
+                                            Acc<B, KAHAN> &acc) {
     constexpr uint32_t rec = group_rec_bytes(B);
+    uint32_t lo_g = 0xFFFFFFFFu;
+    uint4 wlo = make_uint4(0, 0, 0, 0);
     for (int q = 0; q < qn; ++q) {
         const uint32_t e = queue[q * blockDim.x + threadIdx.x];
         const uint32_t g = e >> 19, j = (e >> 16) & 7u, hi = e & 0xFFFFu;
         const uint8_t *r = cb + g * rec;
         const uint32_t zc0 = *reinterpret_cast<const uint32_t *>(r + kRecZs + 4 * j) >> 16;
         const uint32_t zc1 = *reinterpret_cast<const uint16_t *>(r + kRecZc1 + 2 * j);
+        const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
         uint32_t n;
         if (hi > zc0 && hi < zc1) {
             n = 1u;
         } else {
-            const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
-            const uint4 wlo = philox_rk(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
+            if (g != lo_g) {
+                wlo = philox_rk(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
+                lo_g = g;
+            }
             const uint32_t x = (hi << 16) | slot16(wlo, j);
             const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + (gid * 8u + j));
-            if (x <= sr.x) {
-                n = 0u;
-            } else if (x <= sr.y) {
-                n = 1u;
-            } else {
-                n = 2u;
-                for (uint32_t t = 0; t < sr.w; ++t) {
-                    if (x > __ldg(ic.tail + sr.z + t)) ++n;
-                    else break;
-                }
-            }
+            n = count_from_thresholds(x, sr, ic.tail);
         }
         if (n) {
             acc.template add<H>((float)n, reinterpret_cast<const float *>(r + kRecFlux) + j * B);
             if (MODE == kModeCounts) {
-                const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
                 if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
                     a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * 8u + j] = n;
             }
@@ -193,7 +231,7 @@ template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
                                               const PhiloxPrefix &pf, const uint8_t *cb,
                                               uint32_t cnt, int sidx, uint32_t *queue,
-                                              Acc<B, KAHAN> &acc, uint32_t k0, uint32_t k1) {
+                                              Acc<B, KAHAN> &acc) {
     constexpr uint32_t rec = group_rec_bytes(B);
     int qn = 0;
 #pragma unroll 2
@@ -212,35 +250,82 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
                 ++qn;
             } while (m);
             if (qn > kQueueCap - 8) {
-                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
+                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
                 qn = 0;
             }
         }
     }
-    if (qn) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc, k0, k1);
+    if (qn) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+}
+
+// Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
+// both calls of the group are drawn up front and every slot walks its thresholds directly.
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
+                                              int sidx, Acc<B, KAHAN> &acc) {
+    constexpr uint32_t rec = group_rec_bytes(B);
+    const uint32_t nd = ic.active ? d.n_dense[H] : 0u;
+    if (nd == 0u) return;
+    const uint8_t *base = a.tables + d.dense_off[H];
+    const PhiloxPrefix ph = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
+    const PhiloxPrefix pl = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
+    for (uint32_t q = (uint32_t)sidx; q < nd; q += (uint32_t)a.split) {
+        const uint8_t *r = base + (size_t)q * rec;
+        const uint32_t gid = __ldg(reinterpret_cast<const uint32_t *>(r));
+        const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
+        const uint4 wlo = philox_from_prefix_rk(pl, gid, a.rk0, a.rk1);
+        const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * 8u;
+        const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+#pragma unroll 2
+        for (uint32_t j = 0; j < 8u; ++j) {
+            const uint32_t x = (slot16(whi, j) << 16) | slot16(wlo, j);
+            const uint4 sr = __ldg(slow + j);
+            const uint32_t n = count_from_thresholds(x, sr, ic.tail);
+            if (n) {
+                float f[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) f[b] = __ldg(fl + j * B + b);
+                acc.template add<H>((float)n, f);
+                if (MODE == kModeCounts) {
+                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * 8u + j] = n;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ PtrsRec load_ptrs(const PtrsRec *pr, uint32_t q) {
+    PtrsRec rec;
+    const uint4 *src = reinterpret_cast<const uint4 *>(pr + q);
+    uint4 *dst = reinterpret_cast<uint4 *>(&rec);
+    dst[0] = __ldg(src);
+    dst[1] = __ldg(src + 1);
+    dst[2] = __ldg(src + 2);
+    return rec;
 }
 
 template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &ic, const PtrsRec &rec,
+                                              uint32_t n, Acc<B, KAHAN> &acc) {
+    if (!n) return;
+    acc.template add<H>((float)n, rec.flux);
+    if (MODE == kModeCounts) {
+        if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+            a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
+    }
+}
+
+// Transformed-rejection points: every thread runs the attempt loop of each of its records.
+template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic,
-                                             const SetDesc &d, int sidx, Acc<B, KAHAN> &acc,
-                                             uint32_t k0, uint32_t k1) {
+                                             const SetDesc &d, int sidx, Acc<B, KAHAN> &acc) {
     const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
-    for (uint32_t q = (uint32_t)sidx; q < d.n_ptrs[H]; q += (uint32_t)a.split) {
-        PtrsRec rec;
-        const uint4 *src = reinterpret_cast<const uint4 *>(pr + q);
-        uint4 *dst = reinterpret_cast<uint4 *>(&rec);
-        dst[0] = __ldg(src);
-        dst[1] = __ldg(src + 1);
-        dst[2] = __ldg(src + 2);
-        if (!ic.active) continue;
+    const uint32_t n_rec = ic.active ? d.n_ptrs[H] : 0u;
+    for (uint32_t q = (uint32_t)sidx; q < n_rec; q += (uint32_t)a.split) {
+        const PtrsRec rec = load_ptrs(pr, q);
         const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
-        if (n) {
-            acc.template add<H>((float)n, rec.flux);
-            if (MODE == kModeCounts) {
-                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
-            }
-        }
+        ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, n, acc);
     }
 }
 
@@ -352,14 +437,16 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             const uint32_t first = (h ? c - nc0 : c) * chunk;
             const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
             const uint8_t *cb = bufs + b * chunk * rec;
-            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, pf[0], cb, cnt, sidx, queue, acc, k0, k1);
-            else process_chunk<B, KAHAN, MODE, 1>(a, ic, pf[1], cb, cnt, sidx, queue, acc, k0, k1);
+            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, pf[0], cb, cnt, sidx, queue, acc);
+            else process_chunk<B, KAHAN, MODE, 1>(a, ic, pf[1], cb, cnt, sidx, queue, acc);
             __syncthreads();
         }
 
-        // ---- transformed-rejection points (lambda >= 10) ----
-        process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc, k0, k1);
-        process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc, k0, k1);
+        // ---- dense inversion groups, then transformed-rejection points (lambda >= 10) ----
+        process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+        process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+        process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
 
         // ---- combine the splits of each pixel in a fixed order ----
         float v0[B], v1[B];

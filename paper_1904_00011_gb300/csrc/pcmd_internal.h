@@ -9,6 +9,7 @@ constexpr int kMaxBands = 4;
 constexpr int kGroup = 8;                 // isochrone points per Philox HI/LO call
 constexpr float kPtrsThreshold = 10.0f;   // inversion below, transformed rejection at/above
 constexpr int kInvCap = 64;               // inversion counts are capped at 64 (lambda < 10)
+constexpr float kDenseLam = 0.3f;         // groups with a slot at or above this are "dense"
 constexpr uint32_t kPtrsMaxAttempts = 1024u;
 
 // RNG stream kinds (tag = kind << 28 | half << 27 | sub)
@@ -32,7 +33,8 @@ constexpr uint32_t kRecZs = 16, kRecZc1 = 48, kRecFlux = 64;
 struct SlowRec {
     uint32_t z0, z1;        // n > k  <=>  x > Z_k
     uint32_t tail_off;      // index of Z_2 in the tail array
-    uint32_t tail_len;      // number of Z_k, k >= 2, below 0xFFFFFFFF
+    uint32_t tail_len;      // low 16 bits: number of Z_k, k >= 2, below 0xFFFFFFFF;
+                            // high 16 bits: start index of the device's threshold walk
 };
 
 // Transformed-rejection record (lambda >= 10), 48 bytes.
@@ -51,7 +53,8 @@ struct __align__(16) SetDesc {
     uint64_t tail_off;      // uint32 tail thresholds
     uint64_t ptrs_off[2];   // PtrsRec lists
     uint64_t img_off;       // float offset of the raw image [B][n][n]
-    uint32_t n_grp[2], n_ptrs[2];
+    uint64_t dense_off[2];  // group records of the dense inversion groups (global memory)
+    uint32_t n_grp[2], n_ptrs[2], n_dense[2];
     uint32_t n_im, set_id;
     uint32_t item_begin, n_items;   // work items (pixel tiles) of this set
     float dust_a;           // ln(10) * log_ebv

@@ -278,6 +278,7 @@ static void build_part(const Model &m, const std::vector<float> &lam, const std:
     const uint32_t rec = group_rec_bytes(B);
     uint32_t z[kInvCap];
     out.grp.clear();
+    out.dense.clear();
     out.ptrs.clear();
     out.tail.clear();
     out.grp.reserve((size_t)(g1 - g0) * rec);
@@ -285,6 +286,7 @@ static void build_part(const Model &m, const std::vector<float> &lam, const std:
         uint16_t zc0[8], zc1[8];
         float fl[8][kMaxBands];
         bool active = false;
+        float max_lam = 0.0f;
         for (uint32_t j = 0; j < 8; ++j) {
             const uint32_t i = g * 8 + j;
             zc0[j] = 0xFFFFu;
@@ -315,14 +317,22 @@ static void build_part(const Model &m, const std::vector<float> &lam, const std:
                 out.tail.push_back(z[k]);
                 sr.tail_len++;
             }
+            // search start near lambda for the device's threshold walk: 2 <= ks <= len + 1
+            const uint32_t len = sr.tail_len;
+            uint32_t ks = (uint32_t)l;
+            if (ks > len + 1u) ks = len + 1u;
+            if (ks < 2u) ks = 2u;
+            sr.tail_len = len | (ks << 16);
             zc0[j] = (uint16_t)(sr.z0 >> 16);
             zc1[j] = (uint16_t)(sr.z1 >> 16);
             active = true;
+            if (l > max_lam) max_lam = l;
         }
         if (!active) continue;
-        const size_t o = out.grp.size();
-        out.grp.resize(o + rec, 0);
-        uint8_t *r = out.grp.data() + o;
+        std::vector<uint8_t> &dst = max_lam >= kDenseLam ? out.dense : out.grp;
+        const size_t o = dst.size();
+        dst.resize(o + rec, 0);
+        uint8_t *r = dst.data() + o;
         uint32_t zs[8];
         for (uint32_t j = 0; j < 8; ++j) zs[j] = (uint32_t)zc0[j] << 16;
         std::memcpy(r, &g, 4);
@@ -364,19 +374,21 @@ void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool p
     st = SetStats();
     t.tail_total = 0;
     for (int h = 0; h < 2; ++h) {
-        size_t ng = 0, np = 0;
+        size_t ng = 0, np = 0, nd = 0;
         for (int k = 0; k < n_parts; ++k) {
             const uint32_t g0 = (uint32_t)((uint64_t)G * k / n_parts);
             const uint32_t g1 = (uint32_t)((uint64_t)G * (k + 1) / n_parts);
             const uint32_t base = (uint32_t)t.tail_total;
             if (base)
                 for (size_t i = (size_t)g0 * 8; i < (size_t)g1 * 8; ++i)
-                    if (t.slow[h][i].tail_len) t.slow[h][i].tail_off += base;
+                    if (t.slow[h][i].tail_len & 0xFFFFu) t.slow[h][i].tail_off += base;
             t.tail_total += t.parts[h][k].tail.size();
             ng += t.parts[h][k].grp.size() / rec;
+            nd += t.parts[h][k].dense.size() / rec;
             np += t.parts[h][k].ptrs.size();
         }
         st.n_inv_groups[h] = (uint32_t)ng;
+        st.n_dense[h] = (uint32_t)nd;
         st.n_ptrs[h] = (uint32_t)np;
     }
     size_t off = 0;
@@ -387,6 +399,8 @@ void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool p
     };
     for (int h = 0; h < 2; ++h) {
         d.grp_off[h] = place((size_t)st.n_inv_groups[h] * rec);
+        d.dense_off[h] = place((size_t)st.n_dense[h] * rec);
+        d.n_dense[h] = st.n_dense[h];
         d.slow_off[h] = place(t.slow[h].size() * sizeof(SlowRec));
         d.ptrs_off[h] = place((size_t)st.n_ptrs[h] * sizeof(PtrsRec));
         d.n_grp[h] = st.n_inv_groups[h];
@@ -401,6 +415,7 @@ void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool p
     d.dust_sigma = (float)p.dust_sigma;
     for (int b = 0; b < kMaxBands; ++b) d.dust_c[b] = b < B ? (float)(-0.4 * m.r_ext[b]) : 0.0f;
     st.cost_per_pixel = 60.0 * (st.n_inv_groups[0] + st.n_inv_groups[1]) +
+                        400.0 * (st.n_dense[0] + st.n_dense[1]) +
                         180.0 * (st.n_ptrs[0] + st.n_ptrs[1]) + 200.0;
 }
 
@@ -408,11 +423,13 @@ void build_set_tables(const Model &m, const pcmd_params &p, SetTables &t, bool p
 void emit_set_tables(const SetTables &t, uint8_t *dst) {
     const SetDesc &d = t.d;
     for (int h = 0; h < 2; ++h) {
-        size_t go = d.grp_off[h], po = d.ptrs_off[h];
+        size_t go = d.grp_off[h], po = d.ptrs_off[h], dd = d.dense_off[h];
         for (int k = 0; k < t.n_parts; ++k) {
             const Part &pt = t.parts[h][k];
             if (!pt.grp.empty()) std::memcpy(dst + go, pt.grp.data(), pt.grp.size());
             go += pt.grp.size();
+            if (!pt.dense.empty()) std::memcpy(dst + dd, pt.dense.data(), pt.dense.size());
+            dd += pt.dense.size();
             if (!pt.ptrs.empty()) std::memcpy(dst + po, pt.ptrs.data(), pt.ptrs.size() * sizeof(PtrsRec));
             po += pt.ptrs.size() * sizeof(PtrsRec);
         }

@@ -30,6 +30,7 @@ struct Model {
 
 struct SetStats {
     uint32_t n_inv_groups[2] = {0, 0};
+    uint32_t n_dense[2] = {0, 0};
     uint32_t n_ptrs[2] = {0, 0};
     double cost_per_pixel = 0.0;
 };
@@ -41,6 +42,7 @@ void stirlerr_table(float out[16]);
 // Group records, transformed-rejection records and tail thresholds of a range of groups.
 struct Part {
     std::vector<uint8_t> grp;
+    std::vector<uint8_t> dense;
     std::vector<PtrsRec> ptrs;
     std::vector<uint32_t> tail;
 };
