@@ -89,7 +89,9 @@ pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss);
  * predicted diagrams against data counts d_data_hess [dims[n_layers]] (device): predicted counts
  * of the network's image (exp(yhat), or expm1(yhat) under the squared-error convention) times
  * `scale` (model pixels / network-image pixels), floored at 1/2, times `ratio` (data pixels /
- * model pixels); sum d ln mh - mh - ln Gamma(d + 1).  h_ll [B]; synchronises. */
+ * model pixels); sum d ln mh - mh - ln Gamma(d + 1).  Per-bin terms in FP32, sums in FP64 (the
+ * data term in FP64 throughout).  scale and ratio must be positive (PCMD_ERR_ARG).  h_ll [B];
+ * synchronises. */
 pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale,
                              double ratio, double *h_ll);
 

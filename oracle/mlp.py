@@ -7,6 +7,7 @@ finite differences (tests/test_oracle_mlp.py).
 """
 from __future__ import annotations
 
+import math
 from typing import List, Tuple
 
 import numpy as np
@@ -73,3 +74,15 @@ def adam(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def surrogate_loglike(yhat, data, scale: float, ratio: float, poisson: bool = True) -> np.ndarray:
+    """Poisson log-likelihood of each predicted diagram (Section 2.5's alternative likelihood),
+    FP64: rate = exp(y) (log-rate output) or expm1(y) (ln(1 + m) output), mh = max(rate * scale,
+    1/2) * ratio, sum over bins of d ln mh - mh - ln Gamma(d + 1)."""
+    y = np.asarray(yhat, np.float64)
+    d = np.asarray(data, np.float64).reshape(-1)
+    rate = np.exp(y) if poisson else np.expm1(y)
+    mh = np.maximum(rate * scale, 0.5) * ratio
+    lg = np.array([math.lgamma(v + 1.0) for v in d])
+    return (d * np.log(mh) - mh).sum(axis=-1) - lg.sum()

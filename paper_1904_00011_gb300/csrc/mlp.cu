@@ -183,17 +183,14 @@ __global__ void adam_b_kernel(float *b, float *m, float *v, const float *g, int 
 // Surrogate Poisson log-likelihood of each predicted diagram against the data (Section 2.5's
 // Poisson alternative): the predicted counts of a model image `scale` times the network's
 // image, mh = max(counts * scale, 1/2) * N_d / N_m; sum d ln mh - mh - ln Gamma(d+1).
-__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double scale,
-                                         double ratio, int poisson, double *ll) {
+// The data term sum ln Gamma(d+1) does not depend on the prediction: one block computes it
+// once per call (FP64); the per-bin terms are FP32, summed in FP64.
+__global__ void data_lgamma_kernel(const uint32_t *data, int N, double *out) {
     __shared__ double ws[32];
-    const int r = blockIdx.x;
     double acc = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const float yv = yhat[(size_t)r * N + i];
-        const double mh = fmax((double)(poisson ? expf(yv) : expm1f(yv)) * scale, 0.5) * ratio;
         const uint32_t d = data[i];
-        acc -= mh;
-        if (d) acc += (double)d * log(mh) - lgamma((double)d + 1.0);
+        if (d > 1u) acc += lgamma((double)d + 1.0);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -202,7 +199,57 @@ __global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        ll[r] = t;
+        *out = t;
+    }
+}
+
+// One bin: Poisson mode reads y as ln(rate), so ln mh = max(y + ln scale, ln 1/2) + ln ratio
+// without a logarithm; the other mode reads y as ln(1 + rate).
+__device__ __forceinline__ float sll_term(float y, uint32_t d, float sc, float lsc, float ra, float lra,
+                                          int poisson) {
+    float mh, lmh;
+    if (poisson) {
+        mh = fmaxf(expf(y) * sc, 0.5f) * ra;
+        lmh = fmaxf(y + lsc, -0.69314718f) + lra;
+    } else {
+        mh = fmaxf(expm1f(y) * sc, 0.5f) * ra;
+        lmh = logf(mh);
+    }
+    return (float)d * lmh - mh;
+}
+
+__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double scale,
+                                         double ratio, int poisson, const double *lg_sum, double *ll) {
+    __shared__ double ws[32];
+    const int r = blockIdx.x;
+    const float sc = (float)scale, ra = (float)ratio;
+    const float lsc = (float)log(scale), lra = (float)log(ratio);
+    const float *y = yhat + (size_t)r * N;
+    double acc = 0.0;
+    if ((N & 3) == 0) {
+        const float4 *y4 = reinterpret_cast<const float4 *>(y);
+        const uint4 *d4 = reinterpret_cast<const uint4 *>(data);
+        for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
+            const float4 v = __ldg(y4 + i);
+            const uint4 d = __ldg(d4 + i);
+            float t = sll_term(v.x, d.x, sc, lsc, ra, lra, poisson);
+            t += sll_term(v.y, d.y, sc, lsc, ra, lra, poisson);
+            t += sll_term(v.z, d.z, sc, lsc, ra, lra, poisson);
+            t += sll_term(v.w, d.w, sc, lsc, ra, lra, poisson);
+            acc += (double)t;
+        }
+    } else {
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            acc += (double)sll_term(__ldg(y + i), __ldg(data + i), sc, lsc, ra, lra, poisson);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        ll[r] = t - *lg_sum;
     }
 }
 
@@ -327,7 +374,7 @@ pcmd_status pcmd_mlp_create(const int *h_dims, int n_layers, int n_in, const flo
     if (rc == PCMD_OK &&
         (mlp->dz.alloc((size_t)B * dmax) || mlp->dzt.alloc((size_t)B * dmax) || mlp->da.alloc((size_t)B * dmax) ||
          mlp->yhat.alloc((size_t)B * dout) || mlp->target.alloc((size_t)B * dout) ||
-         mlp->theta.alloc((size_t)B * 64) || mlp->loss.alloc(1) || mlp->err.alloc(1) || mlp->ll.alloc(B)))
+         mlp->theta.alloc((size_t)B * 64) || mlp->loss.alloc(1) || mlp->err.alloc(1) || mlp->ll.alloc((size_t)B + 1)))
         rc = PCMD_ERR_OOM;
     if (rc == PCMD_OK) {
         cudaMemset(mlp->err.p, 0, 4);
@@ -506,8 +553,12 @@ pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss) {
 pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale, double ratio,
                              double *h_ll) {
     if (!mlp || !d_data_hess || !h_ll || B < 1 || B > mlp->max_batch) return PCMD_ERR_ARG;
-    surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, mlp->dims[mlp->n_layers], d_data_hess,
-                                                     scale, ratio, mlp->poisson, mlp->ll.p);
+    if (!(scale > 0.0) || !(ratio > 0.0)) return PCMD_ERR_ARG;
+    const int N = mlp->dims[mlp->n_layers];
+    data_lgamma_kernel<<<1, 1024, 0, mlp->st>>>(d_data_hess, N, mlp->ll.p + mlp->max_batch);
+    MCK(cudaGetLastError());
+    surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, N, d_data_hess, scale, ratio, mlp->poisson,
+                                                     mlp->ll.p + mlp->max_batch, mlp->ll.p);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(h_ll, mlp->ll.p, sizeof(double) * B, cudaMemcpyDeviceToHost, mlp->st));
     MCK(cudaStreamSynchronize(mlp->st));

@@ -1,13 +1,16 @@
 // BF16 GEMM on the fifth-generation tensor cores: C = epilogue(A[M,K] . B[N,K]^T), FP32
 // accumulation in tensor memory.
 //
-// One CTA (4 warps) computes a 128 x BN tile.  Warp 0 (one lane) streams 128x64 / BNx64 K-major
-// tiles of A and B into a 4-stage shared-memory ring with TMA (128-byte swizzle); warp 1 (one lane)
-// issues tcgen05.mma (M=128, N=BN, K=16 per instruction) from shared-memory descriptors and
-// commits each stage back to the producer; warp 2 allocates the TMEM accumulator.  After the last
-// K block the four warps read their 32 TMEM lanes (rows) with tcgen05.ld, apply the epilogue and
-// store.  Every mbarrier wait is bounded in wall time; a wait that runs out latches an error and
-// the CTA still frees its tensor memory before it exits.
+// Persistent kernel, one CTA (6 warps) per SM, 128 x 256 output tiles taken in a fixed
+// stride over the tile list.  Warp 0 (one lane) streams 128x64 / 256x64 K-major tiles of A and
+// B into a 4-stage shared-memory ring with TMA (128-byte swizzle); warp 1 owns the tensor
+// memory (two 256-column FP32 accumulators) and one of its lanes issues tcgen05.mma (M=128,
+// N=256, K=16 per instruction), committing each stage back to the producer and each finished
+// tile to the epilogue; warps 2-5 read the accumulator rows of their TMEM lane quarter with
+// tcgen05.ld, apply the epilogue and store, then hand the accumulator back.  With two
+// accumulators the epilogue of one tile overlaps the main loop of the next.  Every mbarrier
+// wait is bounded in wall time; a wait that runs out latches an error, the roles drain what
+// they have in flight (TMA copies, MMAs) and the CTA frees its tensor memory before it exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -17,8 +20,10 @@
 namespace pcmd {
 
 constexpr int kGemmBM = 128;
+constexpr int kGemmBN = 256;
 constexpr int kGemmBK = 64;          // 64 BF16 = 128 bytes: one swizzle row
 constexpr int kGemmStages = 4;
+constexpr int kGemmThreads = 192;
 
 // ---- tcgen05 / TMA primitives (inline PTX) -------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
@@ -64,7 +69,7 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
         "%12, %13, %14, %15}, [%16];"
@@ -72,6 +77,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -96,27 +103,101 @@ __device__ __forceinline__ float gelu_f(float x) {
     return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
 }
 
-template <int BN>
 struct GemmLayout {
     static constexpr uint32_t a_bytes = kGemmBM * kGemmBK * 2;
-    static constexpr uint32_t b_bytes = BN * kGemmBK * 2;
+    static constexpr uint32_t b_bytes = kGemmBN * kGemmBK * 2;
     static constexpr uint32_t stage_bytes = a_bytes + b_bytes;
     static constexpr size_t smem = 1024 + kGemmStages * (size_t)stage_bytes + 256;
 };
 
-template <int BN, int EPI>
-__global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tm_a,
-                                                           const __grid_constant__ CUtensorMap tm_b,
-                                                           const GemmArgs g) {
-    using L = GemmLayout<BN>;
+// Epilogue of 16 consecutive columns [col0, col0 + 16) of one row.
+template <int EPI>
+__device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0, float (&v)[16], bool vec) {
+    if (row >= g.m || col0 >= g.n) return;
+    const bool full16 = col0 + 16 <= g.n;
+    if (EPI != kEpiF32) {
+        if (full16 && vec) {
+            const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + col0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 b = __ldg(b4 + j);
+                v[4 * j] += b.x;
+                v[4 * j + 1] += b.y;
+                v[4 * j + 2] += b.z;
+                v[4 * j + 3] += b.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (col0 + j < g.n) v[j] += __ldg(g.bias + col0 + j);
+        }
+    }
+    if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
+        float *out = reinterpret_cast<float *>(g.c) + (size_t)row * g.ldc + col0;
+        if (full16 && vec) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+            for (int j = 0; j < 16; ++j)
+                if (col0 + j < g.n) out[j] = v[j];
+        }
+        return;
+    }
+    __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.c) + (size_t)row * g.ldc + col0;
+    __nv_bfloat16 *aux = EPI == kEpiBiasGeluBf16
+                             ? reinterpret_cast<__nv_bfloat16 *>(g.aux) + (size_t)row * g.ldc + col0
+                             : nullptr;
+    if (full16 && vec) {
+        uint32_t po[8], pa[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float z0 = v[2 * j], z1 = v[2 * j + 1];
+            __nv_bfloat162 zb = __floats2bfloat162_rn(z0, z1);
+            pa[j] = *reinterpret_cast<uint32_t *>(&zb);
+            if (EPI == kEpiBiasGeluBf16) {
+                __nv_bfloat162 gb = __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
+                po[j] = *reinterpret_cast<uint32_t *>(&gb);
+            } else {
+                po[j] = pa[j];
+            }
+        }
+        uint4 *o4 = reinterpret_cast<uint4 *>(out);
+        o4[0] = make_uint4(po[0], po[1], po[2], po[3]);
+        o4[1] = make_uint4(po[4], po[5], po[6], po[7]);
+        if (EPI == kEpiBiasGeluBf16) {
+            uint4 *a4 = reinterpret_cast<uint4 *>(aux);
+            a4[0] = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+            a4[1] = make_uint4(pa[4], pa[5], pa[6], pa[7]);
+        }
+    } else {
+        for (int j = 0; j < 16; ++j) {
+            if (col0 + j >= g.n) break;
+            if (EPI == kEpiBiasGeluBf16) {
+                aux[j] = __float2bfloat16_rn(v[j]);
+                out[j] = __float2bfloat16_rn(gelu_f(v[j]));
+            } else {
+                out[j] = __float2bfloat16_rn(v[j]);
+            }
+        }
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tm_a,
+                                                                    const __grid_constant__ CUtensorMap tm_b,
+                                                                    const GemmArgs g) {
+    using L = GemmLayout;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
     uint8_t *tiles = base;
     uint64_t *full = reinterpret_cast<uint64_t *>(base + kGemmStages * L::stage_bytes);
     uint64_t *empty = full + kGemmStages;
-    uint64_t *accum = empty + kGemmStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    uint64_t *tfull = empty + kGemmStages;     // [2] accumulator ready for the epilogue
+    uint64_t *tempty = tfull + 2;              // [2] accumulator drained by the epilogue
+    uint64_t *done = tempty + 2;               // all MMAs of this CTA complete
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile uint32_t *abort_flag = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -125,112 +206,126 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_kernel(const __grid_constant
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kGemmThreads - 64);
+        }
+        mbar_init(done, 1);
         *abort_flag = 0u;
         fence_mbar_init();
     }
-    if (warp == 2) tmem_alloc(tmem_slot, BN < 32 ? 32 : BN);
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * kGemmBN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = *tmem_slot;
 
-    const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * BN;
+    const int n_m = (g.m + kGemmBM - 1) / kGemmBM;
+    const int n_n = (g.n + kGemmBN - 1) / kGemmBN;
+    const int n_tiles = n_m * n_n;
     const int nk = (g.k + kGemmBK - 1) / kGemmBK;
-    constexpr uint32_t idesc = idesc_bf16(kGemmBM, BN);
+    constexpr uint32_t idesc = idesc_bf16(kGemmBM, kGemmBN);
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk && !*abort_flag; ++kb) {
-            const int s = kb % kGemmStages;
-            if (kb >= kGemmStages) {
-                if (!mbar_wait(&empty[s], ((kb / kGemmStages) - 1) & 1, g.err)) {
-                    *abort_flag = 1u;
-                    break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            uint32_t kc = 0;   // k blocks issued by this CTA
+            for (int t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (t % n_m) * kGemmBM, n0 = (t / n_m) * kGemmBN;
+                for (int kb = 0; kb < nk; ++kb, ++kc) {
+                    const uint32_t s = kc % kGemmStages, use = kc / kGemmStages;
+                    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1u, g.err)) {
+                        *abort_flag = 1u;
+                        break;
+                    }
+                    uint8_t *sa = tiles + s * L::stage_bytes;
+                    mbar_expect_tx(&full[s], L::stage_bytes);
+                    tma_load_2d(sa, &tm_a, kb * kGemmBK, m0, &full[s]);
+                    tma_load_2d(sa + L::a_bytes, &tm_b, kb * kGemmBK, n0, &full[s]);
                 }
             }
-            uint8_t *sa = tiles + s * L::stage_bytes;
-            uint8_t *sb = sa + L::a_bytes;
-            mbar_expect_tx(&full[s], L::stage_bytes);
-            tma_load_2d(sa, &tm_a, kb * kGemmBK, m0, &full[s]);
-            tma_load_2d(sb, &tm_b, kb * kGemmBK, n0, &full[s]);
+            // drain: the copies of the last issued stages have landed before the CTA exits
+            const uint32_t first = kc > (uint32_t)kGemmStages ? kc - kGemmStages : 0u;
+            for (uint32_t c = first; c < kc; ++c)
+                mbar_wait(&full[c % kGemmStages], (c / kGemmStages) & 1u, g.err);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        bool ok = true;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % kGemmStages;
-            if (!mbar_wait(&full[s], (kb / kGemmStages) & 1, g.err)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            uint32_t kc = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
+                const uint32_t buf = it & 1u, use = it >> 1;
+                if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1u, g.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = taddr + buf * kGemmBN;
+                for (int kb = 0; kb < nk; ++kb, ++kc) {
+                    const uint32_t s = kc % kGemmStages;
+                    if (*abort_flag || !mbar_wait(&full[s], (kc / kGemmStages) & 1u, g.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tiles + s * L::stage_bytes);
+                    const uint32_t sb = sa + L::a_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < kGemmBK / 16; ++kk)
+                        umma_bf16(d, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc,
+                                  (kb | kk) != 0 ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&tfull[buf]);
+            }
+            if (!ok) *abort_flag = 1u;
+            umma_commit(done);
+            mbar_wait(done, 0u, g.err);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+        const uint32_t q = (uint32_t)(warp & 3);
+        const bool vec = ((g.ldc & 7) == 0) && ((reinterpret_cast<uintptr_t>(g.c) & 15) == 0) &&
+                         (EPI != kEpiBiasGeluBf16 || (reinterpret_cast<uintptr_t>(g.aux) & 15) == 0) &&
+                         (EPI == kEpiF32 || (reinterpret_cast<uintptr_t>(g.bias) & 15) == 0);
+        uint32_t it = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+            const uint32_t buf = it & 1u, use = it >> 1;
+            int ready = 0;
+            if (lane == 0) ready = !*abort_flag && mbar_wait(&tfull[buf], use & 1u, g.err);
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            if (!ready) {
                 *abort_flag = 1u;
-                ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(tiles + s * L::stage_bytes);
-            const uint32_t sb = sa + L::a_bytes;
+            const int m0 = (t % n_m) * kGemmBM, n0 = (t / n_m) * kGemmBN;
+            const int row = m0 + (int)(q * 32) + lane;
+            const uint32_t tbase = taddr + ((q * 32u) << 16) + buf * kGemmBN;
+#pragma unroll 1
+            for (int c = 0; c < kGemmBN / 16; c += 2) {
+                uint32_t r0[16], r1[16];
+                tmem_ld16_nowait(tbase + (uint32_t)(c * 16), r0);
+                tmem_ld16_nowait(tbase + (uint32_t)(c * 16 + 16), r1);
+                tmem_ld_wait();
+                float v[16];
 #pragma unroll
-            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
-                const uint64_t bd = smem_desc_sw128(sb + kk * 32);
-                umma_bf16(taddr, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r0[j]);
+                epilogue16<EPI>(g, row, n0 + c * 16, v, vec);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]);
+                epilogue16<EPI>(g, row, n0 + c * 16 + 16, v, vec);
             }
-            umma_commit(&empty[s]);
+            tc_fence_before();
+            mbar_arrive_local(&tempty[buf]);
         }
-        if (ok) umma_commit(accum);
-        else mbar_arrive_local(accum);
     }
     __syncwarp();
-
-    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
-    const bool have = __all_sync(0xffffffffu, mbar_wait(accum, 0, g.err) && !*abort_flag);
-    tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    if (have) {
-#pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
-            uint32_t r[16];
-            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), r);
-            const int col0 = n0 + c * 16;
-            if (row >= g.m || col0 >= g.n) continue;
-            float v[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-            const bool full16 = col0 + 16 <= g.n;
-            if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
-                float *out = reinterpret_cast<float *>(g.c) + (size_t)row * g.ldc + col0;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (EPI == kEpiBiasF32 && col0 + j < g.n) v[j] += g.bias[col0 + j];
-                }
-                if (full16 && ((g.ldc & 3) == 0)) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                } else {
-                    for (int j = 0; j < 16; ++j)
-                        if (col0 + j < g.n) out[j] = v[j];
-                }
-            } else {
-                __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.c) + (size_t)row * g.ldc + col0;
-                __nv_bfloat16 *aux = EPI == kEpiBiasGeluBf16
-                                         ? reinterpret_cast<__nv_bfloat16 *>(g.aux) + (size_t)row * g.ldc + col0
-                                         : nullptr;
-                for (int j = 0; j < 16; ++j) {
-                    if (col0 + j >= g.n) break;
-                    const float z = v[j] + g.bias[col0 + j];
-                    if (EPI == kEpiBiasGeluBf16) {
-                        aux[j] = __float2bfloat16_rn(z);
-                        out[j] = __float2bfloat16_rn(gelu_f(z));
-                    } else {
-                        out[j] = __float2bfloat16_rn(z);
-                    }
-                }
-            }
-        }
-    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) tmem_dealloc(taddr, BN < 32 ? 32 : BN);
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(taddr, 2 * kGemmBN);
 }
 
 // ---- host side --------------------------------------------------------------------------
@@ -265,19 +360,26 @@ static bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int EPI>
+template <int EPI>
 static cudaError_t launch_t(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g,
                             cudaStream_t st) {
-    using L = GemmLayout<BN>;
+    using L = GemmLayout;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>,
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((g.n + BN - 1) / BN, (g.m + kGemmBM - 1) / kGemmBM);
-    gemm_bf16_kernel<BN, EPI><<<grid, 128, L::smem, st>>>(ta, tb, g);
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
+            n_sm = 1;
+    }
+    const int tiles = ((g.m + kGemmBM - 1) / kGemmBM) * ((g.n + kGemmBN - 1) / kGemmBN);
+    gemm_bf16_kernel<EPI><<<tiles < n_sm ? tiles : n_sm, kGemmThreads, L::smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
@@ -286,15 +388,14 @@ cudaError_t launch_gemm_bf16(const void *a, int lda, const void *b, int ldb, con
     if (g.m <= 0 || g.n <= 0 || g.k <= 0 || (lda & 7) || (ldb & 7) || lda < g.k || ldb < g.k ||
         ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
         return cudaErrorInvalidValue;
-    constexpr int BN = 128;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, a, g.m, g.k, lda, kGemmBM) || !make_map(&tb, b, g.n, g.k, ldb, BN))
+    if (!make_map(&ta, a, g.m, g.k, lda, kGemmBM) || !make_map(&tb, b, g.n, g.k, ldb, kGemmBN))
         return cudaErrorInvalidValue;
     switch (epilogue) {
-        case kEpiF32: return launch_t<BN, kEpiF32>(ta, tb, g, st);
-        case kEpiBiasF32: return launch_t<BN, kEpiBiasF32>(ta, tb, g, st);
-        case kEpiBiasGeluBf16: return launch_t<BN, kEpiBiasGeluBf16>(ta, tb, g, st);
-        case kEpiBiasBf16: return launch_t<BN, kEpiBiasBf16>(ta, tb, g, st);
+        case kEpiF32: return launch_t<kEpiF32>(ta, tb, g, st);
+        case kEpiBiasF32: return launch_t<kEpiBiasF32>(ta, tb, g, st);
+        case kEpiBiasGeluBf16: return launch_t<kEpiBiasGeluBf16>(ta, tb, g, st);
+        case kEpiBiasBf16: return launch_t<kEpiBiasBf16>(ta, tb, g, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -25,9 +25,11 @@ def _rand(shape, seed, scale=1.0):
     return full.cuda()[:, :cols]
 
 
-@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (256, 256, 256), (300, 200, 100),
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (256, 256, 256), (300, 200, 100), (300, 203, 100),
                                    (37, 1024, 64), (512, 1024, 1024), (512, 10000, 1024),
-                                   (129, 136, 1000)])
+                                   (129, 136, 1000),
+                                   # several tiles per persistent CTA: accumulator reuse, ring wrap
+                                   (4096, 4000, 136), (2048, 10000, 64)])
 def test_gemm_f32_matches_torch(m, n, k):
     import paper_1904_00011_gb300 as P
     a = _rand((m, k), 1)
@@ -43,9 +45,10 @@ def test_gemm_f32_matches_torch(m, n, k):
 
 
 @pytest.mark.parametrize("epi", ["gelu", "bias_bf16", "bias_f32"])
-def test_gemm_epilogues(epi):
+@pytest.mark.parametrize("m,n,k", [(256, 384, 192), (4096, 2312, 128), (333, 1000, 64),
+                                   (100, 203, 64)])
+def test_gemm_epilogues(epi, m, n, k):
     import paper_1904_00011_gb300 as P
-    m, n, k = 256, 384, 192
     a = _rand((m, k), 3, 0.3)
     b = _rand((n, k), 4, 0.3)
     bias = torch.linspace(-1, 1, n, device="cuda", dtype=torch.float32)

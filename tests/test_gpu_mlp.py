@@ -88,3 +88,18 @@ def test_training_reduces_loss_on_smooth_target():
         if step % 50 == 0 or step == 299:
             losses.append(net.loss())
     assert losses[-1] < 0.1 * losses[0], losses
+
+
+@pytest.mark.parametrize("poisson", [True, False])
+def test_surrogate_loglike_matches_fp64_reference(poisson):
+    net, Ws, bs, theta, x = _setup(seed=6)
+    net.set_loss(poisson)
+    y = net.predict(theta)
+    rng = np.random.default_rng(11)
+    d = rng.poisson(3.0, size=DIMS[-1]).astype(np.uint32)
+    d[::7] = 0
+    d_dev = torch.from_numpy(d.astype(np.int32)).cuda()
+    scale, ratio = 16.0, 0.7
+    got = net.loglike(theta.shape[0], d_dev, scale, ratio)
+    ref = M.surrogate_loglike(y.cpu().numpy(), d, scale, ratio, poisson)
+    assert np.allclose(got, ref, rtol=1e-5, atol=1e-3), np.abs(got - ref).max()

@@ -1,6 +1,7 @@
 """Pins of the FP64 surrogate-network reference: gradients against central finite differences,
-GELU against its closed-form limits."""
+GELU against its closed-form limits, the surrogate likelihood against scipy's Poisson pmf."""
 import numpy as np
+import pytest
 
 from oracle import mlp as M
 
@@ -19,9 +20,6 @@ def test_gelu_limits():
     z = np.linspace(-4, 4, 41)
     fd = (M.gelu(z + 1e-6) - M.gelu(z - 1e-6)) / 2e-6
     assert np.allclose(M.gelu_grad(z), fd, atol=1e-8)
-
-
-import pytest
 
 
 @pytest.mark.parametrize("poisson", [False, True])
@@ -56,3 +54,20 @@ def test_adam_first_step_moves_by_lr():
     w2, m2, v2 = M.adam(w, m, v, g, 1, 0.01)
     # with bias correction the first step is lr * sign(g) (up to eps)
     assert np.allclose(w2, w - 0.01 * np.sign(g), atol=1e-6)
+
+
+@pytest.mark.parametrize("poisson", [True, False])
+def test_surrogate_loglike_is_poisson_logpmf_sum(poisson):
+    from scipy import stats
+    rng = np.random.default_rng(5)
+    y = rng.normal(0.0, 1.5, size=(3, 50))
+    d = rng.poisson(2.0, size=50)
+    scale, ratio = 3.0, 0.25
+    got = M.surrogate_loglike(y, d, scale, ratio, poisson)
+    rate = np.exp(y) if poisson else np.expm1(y)
+    mh = np.maximum(rate * scale, 0.5) * ratio
+    ref = stats.poisson.logpmf(d[None, :], mh).sum(axis=1)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-9)
+    # the floor: a rate far below 1/2 contributes as 1/2
+    low = M.surrogate_loglike(np.full((1, 50), -30.0), d, 1.0, 1.0, True)
+    assert np.isclose(low[0], stats.poisson.logpmf(d, 0.5).sum())
