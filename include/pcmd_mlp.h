@@ -32,7 +32,7 @@ enum {
  * and BF16 B (row-major [n][k], row stride ldb), FP32 accumulation on the tensor cores
  * (tcgen05.mma, operands staged by TMA).  lda, ldb: multiples of 8, >= k; A and B 16-byte
  * aligned; C row stride ldc elements; bias [n] FP32 (bias epilogues); aux like C (GELU
- * epilogue).  d_err: device uint32 error word (bit 2 set if a bounded wait ran out), may not be
+ * epilogue; NULL: the pre-activations are not stored).  d_err: device uint32 error word (bit 2 set if a bounded wait ran out), may not be
  * NULL.  Asynchronous. */
 pcmd_status pcmd_gemm_bf16(const void *d_a, int lda, const void *d_b, int ldb, void *d_c, int ldc,
                            const float *d_bias, void *d_aux, int m, int n, int k, int epilogue,
@@ -94,6 +94,16 @@ pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss);
  * synchronises. */
 pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale,
                              double ratio, double *h_ll);
+
+/* Forward pass and surrogate log-likelihood in one call: the output layer's epilogue forms
+ * the per-bin terms of pcmd_mlp_loglike straight from the tensor-memory accumulator (one
+ * partial sum per row and 64-column block, added in a fixed order), so the B x dims[n_layers]
+ * predicted diagrams are never written to memory.  Arguments as pcmd_mlp_forward and
+ * pcmd_mlp_loglike; d_data_hess 16-byte aligned; B a multiple of 8.  pcmd_mlp_output is left
+ * unchanged.  Synchronises; PCMD_ERR_TIMEOUT if a bounded wait inside a GEMM ran out. */
+pcmd_status pcmd_mlp_forward_loglike(pcmd_mlp *mlp, const float *theta, int on_device, int B,
+                                     const uint32_t *d_data_hess, double scale, double ratio,
+                                     double *h_ll);
 
 /* Host copies of layer l's FP32 weights [dims[l+1]][dims[l]], bias, and the last step's gradients
  * (any pointer may be NULL); set_layer replaces weights and bias.  Synchronous. */

@@ -202,15 +202,16 @@ def pcmd_gemm_bf16(d_a, lda, d_b, ldb, d_c, ldc, d_bias, d_aux, m, n, k, epilogu
                                 d_err, stream), "pcmd_gemm_bf16")
 
 
-def gemm(a, b, bias=None, epilogue=PCMD_GEMM_F32, err=None):
+def gemm(a, b, bias=None, epilogue=PCMD_GEMM_F32, err=None, want_aux=True):
     """C = epilogue(a @ b.T) for BF16 CUDA tensors a [m, k], b [n, k] (row strides multiples of
-    8 elements); returns (C, aux)."""
+    8 elements); returns (C, aux).  want_aux=False skips the pre-activation output of the GELU
+    epilogue."""
     import torch
     m, k = a.shape
     n = b.shape[0]
     bf16_out = epilogue in (PCMD_GEMM_BIAS_GELU_BF16, PCMD_GEMM_BIAS_BF16)
     c = torch.empty((m, n), dtype=torch.bfloat16 if bf16_out else torch.float32, device=a.device)
-    aux = torch.empty_like(c) if epilogue == PCMD_GEMM_BIAS_GELU_BF16 else None
+    aux = torch.empty_like(c) if epilogue == PCMD_GEMM_BIAS_GELU_BF16 and want_aux else None
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device=a.device)
     pcmd_gemm_bf16(a.data_ptr(), a.stride(0), b.data_ptr(), b.stride(0), c.data_ptr(), c.stride(0),

@@ -185,10 +185,10 @@ __global__ void adam_b_kernel(float *b, float *m, float *v, const float *g, int 
 // image, mh = max(counts * scale, 1/2) * N_d / N_m; sum d ln mh - mh - ln Gamma(d+1).
 // The data term sum ln Gamma(d+1) does not depend on the prediction: one block computes it
 // once per call (FP64); the per-bin terms are FP32, summed in FP64.
-__global__ void data_lgamma_kernel(const uint32_t *data, int N, double *out) {
+__global__ void data_lgamma_kernel(const uint32_t *data, int N, double *part) {
     __shared__ double ws[32];
     double acc = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const uint32_t d = data[i];
         if (d > 1u) acc += lgamma((double)d + 1.0);
     }
@@ -199,23 +199,17 @@ __global__ void data_lgamma_kernel(const uint32_t *data, int N, double *out) {
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        *out = t;
+        part[blockIdx.x] = t;
     }
 }
 
-// One bin: Poisson mode reads y as ln(rate), so ln mh = max(y + ln scale, ln 1/2) + ln ratio
-// without a logarithm; the other mode reads y as ln(1 + rate).
-__device__ __forceinline__ float sll_term(float y, uint32_t d, float sc, float lsc, float ra, float lra,
-                                          int poisson) {
-    float mh, lmh;
-    if (poisson) {
-        mh = fmaxf(expf(y) * sc, 0.5f) * ra;
-        lmh = fmaxf(y + lsc, -0.69314718f) + lra;
-    } else {
-        mh = fmaxf(expm1f(y) * sc, 0.5f) * ra;
-        lmh = logf(mh);
+// The block partials of data_lgamma_kernel added in a fixed order.
+__global__ void sum_partials_kernel(const double *part, int n, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < n; ++k) t += part[k];
+        *out = t;
     }
-    return (float)d * lmh - mh;
 }
 
 __global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double scale,
@@ -232,15 +226,15 @@ __global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_
         for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
             const float4 v = __ldg(y4 + i);
             const uint4 d = __ldg(d4 + i);
-            float t = sll_term(v.x, d.x, sc, lsc, ra, lra, poisson);
-            t += sll_term(v.y, d.y, sc, lsc, ra, lra, poisson);
-            t += sll_term(v.z, d.z, sc, lsc, ra, lra, poisson);
-            t += sll_term(v.w, d.w, sc, lsc, ra, lra, poisson);
+            float t = surrogate_ll_term(v.x, d.x, sc, lsc, ra, lra, poisson);
+            t += surrogate_ll_term(v.y, d.y, sc, lsc, ra, lra, poisson);
+            t += surrogate_ll_term(v.z, d.z, sc, lsc, ra, lra, poisson);
+            t += surrogate_ll_term(v.w, d.w, sc, lsc, ra, lra, poisson);
             acc += (double)t;
         }
     } else {
         for (int i = threadIdx.x; i < N; i += blockDim.x)
-            acc += (double)sll_term(__ldg(y + i), __ldg(data + i), sc, lsc, ra, lra, poisson);
+            acc += (double)surrogate_ll_term(__ldg(y + i), __ldg(data + i), sc, lsc, ra, lra, poisson);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -251,6 +245,20 @@ __global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
         ll[r] = t - *lg_sum;
     }
+}
+
+// Fused path: the output layer's epilogue left one partial sum per (row, 64-column block);
+// they are added in a fixed order (no atomics, so the result does not depend on scheduling).
+__global__ void ll_partials_kernel(const double *part, int ld, int B, const double *lg_sum, double *ll) {
+    // one warp per row: coalesced reads, lane-strided sums, then a fixed shuffle tree
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= B) return;
+    double t = 0.0;
+    for (int k = lane; k < ld; k += 32) t += part[(size_t)r * ld + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) ll[r] = t - *lg_sum;
 }
 
 template <class T>
@@ -287,6 +295,8 @@ struct pcmd_mlp {
     Dev<double> loss;
     Dev<uint32_t> err;
     Dev<double> ll;
+    Dev<double> ll_part;         // [max_batch][ll_ld] partial likelihood sums (fused path)
+    int ll_ld = 0;
     int step = 0;
     int poisson = 0;   // 1: log-rate output trained with the Poisson deviance on counts
     std::string err_text;
@@ -376,6 +386,9 @@ pcmd_status pcmd_mlp_create(const int *h_dims, int n_layers, int n_in, const flo
          mlp->yhat.alloc((size_t)B * dout) || mlp->target.alloc((size_t)B * dout) ||
          mlp->theta.alloc((size_t)B * 64) || mlp->loss.alloc(1) || mlp->err.alloc(1) || mlp->ll.alloc((size_t)B + 1)))
         rc = PCMD_ERR_OOM;
+    mlp->ll_ld = kGemmLlBlocks * ((dout + kGemmTileN - 1) / kGemmTileN);
+    if (rc == PCMD_OK && mlp->ll_part.alloc((size_t)B * mlp->ll_ld + 64))
+        rc = PCMD_ERR_OOM;
     if (rc == PCMD_OK) {
         cudaMemset(mlp->err.p, 0, 4);
         cudaMemset(mlp->x[0].p, 0, (size_t)B * mlp->dims[0] * 2);
@@ -402,6 +415,7 @@ void pcmd_mlp_destroy(pcmd_mlp *mlp) {
     mlp->dz.release(); mlp->dzt.release(); mlp->da.release(); mlp->yhat.release();
     mlp->target.release(); mlp->theta.release(); mlp->loss.release(); mlp->err.release();
     mlp->ll.release();
+    mlp->ll_part.release();
     delete mlp;
 }
 
@@ -424,7 +438,7 @@ static pcmd_status forward(pcmd_mlp *mlp, int B, bool train) {
         const int K = mlp->dims[l], N = mlp->dims[l + 1];
         const bool last = l == mlp->n_layers - 1;
         GemmArgs g;
-        g.aux = last ? nullptr : mlp->z[l].p;
+        g.aux = (last || !train) ? nullptr : mlp->z[l].p;   // pre-activations: backward only
         g.bias = mlp->L[l].b.p;
         g.m = B;
         g.n = N;
@@ -550,18 +564,74 @@ pcmd_status pcmd_mlp_loss(pcmd_mlp *mlp, double *h_loss) {
     return PCMD_OK;
 }
 
+// sum ln Gamma(d + 1) of the data into ll[max_batch]: block partials in ll_part (rows B..),
+// then one fixed-order sum.
+static cudaError_t data_lgamma_sum(pcmd_mlp *mlp, const uint32_t *d_data, int N) {
+    constexpr int kBlocks = 64;
+    double *part = mlp->ll_part.p + (size_t)mlp->max_batch * mlp->ll_ld;
+    data_lgamma_kernel<<<kBlocks, 256, 0, mlp->st>>>(d_data, N, part);
+    sum_partials_kernel<<<1, 32, 0, mlp->st>>>(part, kBlocks, mlp->ll.p + mlp->max_batch);
+    return cudaGetLastError();
+}
+
 pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, double scale, double ratio,
                              double *h_ll) {
     if (!mlp || !d_data_hess || !h_ll || B < 1 || B > mlp->max_batch) return PCMD_ERR_ARG;
     if (!(scale > 0.0) || !(ratio > 0.0)) return PCMD_ERR_ARG;
     const int N = mlp->dims[mlp->n_layers];
-    data_lgamma_kernel<<<1, 1024, 0, mlp->st>>>(d_data_hess, N, mlp->ll.p + mlp->max_batch);
-    MCK(cudaGetLastError());
+    MCK(data_lgamma_sum(mlp, d_data_hess, N));
     surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, N, d_data_hess, scale, ratio, mlp->poisson,
                                                      mlp->ll.p + mlp->max_batch, mlp->ll.p);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(h_ll, mlp->ll.p, sizeof(double) * B, cudaMemcpyDeviceToHost, mlp->st));
     MCK(cudaStreamSynchronize(mlp->st));
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_mlp_forward_loglike(pcmd_mlp *mlp, const float *theta, int on_device, int B,
+                                     const uint32_t *d_data_hess, double scale, double ratio, double *h_ll) {
+    if (!mlp || !theta || !d_data_hess || !h_ll || B < 1 || B > mlp->max_batch || (B & 7)) return PCMD_ERR_ARG;
+    if (!(scale > 0.0) || !(ratio > 0.0) || ((uintptr_t)d_data_hess & 15)) return PCMD_ERR_ARG;
+    pcmd_status rc = stage_inputs(mlp, theta, B, on_device != 0);
+    if (rc != PCMD_OK) return rc;
+    const int Lc = mlp->n_layers;
+    for (int l = 0; l < Lc; ++l) {
+        const int K = mlp->dims[l], N = mlp->dims[l + 1];
+        GemmArgs g;
+        g.bias = mlp->L[l].b.p;
+        g.m = B;
+        g.n = N;
+        g.k = K;
+        g.ldc = N;
+        g.err = mlp->err.p;
+        if (l < Lc - 1) {
+            g.c = mlp->x[l + 1].p;
+            MCK(launch_gemm_bf16(mlp->x[l].p, K, mlp->L[l].wb.p, K, g, kEpiBiasGeluBf16, mlp->st));
+        } else {
+            g.ll_data = d_data_hess;
+            g.ll_part = mlp->ll_part.p;
+            g.ll_ld = mlp->ll_ld;
+            g.ll_poisson = mlp->poisson;
+            g.ll_sc = (float)scale;
+            g.ll_lsc = (float)std::log(scale);
+            g.ll_ra = (float)ratio;
+            g.ll_lra = (float)std::log(ratio);
+            MCK(launch_gemm_bf16(mlp->x[l].p, K, mlp->L[l].wb.p, K, g, kEpiPoissonLL, mlp->st));
+        }
+    }
+    const int N = mlp->dims[Lc];
+    MCK(data_lgamma_sum(mlp, d_data_hess, N));
+    ll_partials_kernel<<<(B + 7) / 8, 256, 0, mlp->st>>>(mlp->ll_part.p, mlp->ll_ld, B,
+                                                             mlp->ll.p + mlp->max_batch, mlp->ll.p);
+    MCK(cudaGetLastError());
+    MCK(cudaMemcpyAsync(h_ll, mlp->ll.p, sizeof(double) * B, cudaMemcpyDeviceToHost, mlp->st));
+    MCK(cudaStreamSynchronize(mlp->st));
+    uint32_t e = 0;
+    MCK(cudaMemcpy(&e, mlp->err.p, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        mlp->err_text = "a bounded wait inside a GEMM ran out";
+        return PCMD_ERR_TIMEOUT;
+    }
     return PCMD_OK;
 }
 
@@ -609,7 +679,6 @@ pcmd_status pcmd_gemm_bf16(const void *d_a, int lda, const void *d_b, int ldb, v
     if ((epilogue == PCMD_GEMM_BIAS_F32 || epilogue == PCMD_GEMM_BIAS_GELU_BF16 ||
          epilogue == PCMD_GEMM_BIAS_BF16) && !d_bias)
         return PCMD_ERR_ARG;
-    if (epilogue == PCMD_GEMM_BIAS_GELU_BF16 && !d_aux) return PCMD_ERR_ARG;
     if (epilogue < 0 || epilogue > 3) return PCMD_ERR_ARG;
     GemmArgs g;
     g.c = d_c;

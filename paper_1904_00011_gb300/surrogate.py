@@ -44,12 +44,13 @@ def _setup_types():
     L.pcmd_mlp_train_step.argtypes = [vp, vp, i, i, ctypes.c_float, i]
     L.pcmd_mlp_loss.argtypes = [vp, dp]
     L.pcmd_mlp_loglike.argtypes = [vp, i, vp, d, d, dp]
+    L.pcmd_mlp_forward_loglike.argtypes = [vp, vp, i, i, vp, d, d, dp]
     L.pcmd_mlp_get_layer.argtypes = [vp, i, vp, vp, vp, vp]
     L.pcmd_mlp_set_loss.argtypes = [vp, i]
     L.pcmd_mlp_set_layer.argtypes = [vp, i, vp, vp]
     for n in ["pcmd_mlp_create", "pcmd_mlp_forward", "pcmd_mlp_targets", "pcmd_mlp_set_targets",
               "pcmd_mlp_train_step", "pcmd_mlp_loss", "pcmd_mlp_loglike", "pcmd_mlp_get_layer",
-              "pcmd_mlp_set_layer", "pcmd_mlp_set_loss"]:
+              "pcmd_mlp_set_layer", "pcmd_mlp_set_loss", "pcmd_mlp_forward_loglike"]:
         getattr(L, n).restype = ctypes.c_int
     L._mlp_types = True
     return L
@@ -144,6 +145,17 @@ class Mlp:
         self._chk(self.L.pcmd_mlp_loglike(self.h, B, d_data_hess.data_ptr(), float(scale), float(ratio),
                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                   "pcmd_mlp_loglike")
+        return out
+
+    def forward_loglike(self, theta, d_data_hess, scale: float, ratio: float) -> np.ndarray:
+        """Forward pass and likelihood in one call; the predicted diagrams are not written."""
+        keep, on_dev, ptr = self._theta(theta)
+        B = keep.shape[0]
+        out = np.zeros(B)
+        self._chk(self.L.pcmd_mlp_forward_loglike(self.h, ptr if not on_dev else ptr.data_ptr(), on_dev, B,
+                                                  d_data_hess.data_ptr(), float(scale), float(ratio),
+                                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                  "pcmd_mlp_forward_loglike")
         return out
 
     def get_layer(self, l: int):
@@ -251,9 +263,9 @@ class Surrogate:
         th = np.asarray(theta, np.float32)
         if pad:
             th = np.concatenate([th, np.repeat(th[-1:], pad, axis=0)])
-        self.net.forward(th)
         scale = float(self.exact_n_im ** 2) / float(self.n_im ** 2)
-        ll = self.net.loglike(len(th), d_mock_hess.reshape(-1), scale, mock_n_pix / float(self.exact_n_im ** 2))
+        ll = self.net.forward_loglike(th, d_mock_hess.reshape(-1), scale,
+                                      mock_n_pix / float(self.exact_n_im ** 2))
         return ll[:n]
 
     def exact_loglike(self, theta: np.ndarray, d_mock_hess, mock_moments, mock_n_pix: float,

@@ -65,3 +65,16 @@ def test_gemm_epilogues(epi, m, n, k):
         assert torch.allclose(c.float(), z, rtol=1e-2, atol=1e-2)
     else:
         assert torch.allclose(c, z, rtol=1e-4, atol=1e-4)
+
+
+def test_gelu_without_preactivation_output():
+    import paper_1904_00011_gb300 as P
+    m, n, k = 600, 1000, 128
+    a = _rand((m, k), 5, 0.3)
+    b = _rand((n, k), 6, 0.3)
+    bias = torch.linspace(-1, 1, n, device="cuda", dtype=torch.float32)
+    c1, aux = P.gemm(a, b, bias=bias, epilogue=P.PCMD_GEMM_BIAS_GELU_BF16)
+    c2, none = P.gemm(a, b, bias=bias, epilogue=P.PCMD_GEMM_BIAS_GELU_BF16, want_aux=False)
+    torch.cuda.synchronize()
+    assert none is None and aux is not None
+    assert torch.equal(c1, c2)

@@ -103,3 +103,20 @@ def test_surrogate_loglike_matches_fp64_reference(poisson):
     got = net.loglike(theta.shape[0], d_dev, scale, ratio)
     ref = M.surrogate_loglike(y.cpu().numpy(), d, scale, ratio, poisson)
     assert np.allclose(got, ref, rtol=1e-5, atol=1e-3), np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("poisson", [True, False])
+def test_fused_forward_loglike_matches_two_step_path(poisson):
+    net, Ws, bs, theta, x = _setup(seed=7)
+    net.set_loss(poisson)
+    rng = np.random.default_rng(12)
+    d = rng.poisson(2.0, size=DIMS[-1]).astype(np.uint32)
+    d[::5] = 0
+    d_dev = torch.from_numpy(d.astype(np.int32)).cuda()
+    scale, ratio = 9.0, 1.3
+    y = net.predict(theta)
+    two = net.loglike(theta.shape[0], d_dev, scale, ratio)
+    fused = net.forward_loglike(theta, d_dev, scale, ratio)
+    ref = M.surrogate_loglike(y.cpu().numpy(), d, scale, ratio, poisson)
+    assert np.allclose(fused, two, rtol=1e-5, atol=1e-3), np.abs(fused - two).max()
+    assert np.allclose(fused, ref, rtol=1e-5, atol=1e-3)
