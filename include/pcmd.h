@@ -171,19 +171,22 @@ pcmd_status pcmd_set_launch(pcmd_ctx *ctx, int block, int split, int chunk);
  * events recorded on the context's stream and keeps the pairs per kernel kind;
  * pcmd_kernel_times synchronises, returns the summed milliseconds and launch counts of each
  * kind since the last call (h_ms, h_count: [PCMD_KERNEL_KINDS], host) and clears them.  A graph
- * replay of pcmd_evaluate counts as one PCMD_K_GRAPH launch. */
+ * replay of pcmd_evaluate counts as one PCMD_K_GRAPH launch; PCMD_K_TABLES is the device table
+ * builder (its three launches as one). */
 enum { PCMD_K_DRAW = 0, PCMD_K_HESS = 1, PCMD_K_FINALIZE = 2, PCMD_K_LOGLIKE = 3,
-       PCMD_K_GRAPH = 4, PCMD_K_GEMM = 5, PCMD_K_OTHER = 6, PCMD_KERNEL_KINDS = 8 };
+       PCMD_K_GRAPH = 4, PCMD_K_GEMM = 5, PCMD_K_TABLES = 6, PCMD_KERNEL_KINDS = 8 };
 pcmd_status pcmd_profile(pcmd_ctx *ctx, int enable);
 pcmd_status pcmd_kernel_times(pcmd_ctx *ctx, double *h_ms, int *h_count);
 
 /* Number of isochrone points P = n_ages * n_feh * n_mass of the context. */
 int pcmd_n_points(const pcmd_ctx *ctx);
 
-/* Host copies of one model's tables: h_lam [2][P] FP32 Poisson means of the two dust halves
- * (half 1 = behind the screen), h_flux [P][n_bands] FP32 electrons per star, h_z0 [2][P] the
- * 32-bit draw-word threshold above which a draw is non-zero.  Any pointer may be NULL.
- * Synchronous, host only. */
+/* Host copies of one model's tables, as the device table builder computes them for the draw
+ * kernel: h_lam [2][P] FP32 Poisson means of the two dust halves (half 1 = behind the screen),
+ * h_flux [P][n_bands] FP32 electrons per star, h_z0 [2][P] the 32-bit draw-word threshold above
+ * which a draw is non-zero (0xFFFFFFFF unless 0 < lambda < 10).  Any pointer may be NULL.
+ * Builds the model's tables on the context's stream (replacing staged tables of an earlier
+ * call) and synchronises. */
 pcmd_status pcmd_get_tables(pcmd_ctx *ctx, const pcmd_params *h_params, float *h_lam,
                             float *h_flux, uint32_t *h_z0);
 

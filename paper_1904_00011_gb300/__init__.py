@@ -220,7 +220,7 @@ def gemm(a, b, bias=None, epilogue=PCMD_GEMM_F32, err=None, want_aux=True):
     return c, aux
 
 
-KERNEL_KINDS = ["draw", "hess", "finalize", "loglike", "graph", "gemm", "other", "spare"]
+KERNEL_KINDS = ["draw", "hess", "finalize", "loglike", "graph", "gemm", "tables", "spare"]
 
 
 def pcmd_profile(ctx, enable: bool) -> None:

@@ -11,6 +11,7 @@
 #include "../../include/pcmd.h"
 #include "pcmd_internal.h"
 #include "tables.h"
+#include "tables_dev.h"
 
 namespace pcmd {
 int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int block, size_t smem);
@@ -78,13 +79,13 @@ struct pcmd_ctx {
 
     DevBuf tables, desc, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
-    HostBuf h_tables, h_desc, h_items, h_order, h_meta, h_ll;
+    DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
+    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
-    std::vector<SetTables> sets;
-    size_t tab_bytes = 0;
+    TabLayout layout;
     std::vector<SetDesc> descs;
-    std::vector<SetStats> stats;
+    std::vector<double> cost;
     std::vector<uint2> item_list;
     std::vector<uint32_t> order_list;
 
@@ -180,52 +181,97 @@ static pcmd_status check_params(pcmd_ctx *ctx, const pcmd_params *p, int n_sets,
     return PCMD_OK;
 }
 
-// Build the tables of n_sets models and stage them (host pinned -> device) on the stream.
+// Relative cost per pixel of a model, for the longest-first queue of a batch: lambda of every
+// point from the same FP64 products as the device builder; groups with an inversion point,
+// dense groups (a point at or above kDenseLam) and transformed-rejection points.
+static double model_cost(const Model &m, const double *w, const double hf[2]) {
+    const int P = m.n_points();
+    double c = 200.0;
+    for (int h = 0; h < 2; ++h) {
+        if (hf[h] == 0.0) continue;
+        for (int g = 0; g < (P + 7) / 8; ++g) {
+            float mx = 0.0f;
+            bool act = false;
+            for (int i = g * 8; i < std::min(P, g * 8 + 8); ++i) {
+                const float l = (float)(w[i / m.n_mass] * m.imf[i] * hf[h]);
+                if (l >= kPtrsThreshold) c += 180.0;
+                else if (l > 1e-10f) {
+                    act = true;
+                    mx = std::max(mx, l);
+                }
+            }
+            if (act) c += mx >= kDenseLam ? 400.0 : 60.0;
+        }
+    }
+    return c;
+}
+
+static void half_factors(const Model &m, double hf[2]) {
+    if (!m.dust || m.f_dust <= 0.0) {
+        hf[0] = 1.0;
+        hf[1] = 0.0;
+    } else if (m.f_dust >= 1.0) {
+        hf[0] = 0.0;
+        hf[1] = 1.0;
+    } else {
+        hf[0] = 1.0 - m.f_dust;
+        hf[1] = m.f_dust;
+    }
+}
+
+// Stage n_sets models: the host computes the per-isochrone weights w_jk = SFH_j MDF_k and the
+// distance factor of each model (FP64), one pinned upload carries them with the descriptors and
+// the work items, and the device builds the tables (list lengths land in the descriptors).
 // Items are pixel tiles of block / split pixels; `cost_sorted` orders the queue longest first.
 static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, const int *n_im,
-                              uint32_t first_set_id, bool cost_sorted, int ppc) {
-    const int B = ctx->model.n_bands;
+                              uint32_t first_set_id, bool cost_sorted, int ppc,
+                              float *insp_lam = nullptr, float *insp_flux = nullptr,
+                              uint32_t *insp_z0 = nullptr) {
+    const Model &m = ctx->model;
+    const int B = m.n_bands;
+    const uint32_t P = (uint32_t)m.n_points();
+    const int nw = m.n_ages * m.n_feh;
+    const TabLayout &L = ctx->layout;
+    double hf[2];
+    half_factors(m, hf);
     ctx->descs.assign(n_sets, SetDesc());
-    ctx->stats.assign(n_sets, SetStats());
+    ctx->cost.assign(n_sets, 0.0);
     ctx->item_list.clear();
-    if ((int)ctx->sets.size() < n_sets) ctx->sets.resize(n_sets);
-    auto one = [&](int s) {
-        std::memset(&ctx->sets[s].d, 0, sizeof(SetDesc));
-        build_set_tables(ctx->model, p[s], ctx->sets[s], n_sets == 1);
-    };
-    if (n_sets > 1) parallel_for(n_sets, one);
-    else one(0);
-    std::vector<size_t> base(n_sets);
-    size_t total = 0;
-    for (int s = 0; s < n_sets; ++s) {
-        base[s] = total;
-        total += (ctx->sets[s].bytes + 15) & ~size_t(15);
-    }
-    total = std::max<size_t>(total, 16);
     if (ctx->staged_pending) {
         CK(cudaEventSynchronize(ctx->staged));
         ctx->staged_pending = false;
     }
-    CK(ctx->h_tables.ensure(total));
-    {
-        uint8_t *dst = ctx->h_tables.as<uint8_t>();
-        auto em = [&](int s) { emit_set_tables(ctx->sets[s], dst + base[s]); };
-        if (n_sets > 1) parallel_for(n_sets, em);
-        else em(0);
-    }
-    ctx->tab_bytes = total;
+    const size_t in_bytes = sizeof(TabSetIn) * n_sets, w_bytes = sizeof(double) * (size_t)nw * n_sets;
+    CK(ctx->h_tab_in.ensure(in_bytes + w_bytes));
+    TabSetIn *tin = ctx->h_tab_in.as<TabSetIn>();
+    double *wts = reinterpret_cast<double *>(ctx->h_tab_in.as<uint8_t>() + in_bytes);
+    std::vector<double> mdf;
     uint64_t img_off = 0;
     for (int s = 0; s < n_sets; ++s) {
-        SetDesc &d = ctx->descs[s];
-        d = ctx->sets[s].d;
-        ctx->stats[s] = ctx->sets[s].st;
-        for (int h = 0; h < 2; ++h) {
-            d.grp_off[h] += base[s];
-            d.dense_off[h] += base[s];
-            d.slow_off[h] += base[s];
-            d.ptrs_off[h] += base[s];
+        m.mdf_weights(p[s].feh_mean, p[s].feh_sigma, mdf);
+        double *w = wts + (size_t)s * nw;
+        for (int j = 0; j < m.n_ages; ++j) {
+            const double sfh = std::pow(10.0, p[s].log_sfh[j]);
+            for (int k = 0; k < m.n_feh; ++k) w[j * m.n_feh + k] = sfh * mdf[k];
         }
-        d.tail_off += base[s];
+        tin[s].base = (uint64_t)s * L.bytes;
+        tin[s].flux_factor = std::pow(10.0, -0.4 * p[s].dmod);
+        tin[s].w_off = (uint32_t)(s * nw);
+        tin[s].pad = 0;
+        SetDesc &d = ctx->descs[s];
+        std::memset(&d, 0, sizeof d);
+        for (int h = 0; h < 2; ++h) {
+            d.grp_off[h] = tin[s].base + L.grp_off[h];
+            d.dense_off[h] = tin[s].base + L.dense_off[h];
+            d.slow_off[h] = tin[s].base + L.slow_off[h];
+            d.ptrs_off[h] = tin[s].base + L.ptrs_off[h];
+        }
+        d.tail_off = tin[s].base + L.tail_off;
+        // dust screen of this model (Section 2.2): E = 10^log_ebv exp(sigma z)
+        d.dust_on = m.dust ? 1u : 0u;
+        d.dust_a = (float)(std::log(10.0) * p[s].log_ebv);
+        d.dust_sigma = (float)p[s].dust_sigma;
+        for (int b = 0; b < kMaxBands; ++b) d.dust_c[b] = b < B ? (float)(-0.4 * m.r_ext[b]) : 0.0f;
         d.n_im = (uint32_t)n_im[s];
         d.set_id = first_set_id + (uint32_t)s;
         d.img_off = img_off;
@@ -234,32 +280,60 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         d.item_begin = (uint32_t)ctx->item_list.size();
         d.n_items = (npix + ppc - 1) / ppc;
         for (uint32_t t = 0; t < d.n_items; ++t) ctx->item_list.push_back(make_uint2((uint32_t)s, t));
+        if (cost_sorted && n_sets > 1) ctx->cost[s] = model_cost(m, w, hf);
     }
     const size_t n_items = ctx->item_list.size();
     ctx->order_list.resize(n_items);
     std::iota(ctx->order_list.begin(), ctx->order_list.end(), 0u);
     if (cost_sorted && n_sets > 1) {
         std::stable_sort(ctx->order_list.begin(), ctx->order_list.end(), [&](uint32_t a, uint32_t b) {
-            return ctx->stats[ctx->item_list[a].x].cost_per_pixel >
-                   ctx->stats[ctx->item_list[b].x].cost_per_pixel;
+            return ctx->cost[ctx->item_list[a].x] > ctx->cost[ctx->item_list[b].x];
         });
     }
+    const uint32_t G = (P + 7u) / 8u;
     CK(ctx->h_desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
-    CK(ctx->tables.ensure(ctx->tab_bytes));
+    CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
+    CK(ctx->tab_in.ensure(in_bytes + w_bytes));
+    CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets));
     CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->items.ensure(sizeof(uint2) * n_items));
     CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
     std::memcpy(ctx->h_desc.p, ctx->descs.data(), sizeof(SetDesc) * n_sets);
     std::memcpy(ctx->h_items.p, ctx->item_list.data(), sizeof(uint2) * n_items);
     std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
-    CK(cudaMemcpyAsync(ctx->tables.p, ctx->h_tables.p, ctx->tab_bytes, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, in_bytes + w_bytes, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
+
+    TabArgs ta;
+    std::memset(&ta, 0, sizeof ta);
+    ta.tables = ctx->tables.as<uint8_t>();
+    ta.desc = ctx->desc.as<SetDesc>();
+    ta.sets = ctx->tab_in.as<TabSetIn>();
+    ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
+    ta.imf = ctx->imf_d.as<double>();
+    ta.base_flux = ctx->bflux_d.as<double>();
+    ta.hf[0] = hf[0];
+    ta.hf[1] = hf[1];
+    ta.P = P;
+    ta.G = G;
+    ta.n_mass = m.n_mass;
+    ta.n_bands = B;
+    ta.layout = L;
+    ta.scratch = ctx->tab_scratch.as<uint4>();
+    ta.insp_lam = insp_lam;
+    ta.insp_flux = insp_flux;
+    ta.insp_z0 = insp_z0;
+    {
+        KTimer t(ctx, PCMD_K_TABLES, ctx->st);
+        CK(launch_build_tables(ta, n_sets, ctx->st));
+        t.done(ctx->st);
+    }
     ctx->n_sets = n_sets;
     ctx->n_im.assign(n_im, n_im + n_sets);
     return PCMD_OK;
@@ -387,6 +461,12 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
             if (cudaMemcpy(ctx->psf_d.p, ctx->psf.data(), ctx->psf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
         }
         if (ctx->h_ll.ensure(sizeof(double) * c.max_sets) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+        if (ctx->imf_d.ensure(sizeof(double) * P) != cudaSuccess ||
+            ctx->bflux_d.ensure(sizeof(double) * P * c.n_bands) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+        if (cudaMemcpy(ctx->imf_d.p, m.imf.data(), sizeof(double) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->bflux_d.p, m.base_flux.data(), sizeof(double) * P * c.n_bands,
+                       cudaMemcpyHostToDevice) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
+        ctx->layout = tab_layout((uint32_t)P, c.n_bands);
         if (ctx->h_meta.ensure(sizeof(uint64_t) * (size_t)c.max_sets * 3) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
     } while (0);
     if (rc != PCMD_OK) {
@@ -408,9 +488,10 @@ void pcmd_destroy(pcmd_ctx *ctx) {
         }
     DevBuf *bufs[] = {&ctx->tables, &ctx->desc, &ctx->items, &ctx->order, &ctx->partials,
                       &ctx->part_begin, &ctx->part_count, &ctx->image, &ctx->pix_off, &ctx->hess,
-                      &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err};
+                      &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
+                      &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
     for (DevBuf *b : bufs) b->release();
-    HostBuf *hb[] = {&ctx->h_tables, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
+    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
     for (HostBuf *b : hb) b->release();
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
@@ -726,28 +807,20 @@ pcmd_status pcmd_get_tables(pcmd_ctx *ctx, const pcmd_params *h_params, float *h
     int one = 1;
     pcmd_status rc = check_params(ctx, h_params, 1, &one);
     if (rc != PCMD_OK) return rc;
-    std::vector<float> lam_h[2], flux;
-    ctx->model.lambdas(*h_params, lam_h);
-    ctx->model.fluxes(h_params->dmod, flux);
+    // the device builder's own values (copies written while it builds the model's table)
     const size_t P = (size_t)ctx->model.n_points();
-    if (h_lam) {
-        std::memcpy(h_lam, lam_h[0].data(), P * 4);
-        std::memcpy(h_lam + P, lam_h[1].data(), P * 4);
-    }
-    if (h_flux) std::memcpy(h_flux, flux.data(), flux.size() * 4);
-    if (h_z0) {
-        uint32_t z[kInvCap];
-        for (int h = 0; h < 2; ++h)
-            for (size_t i = 0; i < P; ++i) {
-                const float l = lam_h[h][i];
-                if (!(l > 0.0f) || l >= kPtrsThreshold) h_z0[h * P + i] = 0xFFFFFFFFu;
-                else {
-                    inversion_thresholds(l, z, kInvCap);
-                    h_z0[h * P + i] = z[0];
-                }
-            }
-    }
-    return PCMD_OK;
+    const int B = ctx->model.n_bands;
+    const size_t bytes = P * (2 * 4 + (size_t)B * 4 + 2 * 4);
+    CK(ctx->insp.ensure(bytes));
+    float *lam = ctx->insp.as<float>();
+    float *flux = lam + 2 * P;
+    uint32_t *z0 = reinterpret_cast<uint32_t *>(flux + P * B);
+    rc = stage_sets(ctx, h_params, 1, &one, 0u, false, ctx->block / ctx->split, lam, flux, z0);
+    if (rc != PCMD_OK) return rc;
+    if (h_lam) CK(cudaMemcpyAsync(h_lam, lam, 2 * P * 4, cudaMemcpyDeviceToHost, ctx->st));
+    if (h_flux) CK(cudaMemcpyAsync(h_flux, flux, P * B * 4, cudaMemcpyDeviceToHost, ctx->st));
+    if (h_z0) CK(cudaMemcpyAsync(h_z0, z0, 2 * P * 4, cudaMemcpyDeviceToHost, ctx->st));
+    return pcmd_sync(ctx);
 }
 
 pcmd_status pcmd_counts(pcmd_ctx *ctx, const pcmd_params *h_params, int n_im, uint32_t set_id,
