@@ -18,8 +18,9 @@
  *            as 1, 2, 3"), key = 64-bit seed, counter = (pixel, index, set, tag).
  *   tag      kind << 28 | half << 27 | sub;  kinds HI=1, LO=2, PTRS=3, DUST=4, NOISE=5.
  *   uniform  u(w) = ((w >> 8) | 1) * 2^-24, exact in FP32, in (0, 1).
- *   inversion (lambda < 10): x = hi16 << 16 | lo16 with hi16 / lo16 the (i & 7)-th 16-bit
- *            slot of the HI / LO call with index i >> 3; v = (x + 0.5) 2^-32;
+ *   inversion (lambda < 10): x = b << 24 | l >> 8 with b byte (i & 3) of word (i & 15) >> 2
+ *            of the HI call with index i >> 4, l word (i & 3) of the LO call with index
+ *            i >> 2; v = (x + 0.5) 2^-32;
  *            n = min{k : v < F_k}, F_k the FP64 Poisson CDF by p_k = p_{k-1} lambda / k,
  *            capped at 64.
  *   PTRS (lambda >= 10): Hormann (1993) transformed rejection with squeeze, attempts a use
@@ -74,19 +75,15 @@ static void or_call(uint64_t seed, uint32_t pix, uint32_t index, uint32_t set, u
     or_philox(ctr, key, out);
 }
 
-static uint32_t or_slot16(const uint32_t w[4], uint32_t j)
-{
-    uint32_t word = w[j >> 1];
-    return (j & 1u) ? (word >> 16) : (word & 0xFFFFu);
-}
-
-/* The 32-bit draw word of inversion entry (half, point i) at pixel pix. */
+/* The 32-bit draw word of inversion entry (half, point i) at pixel pix: the top byte from the
+ * HI call of the point's group of 16, the low 24 bits from the LO call of its group of 4. */
 uint32_t or_draw_word(uint64_t seed, uint32_t pix, uint32_t i, uint32_t set, uint32_t half)
 {
     uint32_t whi[4], wlo[4];
-    or_call(seed, pix, i >> 3, set, or_tag(OR_KIND_HI, half, 0), whi);
-    or_call(seed, pix, i >> 3, set, or_tag(OR_KIND_LO, half, 0), wlo);
-    return (or_slot16(whi, i & 7u) << 16) | or_slot16(wlo, i & 7u);
+    or_call(seed, pix, i >> 4, set, or_tag(OR_KIND_HI, half, 0), whi);
+    or_call(seed, pix, i >> 2, set, or_tag(OR_KIND_LO, half, 0), wlo);
+    const uint32_t b = (whi[(i & 15u) >> 2] >> (8u * (i & 3u))) & 0xFFu;
+    return (b << 24) | (wlo[i & 3u] >> 8);
 }
 
 float or_uniform(uint32_t w)

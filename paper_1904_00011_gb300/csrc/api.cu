@@ -189,10 +189,10 @@ static double model_cost(const Model &m, const double *w, const double hf[2]) {
     double c = 200.0;
     for (int h = 0; h < 2; ++h) {
         if (hf[h] == 0.0) continue;
-        for (int g = 0; g < (P + 7) / 8; ++g) {
+        for (int g = 0; g < (P + kGroup - 1) / kGroup; ++g) {
             float mx = 0.0f;
             bool act = false;
-            for (int i = g * 8; i < std::min(P, g * 8 + 8); ++i) {
+            for (int i = g * kGroup; i < std::min(P, g * kGroup + kGroup); ++i) {
                 const float l = (float)(w[i / m.n_mass] * m.imf[i] * hf[h]);
                 if (l >= kPtrsThreshold) c += 180.0;
                 else if (l > 1e-10f) {
@@ -200,7 +200,7 @@ static double model_cost(const Model &m, const double *w, const double hf[2]) {
                     mx = std::max(mx, l);
                 }
             }
-            if (act) c += mx >= kDenseLam ? 400.0 : 60.0;
+            if (act) c += mx >= kDenseLam ? 700.0 : 70.0;
         }
     }
     return c;
@@ -290,7 +290,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
             return ctx->cost[ctx->item_list[a].x] > ctx->cost[ctx->item_list[b].x];
         });
     }
-    const uint32_t G = (P + 7u) / 8u;
+    const uint32_t G = (P + kGroup - 1u) / kGroup;
     CK(ctx->h_desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));

@@ -160,10 +160,15 @@ __device__ __forceinline__ float uniform_of(uint32_t w) {
     return __fmul_rn(__uint2float_rn((w >> 8) | 1u), 5.9604644775390625e-08f);
 }
 
-__device__ __forceinline__ uint32_t slot16(const uint4 &w, uint32_t j) {
-    const uint32_t q = j >> 1;
-    const uint32_t word = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
-    return (j & 1u) ? (word >> 16) : (word & 0xFFFFu);
+__device__ __forceinline__ uint32_t word_of(const uint4 &w, uint32_t k) {
+    return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+}
+
+// Draw-word parts of inversion point i: the coarse byte is byte i & 3 of word (i & 15) >> 2 of
+// the HI call of group i >> 4; the low 24 bits are the top 24 bits of word i & 3 of the LO call
+// of quad i >> 2.  x = byte << 24 | low24.
+__device__ __forceinline__ uint32_t hi_byte(const uint4 &w, uint32_t j) {
+    return (word_of(w, j >> 2) >> (8u * (j & 3u))) & 0xFFu;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -9,10 +9,10 @@
 // the point tables streamed through shared memory by bulk copies.
 //
 // Draw word of inversion point i (lambda < 10) of half h at pixel p:
-//   x = hi16 << 16 | lo16, hi16 / lo16 the (i & 7)-th 16-bit slot of
-//   Philox(p, i >> 3, set, HI|h) / Philox(p, i >> 3, set, LO|h);  n = #{k : x > Z_k}.
-// The fast path only needs hi16: hi16 < Z_0 >> 16 gives n = 0 without the LO call, and a
-// certain hit with hi16 < Z_1 >> 16 gives n = 1.  Both are exact consequences of the rule.
+//   x = b << 24 | l >> 8, b = byte i & 3 of word (i & 15) >> 2 of Philox(p, i >> 4, set, HI|h),
+//   l = word i & 3 of Philox(p, i >> 2, set, LO|h);  n = #{k : x > Z_k}.
+// The fast path only needs b: b < Z_0 >> 24 gives n = 0 without the LO call, and a certain hit
+// with Z_0 >> 24 < b < Z_1 >> 24 gives n = 1.  Both are exact consequences of the rule.
 #include "common.cuh"
 
 namespace pcmd {
@@ -138,19 +138,12 @@ struct Acc {
     }
 };
 
-// Per-slot "maybe non-zero" bits of one HI call against the pre-shifted coarse thresholds:
-// odd slots compare the word itself, even slots the word shifted left by 16.
-__device__ __forceinline__ uint32_t maybe_mask(const uint4 &w, const uint4 &za, const uint4 &zb) {
-    uint32_t m = 0;
-    m |= (uint32_t)((w.x << 16) >= za.x) << 0;
-    m |= (uint32_t)(w.x >= za.y) << 1;
-    m |= (uint32_t)((w.y << 16) >= za.z) << 2;
-    m |= (uint32_t)(w.y >= za.w) << 3;
-    m |= (uint32_t)((w.z << 16) >= zb.x) << 4;
-    m |= (uint32_t)(w.z >= zb.y) << 5;
-    m |= (uint32_t)((w.w << 16) >= zb.z) << 6;
-    m |= (uint32_t)(w.w >= zb.w) << 7;
-    return m;
+// "Maybe non-zero" bits of the 16 slots of one HI call: bit 7 of byte j & 3 of word j >> 2 is
+// set iff HI byte j >= zc_j.  Per byte, (x | 0x80) - (zc & 0x7F) has bit 7 iff the low seven
+// bits of x are >= those of zc (no borrow leaves the byte); the top bits decide the rest.
+__device__ __forceinline__ uint32_t ge_bytes(uint32_t x, uint32_t z7, uint32_t zh) {
+    const uint32_t d = (x | 0x80808080u) - z7;
+    return (x & ~zh) | (~(x ^ zh) & d);          // bit 7 of each byte; other bits are noise
 }
 
 struct ItemCtx {
@@ -162,9 +155,6 @@ struct ItemCtx {
 
 constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
 
-// Resolve the queued maybe-hits of this thread: entry = g << 19 | slot << 16 | hi16, g the
-// group's index in the staged chunk.  n = 1 when hi16 is above Z_0 >> 16 and below Z_1 >> 16;
-// otherwise the LO call completes the 32-bit word and the full thresholds decide.
 // n = #{k : x > Z_k} from the slow record of a slot: Z_0, Z_1 in the record, Z_2.. in the tail
 // (saturated beyond its length).  The search starts at the record's start index k_s (near
 // lambda) and walks up or down; the count equals the linear scan's.
@@ -184,49 +174,50 @@ __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint
     return k;
 }
 
-// Resolve the queued maybe-hits of this thread: entry = g << 19 | slot << 16 | hi16, g the
-// group's index in the staged chunk.  n = 1 when hi16 is above Z_0 >> 16 and below Z_1 >> 16;
-// otherwise the LO call of the group completes the 32-bit word (kept for the following entries
-// of the same group) and the full thresholds decide.
+// Resolve the queued maybe-hits of this thread: entry = g << 12 | slot << 8 | byte, g the
+// group's index in the staged chunk.  n = 1 when the byte is above Z_0 >> 24 and below
+// Z_1 >> 24; otherwise the LO call of the slot's quad completes the 32-bit word (kept for the
+// following entries of the same quad) and the full thresholds decide.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic,
                                             const uint8_t *cb, const uint32_t *queue, int qn,
                                             Acc<B, KAHAN> &acc) {
     constexpr uint32_t rec = group_rec_bytes(B);
-    uint32_t lo_g = 0xFFFFFFFFu;
+    uint32_t lo_q = 0xFFFFFFFFu;
     uint4 wlo = make_uint4(0, 0, 0, 0);
     for (int q = 0; q < qn; ++q) {
         const uint32_t e = queue[q * blockDim.x + threadIdx.x];
-        const uint32_t g = e >> 19, j = (e >> 16) & 7u, hi = e & 0xFFFFu;
+        const uint32_t g = e >> 12, j = (e >> 8) & 15u, hi = e & 0xFFu;
         const uint8_t *r = cb + g * rec;
-        const uint32_t zc0 = *reinterpret_cast<const uint32_t *>(r + kRecZs + 4 * j) >> 16;
-        const uint32_t zc1 = *reinterpret_cast<const uint16_t *>(r + kRecZc1 + 2 * j);
+        const uint32_t zc0 = r[kRecZ7 + j] | r[kRecZh + j];
+        const uint32_t zc1 = r[kRecZc1 + j];
         const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
+        const uint32_t i = gid * (uint32_t)kGroup + j;
         uint32_t n;
         if (hi > zc0 && hi < zc1) {
             n = 1u;
         } else {
-            if (g != lo_g) {
-                wlo = philox_rk(ic.pix, gid, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
-                lo_g = g;
+            if ((i >> 2) != lo_q) {
+                lo_q = i >> 2;
+                wlo = philox_rk(ic.pix, lo_q, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
             }
-            const uint32_t x = (hi << 16) | slot16(wlo, j);
-            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + (gid * 8u + j));
+            const uint32_t x = (hi << 24) | (word_of(wlo, j & 3u) >> 8);
+            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + i);
             n = count_from_thresholds(x, sr, ic.tail);
         }
         if (n) {
             acc.template add<H>((float)n, reinterpret_cast<const float *>(r + kRecFlux) + j * B);
             if (MODE == kModeCounts) {
                 if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * 8u + j] = n;
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
             }
         }
     }
 }
 
 // One staged chunk of groups: the HI call of every (pixel, group) from the pixel's Philox
-// prefix, one compare per slot OR-ed into "any maybe-hit", and the rare maybe-hits pushed to the
-// thread's queue; a thread drains its own queue when it is nearly full and at the chunk's end.
+// prefix, four byte-wise compares OR-ed into "any maybe-hit", and the rare maybe-hits pushed to
+// the thread's queue, which it drains when full and at the chunk's end.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
                                               const PhiloxPrefix &pf, const uint8_t *cb,
@@ -238,20 +229,28 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
     for (uint32_t g = (uint32_t)sidx; g < cnt; g += (uint32_t)a.split) {
         const uint8_t *r = cb + g * rec;
         const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
-        const uint4 za = *reinterpret_cast<const uint4 *>(r + kRecZs);
-        const uint4 zb = *reinterpret_cast<const uint4 *>(r + kRecZs + 16);
+        const uint4 z7 = *reinterpret_cast<const uint4 *>(r + kRecZ7);
+        const uint4 zh = *reinterpret_cast<const uint4 *>(r + kRecZh);
         const uint4 w = philox_from_prefix_rk(pf, gid, a.rk0, a.rk1);
-        uint32_t m = maybe_mask(w, za, zb);
-        if (m) {
-            do {
-                const uint32_t j = (uint32_t)(__ffs(m) - 1);
-                m &= m - 1u;
-                queue[qn * blockDim.x + threadIdx.x] = (g << 19) | (j << 16) | slot16(w, j);
-                ++qn;
-            } while (m);
-            if (qn > kQueueCap - 8) {
-                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
-                qn = 0;
+        const uint32_t m0 = ge_bytes(w.x, z7.x, zh.x), m1 = ge_bytes(w.y, z7.y, zh.y);
+        const uint32_t m2 = ge_bytes(w.z, z7.z, zh.z), m3 = ge_bytes(w.w, z7.w, zh.w);
+        if ((m0 | m1 | m2 | m3) & 0x80808080u) {
+            const uint32_t mw[4] = {m0 & 0x80808080u, m1 & 0x80808080u, m2 & 0x80808080u, m3 & 0x80808080u};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = mw[k];
+                while (m) {
+                    const uint32_t bit = (uint32_t)(__ffs(m) - 1);
+                    m &= m - 1u;
+                    if (qn == kQueueCap) {
+                        drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+                        qn = 0;
+                    }
+                    const uint32_t j = 4u * (uint32_t)k + (bit >> 3);
+                    const uint32_t hb = (word_of(w, (uint32_t)k) >> (bit - 7u)) & 0xFFu;
+                    queue[qn * blockDim.x + threadIdx.x] = (g << 12) | (j << 8) | hb;
+                    ++qn;
+                }
             }
         }
     }
@@ -259,7 +258,8 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
 }
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
-// both calls of the group are drawn up front and every slot walks its thresholds directly.
+// the HI call and the four LO calls of the group are drawn up front and every slot walks its
+// thresholds directly.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -273,22 +273,27 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         const uint8_t *r = base + (size_t)q * rec;
         const uint32_t gid = __ldg(reinterpret_cast<const uint32_t *>(r));
         const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
-        const uint4 wlo = philox_from_prefix_rk(pl, gid, a.rk0, a.rk1);
-        const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * 8u;
+        const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * (uint32_t)kGroup;
         const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+#pragma unroll 1
+        for (uint32_t qd = 0; qd < 4u; ++qd) {
+            const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
 #pragma unroll 2
-        for (uint32_t j = 0; j < 8u; ++j) {
-            const uint32_t x = (slot16(whi, j) << 16) | slot16(wlo, j);
-            const uint4 sr = __ldg(slow + j);
-            const uint32_t n = count_from_thresholds(x, sr, ic.tail);
-            if (n) {
-                float f[B];
+            for (uint32_t t = 0; t < 4u; ++t) {
+                const uint32_t j = 4u * qd + t;
+                const uint32_t x = (hi_byte(whi, j) << 24) | (word_of(wlo, t) >> 8);
+                const uint4 sr = __ldg(slow + j);
+                const uint32_t n = count_from_thresholds(x, sr, ic.tail);
+                if (n) {
+                    float f[B];
 #pragma unroll
-                for (int b = 0; b < B; ++b) f[b] = __ldg(fl + j * B + b);
-                acc.template add<H>((float)n, f);
-                if (MODE == kModeCounts) {
-                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * 8u + j] = n;
+                    for (int b = 0; b < B; ++b) f[b] = __ldg(fl + j * B + b);
+                    acc.template add<H>((float)n, f);
+                    if (MODE == kModeCounts) {
+                        if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                            a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
+                                     gid * (uint32_t)kGroup + j] = n;
+                    }
                 }
             }
         }

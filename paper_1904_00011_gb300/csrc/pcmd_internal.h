@@ -6,7 +6,7 @@
 namespace pcmd {
 
 constexpr int kMaxBands = 4;
-constexpr int kGroup = 8;                 // isochrone points per Philox HI/LO call
+constexpr int kGroup = 16;                // isochrone points per HI call (one byte each)
 constexpr float kPtrsThreshold = 10.0f;   // inversion below, transformed rejection at/above
 constexpr int kInvCap = 64;               // inversion counts are capped at 64 (lambda < 10)
 constexpr float kDenseLam = 0.3f;         // groups with a slot at or above this are "dense"
@@ -18,16 +18,19 @@ enum : uint32_t { kKindHi = 1u, kKindLo = 2u, kKindPtrs = 3u, kKindDust = 4u, kK
 // device error bits
 enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
 
-// Fast-path record of 8 consecutive isochrone points of one dust half (staged in shared memory
-// by bulk copies).  Size 64 + 32 * B bytes (a multiple of 16).
-//   u32 gid              group index (points 8*gid .. 8*gid+7)
+// Fast-path record of 16 consecutive isochrone points of one dust half (staged in shared memory
+// by bulk copies).  Size 64 + 64 * B bytes (a multiple of 16).
+//   u32 gid              group index (points 16*gid .. 16*gid+15)
 //   u32 pad[3]
-//   u32 zs[8]            (Z_0 >> 16) << 16 per slot: slot j "may be non-zero" when
-//                        hi16 >= Z_0 >> 16, i.e. w >= zs (odd j) or (w << 16) >= zs (even j)
-//   u16 zc1[8]           Z_1 >> 16 per slot: a certain hit with hi16 < zc1 has n = 1
-//   f32 flux[8][B]       electrons per star of each slot
-__host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 32u * (uint32_t)nb; }
-constexpr uint32_t kRecZs = 16, kRecZc1 = 48, kRecFlux = 64;
+//   u32 z7[4]            coarse thresholds zc_j = Z_0 >> 24, slot j at byte j & 3 of word j >> 2,
+//                        low 7 bits of each byte
+//   u32 zh[4]            the same bytes' top bits (zc_j & 0x80)
+//   u8  zc1[16]          Z_1 >> 24 per slot: a certain hit with zc_j < byte < zc1_j has n = 1
+//   f32 flux[16][B]      electrons per star of each slot
+// Slot j "may be non-zero" iff its HI byte >= zc_j; the 16 tests are four SIMD-within-a-word
+// byte compares against z7 / zh.
+__host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 64u * (uint32_t)nb; }
+constexpr uint32_t kRecZ7 = 16, kRecZh = 32, kRecZc1 = 48, kRecFlux = 64;
 
 // Slow-path record per point and half (global memory): full 32-bit thresholds.
 struct SlowRec {

@@ -7,10 +7,10 @@
 //   lambda_h,i = (float)((w_jk * imf_i) * hf_h),  flux_i,b = (float)(base_flux_i,b * 10^(-0.4 dmod))
 //   p_0 = exp(-lambda), p_k = (p_{k-1} lambda) / k, F_k = F_{k-1} + p_k,
 //   Z_k = ceil(F_k 2^32 - 1/2) - 1 (saturating at 2^32 - 1): n > k iff x > Z_k.
-// Three launches: count (per point, reduced per 8-point group), scan (per model and half, the
+// Three launches: count (per point, reduced per 16-point group), scan (per model and half, the
 // list positions of every group), write (group records, slow records, tail thresholds,
-// transformed-rejection records at their positions).  One thread per point; the 8 points of a
-// group are 8 consecutive lanes.
+// transformed-rejection records at their positions).  One thread per point; the 16 points of
+// a group are 16 consecutive lanes.
 #include "common.cuh"
 #include "tables_dev.h"
 
@@ -34,7 +34,7 @@ struct PointIn {
 
 __device__ __forceinline__ PointIn point_of(const TabArgs &a, const TabSetIn &in, uint32_t g, int j, int h) {
     PointIn p;
-    p.i = g * 8u + (uint32_t)j;
+    p.i = g * (uint32_t)kGroup + (uint32_t)j;
     p.valid = p.i < a.P;
     p.lam = 0.0f;
     if (p.valid) {
@@ -96,23 +96,23 @@ __device__ __forceinline__ PointCls classify(const PointIn &p) {
     return c;
 }
 
-// Exclusive prefix sum of v over the 8 lanes of a group (lanes 8q .. 8q+7), and the group total.
+// Exclusive prefix sum of v over the 16 lanes of a group, and the group total.
 __device__ __forceinline__ uint32_t group_scan(uint32_t v, int j, uint32_t &total) {
     uint32_t s = v;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, s, o, 8);
+    for (int o = 1; o < kGroup; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, s, o, kGroup);
         if (j >= o) s += u;
     }
-    total = __shfl_sync(0xffffffffu, s, 7, 8);
+    total = __shfl_sync(0xffffffffu, s, kGroup - 1, kGroup);
     return s - v;
 }
 
 __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const int h = blockIdx.y, s = blockIdx.z;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t g = t >> 3;
-    const int j = (int)(t & 7u);
+    const uint32_t g = t / (uint32_t)kGroup;
+    const int j = (int)(t % (uint32_t)kGroup);
     const TabSetIn in = a.sets[s];
     const PointIn p = g < a.G ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
     const PointCls c = classify(p);
@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     group_scan(c.cls == 1 ? c.tail : 0u, j, n_tail);
     group_scan(c.cls == 2 ? 1u : 0u, j, n_ptrs);
     // dense: an inversion slot at or above kDenseLam
-    const uint32_t act = __ballot_sync(0xffffffffu, c.cls == 1) >> (threadIdx.x & 24u) & 0xFFu;
-    const uint32_t dense = __ballot_sync(0xffffffffu, c.cls == 1 && p.lam >= kDenseLam) >> (threadIdx.x & 24u) & 0xFFu;
+    const uint32_t act = __ballot_sync(0xffffffffu, c.cls == 1) >> (threadIdx.x & 16u) & 0xFFFFu;
+    const uint32_t dense = __ballot_sync(0xffffffffu, c.cls == 1 && p.lam >= kDenseLam) >> (threadIdx.x & 16u) & 0xFFFFu;
     if (j == 0 && g < a.G) {
         const uint32_t cls = act == 0u ? 0u : (dense ? 2u : 1u);
         a.scratch[((size_t)s * 2 + h) * a.G + g] = make_uint4(cls, n_tail, n_ptrs, 0u);
@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(1024) tab_scan_kernel(const TabArgs a) {
 __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     const int h = blockIdx.y, s = blockIdx.z;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t g = t >> 3;
-    const int j = (int)(t & 7u);
+    const uint32_t g = t / (uint32_t)kGroup;
+    const int j = (int)(t % (uint32_t)kGroup);
     const bool in_range = g < a.G;
     const TabSetIn in = a.sets[s];
     const PointIn p = in_range ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         if (ks < 2u) ks = 2u;
         const uint4 sr = c.cls == 1 ? make_uint4(z0, z1, tail_off, len | (ks << 16))
                                     : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
-        reinterpret_cast<uint4 *>(tab + L.slow_off[h])[(size_t)g * 8 + j] = sr;
+        reinterpret_cast<uint4 *>(tab + L.slow_off[h])[(size_t)g * kGroup + j] = sr;
     }
 
     // fluxes of this point
@@ -284,11 +284,12 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     if (in_range && sc.x != 0u) {
         const uint32_t rec = group_rec_bytes(B);
         uint8_t *r = tab + (sc.x == 2u ? L.dense_off[h] : L.grp_off[h]) + (size_t)sc.y * rec;
-        const uint32_t zc0 = c.cls == 1 ? (z0 >> 16) : 0xFFFFu;
-        const uint32_t zc1 = c.cls == 1 ? (z1 >> 16) : 0xFFFFu;
+        const uint32_t zc0 = c.cls == 1 ? (z0 >> 24) : 0xFFu;
+        const uint32_t zc1 = c.cls == 1 ? (z1 >> 24) : 0xFFu;
         if (j == 0) *reinterpret_cast<uint4 *>(r) = make_uint4(g, 0u, 0u, 0u);
-        reinterpret_cast<uint32_t *>(r + kRecZs)[j] = zc0 << 16;
-        reinterpret_cast<uint16_t *>(r + kRecZc1)[j] = (uint16_t)zc1;
+        r[kRecZ7 + j] = (uint8_t)(zc0 & 0x7Fu);
+        r[kRecZh + j] = (uint8_t)(zc0 & 0x80u);
+        r[kRecZc1 + j] = (uint8_t)zc1;
         float *f = reinterpret_cast<float *>(r + kRecFlux) + j * B;
         for (int b = 0; b < B; ++b) f[b] = fl[b];
     }
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
 
 TabLayout tab_layout(uint32_t P, int n_bands) {
     TabLayout L;
-    const uint32_t G = (P + 7u) / 8u;
+    const uint32_t G = (P + kGroup - 1u) / kGroup;
     const uint64_t rec = group_rec_bytes(n_bands);
     uint64_t off = 0;
     auto place = [&](uint64_t bytes) {
@@ -317,7 +318,7 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
     for (int h = 0; h < 2; ++h) {
         L.grp_off[h] = place(G * rec);
         L.dense_off[h] = place(G * rec);
-        L.slow_off[h] = place((uint64_t)G * 8u * sizeof(SlowRec));
+        L.slow_off[h] = place((uint64_t)G * kGroup * sizeof(SlowRec));
         L.ptrs_off[h] = place((uint64_t)P * sizeof(PtrsRec));
     }
     L.tail_off = place(2ull * P * (kInvCap - 2) * 4u + 4u);
@@ -327,7 +328,7 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
 
 cudaError_t launch_build_tables(const TabArgs &a, int n_sets, cudaStream_t st) {
     if (a.G == 0 || n_sets < 1 || n_sets > 65535) return cudaErrorInvalidValue;
-    const dim3 grid((a.G * 8u + 255u) / 256u, 2, n_sets);
+    const dim3 grid((a.G * kGroup + 255u) / 256u, 2, n_sets);
     tab_count_kernel<<<grid, 256, 0, st>>>(a);
     tab_scan_kernel<<<dim3(2, n_sets), 1024, 0, st>>>(a);
     tab_write_kernel<<<grid, 256, 0, st>>>(a);

@@ -12,7 +12,7 @@ namespace pcmd {
 struct TabLayout {
     uint64_t grp_off[2];    // group records of the sparse inversion groups, G per half
     uint64_t dense_off[2];  // group records of the dense inversion groups, G per half
-    uint64_t slow_off[2];   // SlowRec[8 G] per half
+    uint64_t slow_off[2];   // SlowRec[16 G] per half
     uint64_t ptrs_off[2];   // PtrsRec[P] per half
     uint64_t tail_off;      // uint32 [2][P][kInvCap - 2] tail thresholds
     uint64_t bytes;         // table size (256-byte multiple)

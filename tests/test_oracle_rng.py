@@ -147,12 +147,28 @@ def test_draw_switches_sampler_at_ten():
 
 
 def test_draw_word_layout():
-    """x = hi16 << 16 | lo16 from the HI / LO calls of group i >> 3, slot i & 7."""
+    """x = b << 24 | l >> 8: b byte i & 3 of word (i & 15) >> 2 of the HI call of group i >> 4,
+    l word i & 3 of the LO call of quad i >> 2."""
     seed = (0xDEADBEEF << 32) | 0x01234567
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    for (pix, i, s, h) in [(0, 0, 0, 0), (17, 9, 4, 1), (65535, 199, 511, 0), (3, 7, 2, 1)]:
-        whi = O.philox([pix, i >> 3, s, (1 << 28) | (h << 27)], key)
-        wlo = O.philox([pix, i >> 3, s, (2 << 28) | (h << 27)], key)
-        j = i & 7
-        sl = (lambda w: (int(w[j >> 1]) >> 16) if j & 1 else (int(w[j >> 1]) & 0xFFFF))
-        assert O.draw_word(seed, pix, i, s, h) == (sl(whi) << 16) | sl(wlo)
+    for (pix, i, s, h) in [(0, 0, 0, 0), (17, 9, 4, 1), (65535, 199, 511, 0), (3, 7, 2, 1), (8, 31, 1, 0)]:
+        whi = O.philox([pix, i >> 4, s, (1 << 28) | (h << 27)], key)
+        wlo = O.philox([pix, i >> 2, s, (2 << 28) | (h << 27)], key)
+        b = (int(whi[(i & 15) >> 2]) >> (8 * (i & 3))) & 0xFF
+        assert O.draw_word(seed, pix, i, s, h) == (b << 24) | (int(wlo[i & 3]) >> 8)
+
+
+def test_draw_words_are_uniform_and_distinct_across_points():
+    """Every point of a group has its own byte and its own low bits: over many pixels the words
+    of the 16 points of one group are uniform (chi-square on the top 4 bits) and pairwise
+    uncorrelated."""
+    from scipy import stats
+    seed = 12345
+    W = np.array([[O.draw_word(seed, p, i, 2, 0) for i in range(16)] for p in range(4000)], np.float64)
+    top = (W.astype(np.uint64) >> np.uint64(28)).astype(int)
+    for i in range(16):
+        cnt = np.bincount(top[:, i], minlength=16)
+        assert stats.chisquare(cnt).pvalue > 1e-4
+    c = np.corrcoef(W.T)
+    off = c[~np.eye(16, dtype=bool)]
+    assert np.abs(off).max() < 0.08
