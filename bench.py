@@ -51,7 +51,7 @@ def _args():
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     ap.add_argument("--surrogate-sims", type=int, default=262144,
                     help="simulations the surrogate is trained on in the extras")
-    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate"],
+    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp"],
                     help="run one extra section alone and print its JSON (profiling runs)")
     ap.add_argument("--large-n-im", type=int, default=1024, help="image edge of the large-Npix line")
     return ap.parse_args()
@@ -391,6 +391,9 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 102
     w = W.large(log_npix=log_npix, n_im=n_im)
     n = w.n_im
     sim = P.Simulator(w, max_sets=1)
+    # launch shape tuned on a 256x256 image of the same model (same per-pixel work)
+    from paper_1904_00011_gb300 import autotune
+    tuned = autotune.tune(sim, w.params, [min(n, 256)], reps=2, use_cache=False)
     sim.simulate(w.params, [n], 2_000_000)
     h, m, c, _ = sim.hess(1, [n])
     torch.cuda.synchronize()
@@ -412,6 +415,7 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 102
             "model_pixels_per_s": n * n / dt, "evals_per_s": 1.0 / dt, "ms_per_eval": 1e3 * dt,
             "draw_ms": draw_ms, "hess_ms": kt["hess"][0] / max(1, kt["hess"][1]),
             "entries_per_pixel": inv + ptrs, "ptrs_entries_per_pixel": ptrs,
+            "launch": {k: tuned[k] for k in ("block", "split", "chunk")},
             "draws_per_s": (inv + ptrs) * n * n / (draw_ms / 1e3)}
 
 
@@ -474,6 +478,41 @@ def run_surrogate(torch, n_sims: int = 262144, infer_batch: int = 4096, reps: in
                           "judge": "exact simulator, 256x256 images, Poisson likelihood"}}
 
 
+def run_mlp(torch, batch: int = 4096, reps: int = 20):
+    """Surrogate network alone (random init, no training): the 5-layer inference forward and the
+    fused forward + likelihood on a batch of parameter points; GEMM roofline."""
+    from paper_1904_00011_gb300.surrogate import Mlp
+    dims = [64, 1024, 1024, 1024, 1024, 10000]
+    net = Mlp(dims, 12, -np.ones(12), np.ones(12), max_batch=batch, seed=1)
+    net.set_loss(True)
+    rng = np.random.default_rng(0)
+    th = torch.from_numpy(rng.uniform(-1, 1, size=(batch, 12)).astype(np.float32)).cuda()
+    data = torch.from_numpy(rng.poisson(3.0, size=dims[-1]).astype(np.int32)).cuda()
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        net.forward(th)
+        net.forward_loglike(th, data, 16.0, 1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        net.forward(th)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.forward_loglike(th, data, 16.0, 1.0)
+    fused_ms = 1e3 * (time.perf_counter() - t0) / reps
+    flop = 2.0 * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1)) * batch
+    tflops = flop / (fwd_ms / 1e3) / 1e12
+    peak = _measured_peak("bf16_tflops", 1900.0)
+    return {"workload": "MLP 64(12)-4x1024 GELU-10000, BF16, batch %d, random weights" % batch,
+            "forward_ms": fwd_ms, "fused_loglike_ms": fused_ms, "evals_per_s": batch / (fused_ms / 1e3),
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "kernel": "gemm_bf16_kernel (5 layers)"}}
+
+
 def _measured_peak(key: str, fallback: float) -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -499,6 +538,8 @@ def main():
             out = run_large(P, W, torch, n_im=args.large_n_im)
         elif args.only == "batched":
             out = run_batched(None, P, W, torch)
+        elif args.only == "mlp":
+            out = run_mlp(torch)
         else:
             out = run_surrogate(torch, n_sims=args.surrogate_sims)
         print(json.dumps({"section": args.only, **out}), flush=True)
