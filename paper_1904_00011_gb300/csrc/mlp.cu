@@ -212,12 +212,10 @@ __global__ void sum_partials_kernel(const double *part, int n, double *out) {
     }
 }
 
-__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, double scale,
-                                         double ratio, int poisson, const double *lg_sum, double *ll) {
+__global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_t *data, const LLConsts k,
+                                         int poisson, const double *lg_sum, double *ll) {
     __shared__ double ws[32];
     const int r = blockIdx.x;
-    const float sc = (float)scale, ra = (float)ratio;
-    const float lsc = (float)log(scale), lra = (float)log(ratio);
     const float *y = yhat + (size_t)r * N;
     double acc = 0.0;
     if ((N & 3) == 0) {
@@ -226,15 +224,15 @@ __global__ void surrogate_loglike_kernel(const float *yhat, int N, const uint32_
         for (int i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
             const float4 v = __ldg(y4 + i);
             const uint4 d = __ldg(d4 + i);
-            float t = surrogate_ll_term(v.x, d.x, sc, lsc, ra, lra, poisson);
-            t += surrogate_ll_term(v.y, d.y, sc, lsc, ra, lra, poisson);
-            t += surrogate_ll_term(v.z, d.z, sc, lsc, ra, lra, poisson);
-            t += surrogate_ll_term(v.w, d.w, sc, lsc, ra, lra, poisson);
+            float t = surrogate_ll_term(v.x, d.x, k, poisson);
+            t += surrogate_ll_term(v.y, d.y, k, poisson);
+            t += surrogate_ll_term(v.z, d.z, k, poisson);
+            t += surrogate_ll_term(v.w, d.w, k, poisson);
             acc += (double)t;
         }
     } else {
         for (int i = threadIdx.x; i < N; i += blockDim.x)
-            acc += (double)surrogate_ll_term(__ldg(y + i), __ldg(data + i), sc, lsc, ra, lra, poisson);
+            acc += (double)surrogate_ll_term(__ldg(y + i), __ldg(data + i), k, poisson);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -580,7 +578,7 @@ pcmd_status pcmd_mlp_loglike(pcmd_mlp *mlp, int B, const uint32_t *d_data_hess, 
     if (!(scale > 0.0) || !(ratio > 0.0)) return PCMD_ERR_ARG;
     const int N = mlp->dims[mlp->n_layers];
     MCK(data_lgamma_sum(mlp, d_data_hess, N));
-    surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, N, d_data_hess, scale, ratio, mlp->poisson,
+    surrogate_loglike_kernel<<<B, 256, 0, mlp->st>>>(mlp->yhat.p, N, d_data_hess, ll_consts(scale, ratio), mlp->poisson,
                                                      mlp->ll.p + mlp->max_batch, mlp->ll.p);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(h_ll, mlp->ll.p, sizeof(double) * B, cudaMemcpyDeviceToHost, mlp->st));
@@ -612,10 +610,7 @@ pcmd_status pcmd_mlp_forward_loglike(pcmd_mlp *mlp, const float *theta, int on_d
             g.ll_part = mlp->ll_part.p;
             g.ll_ld = mlp->ll_ld;
             g.ll_poisson = mlp->poisson;
-            g.ll_sc = (float)scale;
-            g.ll_lsc = (float)std::log(scale);
-            g.ll_ra = (float)ratio;
-            g.ll_lra = (float)std::log(ratio);
+            g.llk = ll_consts(scale, ratio);
             MCK(launch_gemm_bf16(mlp->x[l].p, K, mlp->L[l].wb.p, K, g, kEpiPoissonLL, mlp->st));
         }
     }

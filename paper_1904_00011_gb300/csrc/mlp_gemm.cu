@@ -374,17 +374,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
                         for (int j = 0; j < 8; ++j) {
                             const float4 bb = __ldg(b4 + j);
                             const uint4 dd = __ldg(d4 + j);
-                            sum += surrogate_ll_term(v[4 * j] + bb.x, dd.x, g.ll_sc, g.ll_lsc, g.ll_ra, g.ll_lra, g.ll_poisson);
-                            sum += surrogate_ll_term(v[4 * j + 1] + bb.y, dd.y, g.ll_sc, g.ll_lsc, g.ll_ra, g.ll_lra, g.ll_poisson);
-                            sum += surrogate_ll_term(v[4 * j + 2] + bb.z, dd.z, g.ll_sc, g.ll_lsc, g.ll_ra, g.ll_lra, g.ll_poisson);
-                            sum += surrogate_ll_term(v[4 * j + 3] + bb.w, dd.w, g.ll_sc, g.ll_lsc, g.ll_ra, g.ll_lra, g.ll_poisson);
+                            sum += surrogate_ll_term(v[4 * j] + bb.x, dd.x, g.llk, g.ll_poisson);
+                            sum += surrogate_ll_term(v[4 * j + 1] + bb.y, dd.y, g.llk, g.ll_poisson);
+                            sum += surrogate_ll_term(v[4 * j + 2] + bb.z, dd.z, g.llk, g.ll_poisson);
+                            sum += surrogate_ll_term(v[4 * j + 3] + bb.w, dd.w, g.llk, g.ll_poisson);
                         }
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
                             if (col0 + j < g.n)
                                 sum += surrogate_ll_term(v[j] + __ldg(g.bias + col0 + j), __ldg(g.ll_data + col0 + j),
-                                                         g.ll_sc, g.ll_lsc, g.ll_ra, g.ll_lra, g.ll_poisson);
+                                                         g.llk, g.ll_poisson);
                     }
                     ll_acc += (double)sum;
                     continue;

@@ -1,6 +1,7 @@
 // Internal declarations of the surrogate MLP kernels.
 #pragma once
 #include <stdint.h>
+#include <cmath>
 #include <cuda_runtime.h>
 
 namespace pcmd {
@@ -13,6 +14,22 @@ enum GemmEpilogue : int {
     kEpiBiasBf16 = 3,      // C (BF16) = D + bias[n]
     kEpiPoissonLL = 4,     // no C: per (row, 64-column block) sums of the surrogate likelihood terms
 };
+
+// Constants of the surrogate likelihood of one call: model counts = rate * scale, floored at
+// 1/2, times ratio = N_d / N_m.
+struct LLConsts {
+    float c1, c0;      // ln(scale * ratio), ln(1/2) + ln(ratio)
+    float sc, ra;      // scale, ratio (the ln(1 + m) convention)
+};
+
+__host__ inline LLConsts ll_consts(double scale, double ratio) {
+    LLConsts k;
+    k.c1 = (float)(std::log(scale) + std::log(ratio));
+    k.c0 = (float)(std::log(0.5) + std::log(ratio));
+    k.sc = (float)scale;
+    k.ra = (float)ratio;
+    return k;
+}
 
 // Output tiles are 128 x kGemmTileN; the likelihood epilogue leaves kGemmLlBlocks partial sums
 // per row and tile (one per epilogue warp's column block).
@@ -31,23 +48,20 @@ struct GemmArgs {                 // every field has a default: an unset pointer
     const uint32_t *ll_data = nullptr;
     double *ll_part = nullptr;
     int ll_ld = 0, ll_poisson = 1;
-    float ll_sc = 1.0f, ll_lsc = 0.0f, ll_ra = 1.0f, ll_lra = 0.0f;
+    LLConsts llk = {0.0f, -0.69314718f, 1.0f, 1.0f};
 };
 
-// One bin of the surrogate Poisson likelihood: the log-rate mode reads y as ln(rate), so
-// ln mh = max(y + ln scale, ln 1/2) + ln ratio needs no logarithm; the other mode reads y as
-// ln(1 + rate).  mh = max(rate * scale, 1/2) * ratio; the term is d ln mh - mh.
-__device__ __forceinline__ float surrogate_ll_term(float y, uint32_t d, float sc, float lsc, float ra,
-                                                   float lra, int poisson) {
-    float mh, lmh;
+
+// One bin of the surrogate Poisson likelihood, d ln mh - mh.  The log-rate output y gives
+// ln mh = u = max(y + ln scale, ln 1/2) + ln ratio and mh = e^u (no logarithm); the ln(1 + m)
+// output gives mh = max(expm1(y) scale, 1/2) ratio.
+__device__ __forceinline__ float surrogate_ll_term(float y, uint32_t d, const LLConsts &k, int poisson) {
     if (poisson) {
-        mh = fmaxf(__expf(y) * sc, 0.5f) * ra;
-        lmh = fmaxf(y + lsc, -0.69314718f) + lra;
-    } else {
-        mh = fmaxf(expm1f(y) * sc, 0.5f) * ra;
-        lmh = logf(mh);
+        const float u = fmaxf(y + k.c1, k.c0);
+        return fmaf((float)d, u, -__expf(u));
     }
-    return (float)d * lmh - mh;
+    const float mh = fmaxf(expm1f(y) * k.sc, 0.5f) * k.ra;
+    return (float)d * logf(mh) - mh;
 }
 
 // Launch C = A . B^T (both operands K-major BF16, row strides lda / ldb elements, multiples
