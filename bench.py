@@ -36,7 +36,7 @@ WORKLOAD = ("plain full model: 256x256, 2 bands, 7 SFH x 7 [Fe/H] x 300 masses (
 METRIC = "model pixels/s (plain full model, one likelihood evaluation per step)"
 # Each step evaluates a new parameter point (a sampler-like random walk) with a new RNG set id.
 PEAK_ISSUE_PER_SM_CLK = 128          # 4 schedulers x 32 lanes: thread-instructions per clock
-OPS_PER_INV_DRAW = 6.0               # 1/8 Philox4x32-10 block (40 instr) + 16-bit compare
+OPS_PER_INV_DRAW = 3.5               # 1/16 Philox4x32-10 block (40 instr) + one byte compare
 OPS_PER_PTRS_DRAW = 60.0             # 1/2 Philox block + ~40 FP32 ops of the squeeze test
 
 
@@ -190,6 +190,32 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------------------
 # the GB300 arm
 # ---------------------------------------------------------------------------------------
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12   # FMA lanes x 2 FLOP x max SM clock
+
+
+def hess_roofline(hess_ms: float, n_bands: int, npix: int, psf: int, nbins: int) -> dict:
+    """PSF / noise / magnitude / Hess kernel: 2 KS^2 FLOP per pixel and band (the stencil) against
+    the FP32 FMA peak, and its algorithmic bytes (raw image read once, histogram flush) against
+    the measured HBM copy bandwidth."""
+    s = hess_ms / 1e3
+    flop = 2.0 * psf * psf * n_bands * npix
+    byts = 4.0 * n_bands * npix + 4.0 * nbins
+    hbm = _measured_peak("hbm_gbs", 6800.0)
+    return {"kernel": "hess_kernel<%d,%d>" % (n_bands, psf), "avg_launch_ms": hess_ms,
+            "fp32": {"bound": "fp32", "achieved": flop / s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flop / s / 1e12 / FP32_PEAK_TFLOPS,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
+            "hbm": {"bound": "hbm", "achieved": byts / s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": byts / s / 1e9 / hbm, "bytes_per_launch": byts}}
+
+
+def issue_roofline(instr: float, seconds: float, what: str) -> dict:
+    peak = 152 * PEAK_ISSUE_PER_SM_CLK * 2070e6 / 1e12
+    a = instr / seconds / 1e12
+    return {"bound": "alu", "achieved": a, "peak": peak, "unit": "Tinstr/s", "frac": a / peak,
+            "algorithmic": what, "peak_basis": "152 SMs x 128 issue slots/clk x 2070 MHz"}
+
+
 def algorithmic_ops(sim, params):
     lam, _, _ = sim.tables(params)
     inv = int(((lam > 0) & (lam < 10)).sum())
@@ -328,6 +354,9 @@ def run_gb300(args, world, rank, local):
                      "algorithmic": "%g instr/pixel = %d inversion draws x %g + %d PTRS draws x %g"
                                     % (ops, n_inv, OPS_PER_INV_DRAW, n_ptrs, OPS_PER_PTRS_DRAW),
                      "peak_basis": "152 SMs x 128 issue slots/clk x 2070 MHz (issue-slot roofline)"},
+        "secondary_rooflines": {"hess": hess_roofline(kt["hess"][0] / max(1, kt["hess"][1]), w.n_bands,
+                                                      npix, 25 if w.psf is not None else 0,
+                                                      w.hess_nx * w.hess_ny)},
         "kernel_ms_per_step": {k: ms / args.steps for k, (ms, c) in kt.items() if c},
         # the table builder's timer brackets its three kernels (count, scan, write)
         "gpu_launches": int(round(sum(c * (3 if k == "tables" else 1) for k, (ms, c) in kt.items()))),
@@ -378,11 +407,20 @@ def run_batched(sim_plain, P, W, torch):
     sim.profile(False)
     step = statistics.median(t)
     pix = sum(n * n for n in w.n_ims)
+    instr = 0.0
+    for p_, n_ in zip(w.params, w.n_ims):
+        ops, _, _ = algorithmic_ops(sim, p_)
+        instr += ops * n_ * n_
+    graph_ms = kt["graph"][0] / max(1, kt["graph"][1])
     return {"workload": "512 sets, images 128..512 (step 16), log10 Npix U[1,6], dmod U[22,26], "
                         "log E(B-V) U[-1,0], 200-point isochrone, Poisson likelihood",
             "evals_per_s": w.n_sets / step, "model_pixels_per_s": pix / step, "ms_per_batch": 1e3 * step,
-            "graph_ms_per_batch": kt["graph"][0] / max(1, kt["graph"][1]),
-            "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
+            "graph_ms_per_batch": graph_ms,
+            "launch": {k: tuned[k] for k in ("block", "split", "chunk")},
+            "roofline": issue_roofline(instr, graph_ms / 1e3,
+                                       "%.3g instr per batch: inversion draws x %g + PTRS draws x %g "
+                                       "(draw, noise, magnitudes and histogram in one graph replay)"
+                                       % (instr, OPS_PER_INV_DRAW, OPS_PER_PTRS_DRAW))}
 
 
 def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 1024):
@@ -410,13 +448,19 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 102
     inv = int(((lam > 0) & (lam < 10)).sum())
     ptrs = int((lam >= 10).sum())
     draw_ms = kt["draw"][0] / max(1, kt["draw"][1])
+    instr = (inv * OPS_PER_INV_DRAW + ptrs * OPS_PER_PTRS_DRAW) * n * n
     return {"workload": "%dx%d, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
                         "dust, 25x25 PSF, noise, Kahan sums" % (n, n, log_npix),
             "model_pixels_per_s": n * n / dt, "evals_per_s": 1.0 / dt, "ms_per_eval": 1e3 * dt,
             "draw_ms": draw_ms, "hess_ms": kt["hess"][0] / max(1, kt["hess"][1]),
             "entries_per_pixel": inv + ptrs, "ptrs_entries_per_pixel": ptrs,
             "launch": {k: tuned[k] for k in ("block", "split", "chunk")},
-            "draws_per_s": (inv + ptrs) * n * n / (draw_ms / 1e3)}
+            "draws_per_s": (inv + ptrs) * n * n / (draw_ms / 1e3),
+            "roofline": issue_roofline(instr, draw_ms / 1e3,
+                                       "%d inversion draws x %g + %d PTRS draws x %g per pixel"
+                                       % (inv, OPS_PER_INV_DRAW, ptrs, OPS_PER_PTRS_DRAW)),
+            "hess_roofline": hess_roofline(kt["hess"][0] / max(1, kt["hess"][1]), 3, n * n, 25,
+                                           w.hess_nx * w.hess_ny)}
 
 
 def run_surrogate(torch, n_sims: int = 262144, infer_batch: int = 4096, reps: int = 10):
