@@ -51,7 +51,7 @@ def _args():
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     ap.add_argument("--surrogate-sims", type=int, default=262144,
                     help="simulations the surrogate is trained on in the extras")
-    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp"],
+    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp", "lmax"],
                     help="run one extra section alone and print its JSON (profiling runs)")
     ap.add_argument("--large-n-im", type=int, default=1024, help="image edge of the large-Npix line")
     return ap.parse_args()
@@ -317,6 +317,7 @@ def run_gb300(args, world, rank, local):
     if args.extras and rank == 0:
         extras["batched"] = run_batched(sim, P, W, torch)
         extras["large_npix"] = run_large(P, W, torch, n_im=args.large_n_im)
+        extras["lmax"] = run_lmax(P, W, torch)
         extras["surrogate"] = run_surrogate(torch, n_sims=args.surrogate_sims)
 
     if rank != 0:
@@ -522,6 +523,29 @@ def run_surrogate(torch, n_sims: int = 262144, infer_batch: int = 4096, reps: in
                           "judge": "exact simulator, 256x256 images, Poisson likelihood"}}
 
 
+def run_lmax(P, W, torch, reps: int = 100):
+    """Appendix A workload: the best fit of the full model (here the mock's own parameters)
+    recomputed `reps` times with distinct RNG set ids in one batched call; L_max = median."""
+    from paper_1904_00011_gb300 import sampler as S
+    w = W.full()
+    n = w.n_im
+    sim = P.Simulator(w, max_sets=reps)
+    sim.simulate(w.params, [n], 3_000_000)
+    h, m, _, _ = sim.hess(1, [n])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    p = w.params[0]
+    sim.evaluate([p] * reps, [n] * reps, mock, mom, n * n, W.LL_PAPER, first_set_id=10)
+    t0 = time.perf_counter()
+    ll = sim.evaluate([p] * reps, [n] * reps, mock, mom, n * n, W.LL_PAPER, first_set_id=1000)
+    dt = time.perf_counter() - t0
+    return {"workload": "full model 256x256, best fit recomputed %d times in one batched call "
+                        "(Appendix A ceiling)" % reps,
+            "ms": 1e3 * dt, "evals_per_s": reps / dt, "model_pixels_per_s": reps * n * n / dt,
+            "l_max": S.lmax_from_repeats(ll), "ll_std": float(np.std(ll)),
+            "ll_min": float(np.min(ll)), "ll_max": float(np.max(ll))}
+
+
 def run_mlp(torch, batch: int = 4096, reps: int = 20):
     """Surrogate network alone (random init, no training): the 5-layer inference forward and the
     fused forward + likelihood on a batch of parameter points; GEMM roofline."""
@@ -584,6 +608,8 @@ def main():
             out = run_batched(None, P, W, torch)
         elif args.only == "mlp":
             out = run_mlp(torch)
+        elif args.only == "lmax":
+            out = run_lmax(P, W, torch)
         else:
             out = run_surrogate(torch, n_sims=args.surrogate_sims)
         print(json.dumps({"section": args.only, **out}), flush=True)

@@ -13,7 +13,7 @@ statistic reported is the number of exact likelihood calls per accepted replacem
 from __future__ import annotations
 
 import dataclasses
-from typing import Callable, Optional
+from typing import Callable, Optional, Sequence
 
 import numpy as np
 
@@ -25,6 +25,9 @@ class RunStats:
     surrogate_calls: int
     log_evidence: float
     l_min_final: float
+    dead_theta: Optional[np.ndarray] = None     # [iterations][d] replaced (dead) points
+    dead_log_l: Optional[np.ndarray] = None     # their log-likelihoods
+    dead_log_x: Optional[np.ndarray] = None     # log prior volume at each death
 
     @property
     def exact_calls_per_replacement(self) -> float:
@@ -47,11 +50,15 @@ def nested_sampling(exact_ll: Callable[[np.ndarray], np.ndarray],
     log_z = -np.inf
     log_x = 0.0
     it = 0
+    d_theta, d_ll, d_lx = [], [], []
     for it in range(n_iter):
         worst = int(np.argmin(live_ll))
         l_min = float(live_ll[worst])
         log_w = log_x + np.log1p(-np.exp(-1.0 / n_live))
         log_z = np.logaddexp(log_z, log_w + l_min)
+        d_theta.append(np.array(live[worst]))
+        d_ll.append(l_min)
+        d_lx.append(log_x)
         log_x -= 1.0 / n_live
         new = None
         while new is None and calls < max_exact:
@@ -71,4 +78,21 @@ def nested_sampling(exact_ll: Callable[[np.ndarray], np.ndarray],
         if new is None:
             break
         live[worst], live_ll[worst] = new
-    return RunStats(it + 1, calls, s_calls, float(log_z), float(np.min(live_ll)))
+    return RunStats(it + 1, calls, s_calls, float(log_z), float(np.min(live_ll)),
+                    np.array(d_theta), np.array(d_ll), np.array(d_lx))
+
+
+def lmax_from_repeats(log_l_repeats: Sequence[float]) -> float:
+    """Appendix A: the ceiling is the median of the best fit's recomputed log-likelihoods."""
+    return float(np.median(np.asarray(log_l_repeats, np.float64)))
+
+
+def capped_weights(dead_log_l: np.ndarray, dead_log_x: np.ndarray, n_live: int, l_max: float):
+    """Recompute the nested-sampling weights with every log-likelihood capped at l_max: dead point
+    i (at log prior volume log X_i) gets log w_i = log(X_i - X_{i+1}) + min(L_i, L_max), with
+    X_{i+1} = X_i e^{-1/n_live}.  Returns (normalised posterior weights, log evidence)."""
+    ll = np.minimum(np.asarray(dead_log_l, np.float64), l_max)
+    log_dx = np.asarray(dead_log_x, np.float64) + np.log1p(-np.exp(-1.0 / n_live))
+    log_w = log_dx + ll
+    log_z = float(np.logaddexp.reduce(log_w)) if log_w.size else -np.inf
+    return np.exp(log_w - log_z), log_z
