@@ -33,7 +33,7 @@ extern "C" {
 #endif
 
 #define PCMD_MAX_BANDS 4
-#define PCMD_MAX_SFH 16
+#define PCMD_MAX_SFH 32
 #define PCMD_MAX_PSF 31
 
 typedef int pcmd_status;
@@ -57,6 +57,11 @@ enum {
 
 /* likelihood modes */
 enum { PCMD_LL_PAPER = 0, PCMD_LL_POISSON = 1 };
+
+/* Initial mass function of the IMF weights (Section 2.2): a single power law dN/dm ~ m^-imf_slope
+ * (Salpeter: 2.35), or Kroupa (2001): slopes 0.3 below 0.08 Msun, 1.3 to 0.5 Msun, 2.3 above,
+ * continuous at the breaks (imf_slope unused). */
+enum { PCMD_IMF_POWER = 0, PCMD_IMF_KROUPA = 1 };
 
 /* Hyper-parameters (Table 2) and isochrones; copied at pcmd_create. */
 typedef struct {
@@ -83,6 +88,7 @@ typedef struct {
     uint64_t seed;               /* Philox key */
     unsigned flags;              /* PCMD_FLAG_* */
     void *stream;                /* cudaStream_t for all work of this context */
+    int imf;                     /* PCMD_IMF_POWER (default) or PCMD_IMF_KROUPA */
 } pcmd_config;
 
 /* Free parameters of one model (Table 1): S5 non-parametric SFH, M2/M3 Gaussian MDF
@@ -177,6 +183,20 @@ enum { PCMD_K_DRAW = 0, PCMD_K_HESS = 1, PCMD_K_FINALIZE = 2, PCMD_K_LOGLIKE = 3
        PCMD_K_GRAPH = 4, PCMD_K_GEMM = 5, PCMD_K_TABLES = 6, PCMD_KERNEL_KINDS = 8 };
 pcmd_status pcmd_profile(pcmd_ctx *ctx, int enable);
 pcmd_status pcmd_kernel_times(pcmd_ctx *ctx, double *h_ms, int *h_count);
+
+/* Parametric star-formation histories (Section 2.2 S1-S4) on an age grid: fills h_log_sfh[n_bins]
+ * with log10 stars per pixel formed in each bin, summing to Npix, for use as pcmd_params.log_sfh.
+ * Bins are [log_age_edges[j], log_age_edges[j+1]) in log10 years (n_bins + 1 increasing edges);
+ * star formation starts at the oldest edge T0 (formation time t = T0 - age).
+ *   PCMD_SFH_SSP          theta = {log10 Npix, log10 age}: all stars in the bin holding the age
+ *   PCMD_SFH_CONSTANT     theta = {log10 Npix}: constant rate, bin mass ~ its width in years
+ *   PCMD_SFH_TAU          theta = {log10 Npix, tau [Gyr]}: rate ~ exp(-t / tau)
+ *   PCMD_SFH_DELAYED_TAU  theta = {log10 Npix, tau [Gyr]}: rate ~ t exp(-t / tau)
+ * Bin masses are the closed-form integrals of the rate over each bin.  Empty bins get -30 (no
+ * stars).  Host only; PCMD_ERR_ARG on a bad model, theta, edge list or an all-empty grid. */
+enum { PCMD_SFH_SSP = 1, PCMD_SFH_CONSTANT = 2, PCMD_SFH_TAU = 3, PCMD_SFH_DELAYED_TAU = 4 };
+pcmd_status pcmd_sfh_bins(int model, const double *theta, int n_theta, int n_bins,
+                          const double *log_age_edges, double *h_log_sfh);
 
 /* Number of isochrone points P = n_ages * n_feh * n_mass of the context. */
 int pcmd_n_points(const pcmd_ctx *ctx);

@@ -81,7 +81,7 @@ def lib():
                                   ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.POINTER(ctypes.c_int)]
             L.or_draw.restype = ctypes.c_uint32
-            L.or_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p, ctypes.c_double,
+            L.or_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p, ctypes.c_double, ctypes.c_int,
                                      f64p, f64p, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, f64p]
             L.or_weights.restype = None
@@ -182,7 +182,8 @@ def weights(w, params) -> np.ndarray:
     if sfh.size != na:
         raise ValueError("one SFH value per age bin required")
     out = np.zeros((na, nf, nm))
-    lib().or_weights(na, nf, nm, _p(mass, ctypes.c_double), w.imf_slope, _p(feh, ctypes.c_double),
+    lib().or_weights(na, nf, nm, _p(mass, ctypes.c_double), w.imf_slope, int(getattr(w, "imf", 0)),
+                     _p(feh, ctypes.c_double),
                      _p(sfh, ctypes.c_double), params.feh_mean, params.feh_sigma, w.mdf_cut,
                      _p(out, ctypes.c_double))
     return out
@@ -339,3 +340,40 @@ def loglike(model_hist, model_moments, n_m, data_hist, data_moments, n_d,
     m_m = model_moments[1] / model_moments[2]
     cterm = -((c_d - c_m) ** 2) / (2 * 0.05 ** 2) - ((m_d - m_m) ** 2) / (2 * 0.05 ** 2)
     return float(np.sum(g) + cterm)
+
+
+# ----------------------------------------------------------------------------------------
+# parametric star-formation histories (Section 2.2, S1-S4)
+# ----------------------------------------------------------------------------------------
+
+SFH_SSP, SFH_CONSTANT, SFH_TAU, SFH_DELAYED_TAU = 1, 2, 3, 4
+
+
+def sfh_bins(model: int, theta, log_age_edges) -> np.ndarray:
+    """log10 stars per pixel formed in each age bin [e_j, e_j+1) (log10 years), summing to
+    Npix = 10^theta[0].  Star formation starts at the oldest edge T0; a star of age a formed at
+    t = T0 - a.  S1: all stars in the bin holding age 10^theta[1]; S2: constant rate; S3: rate
+    exp(-t/tau); S4: rate t exp(-t/tau), tau = theta[1] Gyr.  The mass of a bin is the integral
+    of the rate over its formation times, evaluated here in closed form (FP64); empty bins -30."""
+    e = np.asarray(log_age_edges, np.float64)
+    ages = 10.0 ** e
+    t0 = ages[-1]
+    n = e.size - 1
+    mass = np.zeros(n)
+    if model == SFH_SSP:
+        j = np.nonzero((theta[1] >= e[:-1]) & (theta[1] < e[1:]))[0]
+        mass[j[0]] = 1.0
+    elif model == SFH_CONSTANT:
+        mass = ages[1:] - ages[:-1]
+    else:
+        tau = theta[1] * 1e9
+        early, late = t0 - ages[1:], t0 - ages[:-1]      # formation-time bounds of each bin
+        if model == SFH_TAU:
+            prim = lambda t: -tau * np.exp(-t / tau)                 # noqa: E731
+        else:
+            prim = lambda t: -tau * np.exp(-t / tau) * (t + tau)     # noqa: E731
+        mass = prim(late) - prim(early)
+    v = 10.0 ** theta[0] * mass / mass.sum()
+    with np.errstate(divide="ignore"):
+        out = np.where(v > 0, np.log10(np.where(v > 0, v, 1.0)), -30.0)
+    return np.maximum(out, -30.0)

@@ -289,7 +289,27 @@ uint32_t or_draw(float lam, uint64_t seed, uint32_t pix, uint32_t i, uint32_t se
  *           renormalised (M2/M3); feh_sigma <= 0 puts all weight on the nearest grid point
  *  IMF_i  = integral of m^-slope over the mass cell of point i (cells bounded by geometric
  *           midpoints), normalised over the isochrone (Salpeter slope 2.35).  */
-void or_weights(int n_ages, int n_feh, int n_mass, const double *mass, double slope,
+/* Kroupa (2001) IMF over [a, b]: dN/dm proportional to m^-0.3 below 0.08 Msun, m^-1.3 from 0.08 to
+ * 0.5 Msun and m^-2.3 above, the three pieces joined continuously (factors 1, 0.08, 0.04). */
+static double or_kroupa(double a, double b)
+{
+    const double edge[4] = {0.0, 0.08, 0.5, 1.0e300};
+    const double alpha[3] = {0.3, 1.3, 2.3};
+    const double join[3] = {1.0, 0.08, 0.04};
+    double total = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        double x0 = a > edge[s] ? a : edge[s];
+        double x1 = b < edge[s + 1] ? b : edge[s + 1];
+        if (x1 <= x0) continue;
+        double p = 1.0 - alpha[s];
+        double v = pow(x1, p) - pow(x0, p);
+        v = v / p;
+        total = total + join[s] * v;
+    }
+    return total;
+}
+
+void or_weights(int n_ages, int n_feh, int n_mass, const double *mass, double slope, int kroupa,
                 const double *feh_grid, const double *log_sfh, double feh_mean,
                 double feh_sigma, double mdf_cut, double *lam_out)
 {
@@ -332,7 +352,9 @@ void or_weights(int n_ages, int n_feh, int n_mass, const double *mass, double sl
                 double a1 = 1.0 - slope;
                 for (int i = 0; i < n_mass; ++i) {
                     double w;
-                    if (a1 != 0.0) {
+                    if (kroupa) {
+                        w = or_kroupa(edge[i], edge[i + 1]);
+                    } else if (a1 != 0.0) {
                         w = pow(edge[i + 1], a1) - pow(edge[i], a1);
                         w = w / a1;
                     } else {

@@ -21,12 +21,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpcmd.so")
 
 PCMD_MAX_BANDS = 4
-PCMD_MAX_SFH = 16
+PCMD_MAX_SFH = 32
 
 STATUS = {0: "PCMD_OK", 1: "PCMD_ERR_ARG", 2: "PCMD_ERR_CUDA", 3: "PCMD_ERR_OOM",
           4: "PCMD_ERR_SAMPLER_LIMIT", 5: "PCMD_ERR_STATE", 6: "PCMD_ERR_TIMEOUT"}
 PCMD_FLAG_DUST, PCMD_FLAG_NOISE, PCMD_FLAG_KAHAN, PCMD_FLAG_SIGMA_SQRTSUM = 1, 2, 4, 8
 PCMD_LL_PAPER, PCMD_LL_POISSON = 0, 1
+PCMD_IMF_POWER, PCMD_IMF_KROUPA = 0, 1
+PCMD_SFH_SSP, PCMD_SFH_CONSTANT, PCMD_SFH_TAU, PCMD_SFH_DELAYED_TAU = 1, 2, 3, 4
 
 
 class PcmdError(RuntimeError):
@@ -51,6 +53,7 @@ class pcmd_config(ctypes.Structure):
         ("hess_width", ctypes.c_double),
         ("max_im", ctypes.c_int), ("max_sets", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
+        ("imf", ctypes.c_int),
     ]
 
 
@@ -97,6 +100,8 @@ def lib():
         L.pcmd_n_points.argtypes = [vp]
         L.pcmd_set_launch.argtypes = [vp, i, i, i]
         L.pcmd_get_tables.argtypes = [vp, parp, vp, vp, vp]
+        L.pcmd_sfh_bins.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.pcmd_sfh_bins.restype = ctypes.c_int
         L.pcmd_counts.argtypes = [vp, parp, i, u32, u32, u32, vp]
         L.pcmd_bin_mags.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
         L.pcmd_profile.argtypes = [vp, i]
@@ -179,6 +184,17 @@ def pcmd_evaluate(ctx, params, n_sets, n_im, first_set_id, d_mock_hess, mock_mom
                   mode, h_ll) -> None:
     _check(lib().pcmd_evaluate(ctx, params, n_sets, n_im, first_set_id, d_mock_hess,
                                _dptr(mock_moments), mock_n_pix, mode, _dptr(h_ll)), "pcmd_evaluate", ctx)
+
+
+def sfh_bins(model: int, theta, log_age_edges) -> np.ndarray:
+    """Parametric SFH (Section 2.2 S1-S4) as log10 stars per age bin (host computation in the
+    library; see pcmd_sfh_bins)."""
+    th = np.ascontiguousarray(theta, np.float64)
+    ed = np.ascontiguousarray(log_age_edges, np.float64)
+    out = np.zeros(ed.size - 1, np.float64)
+    _check(lib().pcmd_sfh_bins(int(model), th.ctypes.data, th.size, out.size, ed.ctypes.data,
+                               out.ctypes.data), "pcmd_sfh_bins")
+    return out
 
 
 def pcmd_sync(ctx) -> None:
@@ -271,6 +287,7 @@ class Simulator:
         cfg.mass = dbl(iso.mass)
         cfg.abs_mag = dbl(iso.abs_mag[..., :w.n_bands])
         cfg.imf_slope = w.imf_slope
+        cfg.imf = int(getattr(w, "imf", PCMD_IMF_POWER))
         for b in range(PCMD_MAX_BANDS):
             cfg.exptime[b] = w.exptime[b]
             cfg.zeropoint[b] = w.zeropoint[b]

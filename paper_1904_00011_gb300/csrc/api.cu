@@ -389,6 +389,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
     if ((long long)c.n_ages * c.n_feh * c.n_mass > (1LL << 24)) return PCMD_ERR_ARG;
     if (!c.feh_grid || !c.mass || !c.abs_mag) return PCMD_ERR_ARG;
     if (!is_fin(c.imf_slope) || !is_fin(c.f_dust) || c.f_dust < 0.0 || c.f_dust > 1.0) return PCMD_ERR_ARG;
+    if (c.imf != PCMD_IMF_POWER && c.imf != PCMD_IMF_KROUPA) return PCMD_ERR_ARG;
     if (!is_fin(c.mdf_cut) || c.mdf_cut < 0.0 || c.mdf_cut >= 1.0) return PCMD_ERR_ARG;
     if (c.hess_nx < 1 || c.hess_ny < 1 || (long long)c.hess_nx * c.hess_ny > 40000) return PCMD_ERR_ARG;
     if (!(c.hess_width > 0.0) || !is_fin(c.hess_c_lo) || !is_fin(c.hess_m_lo)) return PCMD_ERR_ARG;
@@ -419,6 +420,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
     m.mass.assign(c.mass, c.mass + P);
     m.abs_mag.assign(c.abs_mag, c.abs_mag + P * c.n_bands);
     m.imf_slope = c.imf_slope;
+    m.imf_kind = c.imf;
     m.mdf_cut = c.mdf_cut;
     m.f_dust = c.f_dust;
     m.dust = (c.flags & PCMD_FLAG_DUST) != 0;
@@ -799,6 +801,11 @@ pcmd_status pcmd_evaluate(pcmd_ctx *ctx, const pcmd_params *h_params, int n_sets
     rc = pcmd_sync(ctx);
     std::memcpy(h_ll, ctx->h_ll.p, sizeof(double) * n_sets);
     return rc;
+}
+
+pcmd_status pcmd_sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *log_age_edges,
+                          double *h_log_sfh) {
+    return sfh_bins(model, theta, n_theta, n_bins, log_age_edges, h_log_sfh) ? PCMD_OK : PCMD_ERR_ARG;
 }
 
 pcmd_status pcmd_get_tables(pcmd_ctx *ctx, const pcmd_params *h_params, float *h_lam, float *h_flux,

@@ -11,8 +11,28 @@
 #include "tables.h"
 
 #include <cmath>
+#include <vector>
 
 namespace pcmd {
+
+// Kroupa (2001) IMF integrated over [a, b]: xi(m) = k_s m^-alpha_s on the segments
+// [0, 0.08), [0.08, 0.5), [0.5, inf) with alpha = 0.3, 1.3, 2.3 and k = 1, 0.08, 0.04 (continuous).
+static double kroupa_cell(double a, double b) {
+    const double lo[3] = {0.0, 0.08, 0.5}, hi[3] = {0.08, 0.5, 1.0e300};
+    const double alpha[3] = {0.3, 1.3, 2.3}, k[3] = {1.0, 0.08, 0.04};
+    double s = 0.0;
+    for (int g = 0; g < 3; ++g) {
+        const double x0 = a > lo[g] ? a : lo[g];
+        const double x1 = b < hi[g] ? b : hi[g];
+        if (x1 > x0) {
+            const double e = 1.0 - alpha[g];
+            double t = std::pow(x1, e) - std::pow(x0, e);
+            t = t / e;
+            s = s + k[g] * t;
+        }
+    }
+    return s;
+}
 
 void Model::build_imf() {
     imf.assign((size_t)n_ages * n_feh * n_mass, 0.0);
@@ -31,7 +51,9 @@ void Model::build_imf() {
                 const double a1 = 1.0 - imf_slope;
                 for (int i = 0; i < n_mass; ++i) {
                     double w;
-                    if (a1 != 0.0) {
+                    if (imf_kind == PCMD_IMF_KROUPA) {
+                        w = kroupa_cell(edge[i], edge[i + 1]);
+                    } else if (a1 != 0.0) {
                         w = std::pow(edge[i + 1], a1) - std::pow(edge[i], a1);
                         w = w / a1;
                     } else {
@@ -95,6 +117,50 @@ void stirlerr_table(float out[16]) {
         s = s - 0.5 * std::log(2.0 * M_PI);
         out[k] = (float)s;
     }
+}
+
+// Section 2.2 S1-S4.  Ages a in years, formation times t = T0 - a with T0 the oldest edge; the
+// mass formed in bin [a_lo, a_hi) is the integral of the rate over t in [T0 - a_hi, T0 - a_lo].
+bool sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *edges, double *out) {
+    if (!theta || !edges || !out || n_bins < 1 || n_bins > PCMD_MAX_SFH || n_theta < 1) return false;
+    for (int j = 0; j <= n_bins; ++j)
+        if (!std::isfinite(edges[j]) || (j > 0 && !(edges[j] > edges[j - 1]))) return false;
+    for (int i = 0; i < n_theta; ++i)
+        if (!std::isfinite(theta[i])) return false;
+    const double npix = std::pow(10.0, theta[0]);
+    const double T0 = std::pow(10.0, edges[n_bins]);
+    std::vector<double> m(n_bins, 0.0);
+    if (model == PCMD_SFH_SSP) {
+        if (n_theta < 2) return false;
+        int j0 = -1;
+        for (int j = 0; j < n_bins; ++j)
+            if (theta[1] >= edges[j] && theta[1] < edges[j + 1]) j0 = j;
+        if (j0 < 0) return false;
+        m[j0] = 1.0;
+    } else if (model == PCMD_SFH_CONSTANT) {
+        for (int j = 0; j < n_bins; ++j) m[j] = std::pow(10.0, edges[j + 1]) - std::pow(10.0, edges[j]);
+    } else if (model == PCMD_SFH_TAU || model == PCMD_SFH_DELAYED_TAU) {
+        if (n_theta < 2 || !(theta[1] > 0.0)) return false;
+        const double tau = theta[1] * 1.0e9;
+        for (int j = 0; j < n_bins; ++j) {
+            const double t1 = T0 - std::pow(10.0, edges[j + 1]);   // older edge: earlier time
+            const double t2 = T0 - std::pow(10.0, edges[j]);
+            const double e1 = std::exp(-t1 / tau), e2 = std::exp(-t2 / tau);
+            if (model == PCMD_SFH_TAU) m[j] = tau * (e1 - e2);
+            else m[j] = tau * (e1 * (t1 + tau) - e2 * (t2 + tau));
+        }
+    } else {
+        return false;
+    }
+    double tot = 0.0;
+    for (int j = 0; j < n_bins; ++j) tot += m[j];
+    if (!(tot > 0.0)) return false;
+    for (int j = 0; j < n_bins; ++j) {
+        const double v = npix * (m[j] / tot);
+        out[j] = v > 0.0 ? std::log10(v) : -30.0;
+        if (out[j] < -30.0) out[j] = -30.0;
+    }
+    return true;
 }
 
 }  // namespace pcmd

@@ -18,6 +18,7 @@ struct Model {
     double exptime[kMaxBands] = {1, 1, 1, 1}, zeropoint[kMaxBands] = {0, 0, 0, 0};
     double r_ext[kMaxBands] = {0, 0, 0, 0};
     bool dust = false;
+    int imf_kind = 0;          // PCMD_IMF_POWER / PCMD_IMF_KROUPA
 
     int n_points() const { return n_ages * n_feh * n_mass; }
     void build_imf();
@@ -26,5 +27,7 @@ struct Model {
 };
 
 void stirlerr_table(float out[16]);
+// Parametric SFH on an age grid (PCMD_SFH_*): log10 stars per bin; false on bad input.
+bool sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *edges, double *out);
 
 }  // namespace pcmd

@@ -88,6 +88,7 @@ class Workload:
     params: List[Params]
     n_ims: List[int]
     imf_slope: float = 2.35
+    imf: int = 0                              # 0 power law (imf_slope), 1 Kroupa (2001)
     exptime: Sequence[float] = EXPTIME
     zeropoint: Sequence[float] = ZEROPOINT
     sky: Sequence[float] = (0.0, 0.0, 0.0, 0.0)

@@ -44,9 +44,20 @@ def _flux_close(got, ref, scale):
 
 # ------------------------------------------------------------------------------ tables
 
-@pytest.mark.parametrize("name", ["tiny", "full", "large"])
+def _parametric_full():
+    """The full model with a Kroupa IMF and a delayed-tau SFH (Section 2.2 S4) on its age bins."""
+    import paper_1904_00011_gb300 as P
+    w = W.full()
+    edges = np.array(W._edges(W.FULL_LOG_AGES))
+    sfh = P.sfh_bins(P.PCMD_SFH_DELAYED_TAU, [2.5, 3.0], edges)
+    p = dataclasses.replace(w.params[0], log_sfh=sfh)
+    return dataclasses.replace(w, imf=1, params=[p])
+
+
+@pytest.mark.parametrize("name", ["tiny", "full", "large", "kroupa_tau"])
 def test_tables_match_oracle(name):
-    w = {"tiny": W.tiny, "full": W.full, "large": lambda: W.large(log_npix=6.5)}[name]()
+    w = {"tiny": W.tiny, "full": W.full, "large": lambda: W.large(log_npix=6.5),
+         "kroupa_tau": _parametric_full}[name]()
     s = _sim(w)
     lam, flux, z0 = s.tables(w.params[0])
     lam_o, flux_o, _ = O.tables(w)
@@ -85,6 +96,10 @@ def test_counts_bit_exact_tiny_whole_image():
 def test_counts_bit_exact_full_sampled_pixels():
     w = W.full()
     _counts_case(w, 256, 7, [(0, 96), (33000, 64), (65536 - 70, 70)])
+
+
+def test_counts_bit_exact_kroupa_delayed_tau():
+    _counts_case(_parametric_full(), 256, 9, [(100, 64), (40000, 64)])
 
 
 @pytest.mark.parametrize("log_npix", [4.0, 6.5])
