@@ -51,7 +51,7 @@ def _args():
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     ap.add_argument("--surrogate-sims", type=int, default=262144,
                     help="simulations the surrogate is trained on in the extras")
-    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp", "lmax"],
+    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp", "lmax", "psf_grid"],
                     help="run one extra section alone and print its JSON (profiling runs)")
     ap.add_argument("--large-n-im", type=int, default=1024, help="image edge of the large-Npix line")
     return ap.parse_args()
@@ -318,6 +318,7 @@ def run_gb300(args, world, rank, local):
         extras["batched"] = run_batched(sim, P, W, torch)
         extras["large_npix"] = run_large(P, W, torch, n_im=args.large_n_im)
         extras["lmax"] = run_lmax(P, W, torch)
+        extras["psf_grid"] = run_psf_grid(P, W, torch)
         extras["surrogate"] = run_surrogate(torch, n_sims=args.surrogate_sims)
 
     if rank != 0:
@@ -546,6 +547,32 @@ def run_lmax(P, W, torch, reps: int = 100):
             "ll_min": float(np.min(ll)), "ll_max": float(np.max(ll))}
 
 
+def run_psf_grid(P, W, torch, reps: int = 10):
+    """The full model with the 4x4 grid of sub-pixel-shifted PSFs (Section 2.2): per-evaluation
+    time and the PSF / Hess kernel's rooflines."""
+    w = W.full(psf_grid=True)
+    n = w.n_im
+    sim = P.Simulator(w, max_sets=1)
+    from paper_1904_00011_gb300 import autotune
+    autotune.tune(sim, w.params, [n], reps=2, use_cache=False)
+    sim.simulate(w.params, [n], 4_000_000)
+    h, m, _, _ = sim.hess(1, [n])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=1)
+    sim.profile(True)
+    t0 = time.perf_counter()
+    for i in range(reps):
+        sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=10 + i)
+    dt = (time.perf_counter() - t0) / reps
+    kt = sim.kernel_times()
+    sim.profile(False)
+    hess_ms = kt["hess"][0] / max(1, kt["hess"][1])
+    return {"workload": "full model 256x256 with a 4x4 grid of sub-pixel-shifted 25x25 Moffat PSFs",
+            "ms_per_eval": 1e3 * dt, "model_pixels_per_s": n * n / dt, "hess_ms": hess_ms,
+            "hess_roofline": hess_roofline(hess_ms, w.n_bands, n * n, 25, w.hess_nx * w.hess_ny)}
+
+
 def run_mlp(torch, batch: int = 4096, reps: int = 20):
     """Surrogate network alone (random init, no training): the 5-layer inference forward and the
     fused forward + likelihood on a batch of parameter points; GEMM roofline."""
@@ -610,6 +637,8 @@ def main():
             out = run_mlp(torch)
         elif args.only == "lmax":
             out = run_lmax(P, W, torch)
+        elif args.only == "psf_grid":
+            out = run_psf_grid(P, W, torch)
         else:
             out = run_surrogate(torch, n_sims=args.surrogate_sims)
         print(json.dumps({"section": args.only, **out}), flush=True)

@@ -89,6 +89,10 @@ typedef struct {
     unsigned flags;              /* PCMD_FLAG_* */
     void *stream;                /* cudaStream_t for all work of this context */
     int imf;                     /* PCMD_IMF_POWER (default) or PCMD_IMF_KROUPA */
+    int psf_grid;                /* 0 or 1: one PSF per band; 4: sub-pixel PSFs (Section 2.2): the
+                                  * image is a 4x4 grid of regions, output pixel (y, x) in region
+                                  * (4y/N, 4x/N) (integer division) uses its own kernel, and psf
+                                  * holds [16][n_bands][psf_size][psf_size], region r = 4 ry + rx */
 } pcmd_config;
 
 /* Free parameters of one model (Table 1): S5 non-parametric SFH, M2/M3 Gaussian MDF

@@ -97,6 +97,8 @@ def lib():
             L.or_simulate.restype = ctypes.c_int
             L.or_psf.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f64p, f64p]
             L.or_psf.restype = None
+            L.or_psf_grid.argtypes = L.or_psf.argtypes
+            L.or_psf_grid.restype = None
             L.or_noise_mags.argtypes = [ctypes.c_int, ctypes.c_int, f64p, ctypes.c_int, f64p, f64p,
                                         f64p, ctypes.c_uint32, ctypes.c_uint64, f32p, f32p,
                                         ctypes.POINTER(ctypes.c_uint8), f64p]
@@ -248,15 +250,21 @@ def simulate(w, set_index: int = 0, set_id: Optional[int] = None, pix_begin: int
 
 
 def psf(image: np.ndarray, kernel: np.ndarray, n_im: int) -> np.ndarray:
-    """Periodic PSF convolution per band, FP64."""
+    """Periodic PSF convolution per band, FP64.  kernel [B][S][S], or [16][B][S][S] for the 4x4
+    grid of sub-pixel PSFs (Section 2.2; region (4y/N, 4x/N) uses kernel 4 ry + rx)."""
     nb = image.shape[0]
     out = np.zeros_like(image)
     for b in range(nb):
-        k = np.ascontiguousarray(kernel[b], np.float32)
         src = np.ascontiguousarray(image[b], np.float64)
         dst = np.zeros(n_im * n_im)
-        lib().or_psf(n_im, k.shape[0], _p(k, ctypes.c_float), _p(src, ctypes.c_double),
-                     _p(dst, ctypes.c_double))
+        if kernel.ndim == 4:
+            k = np.ascontiguousarray(kernel[:, b], np.float32)
+            lib().or_psf_grid(n_im, k.shape[-1], _p(k, ctypes.c_float), _p(src, ctypes.c_double),
+                              _p(dst, ctypes.c_double))
+        else:
+            k = np.ascontiguousarray(kernel[b], np.float32)
+            lib().or_psf(n_im, k.shape[0], _p(k, ctypes.c_float), _p(src, ctypes.c_double),
+                         _p(dst, ctypes.c_double))
         out[b] = dst
     return out
 

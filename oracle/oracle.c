@@ -487,6 +487,27 @@ void or_psf(int n_im, int ksize, const float *kernel, const double *in, double *
         }
 }
 
+/* Sub-pixel PSFs (Section 2.2): the image is a 4x4 grid of regions; output pixel (y, x) belongs to
+ * region (4y/n, 4x/n) (integer division) and is convolved (periodically) with that region's
+ * kernel, kernels[(4 ry + rx) * ksize^2 ..]. */
+void or_psf_grid(int n_im, int ksize, const float *kernels, const double *in, double *out)
+{
+    int R = ksize / 2;
+    for (int y = 0; y < n_im; ++y)
+        for (int x = 0; x < n_im; ++x) {
+            const float *kernel = kernels + (size_t)((4 * y / n_im) * 4 + 4 * x / n_im) * ksize * ksize;
+            double s = 0.0;
+            for (int u = 0; u < ksize; ++u) {
+                int yy = ((y + R - u) % n_im + n_im) % n_im;
+                for (int v = 0; v < ksize; ++v) {
+                    int xx = ((x + R - v) % n_im + n_im) % n_im;
+                    s += (double)kernel[u * ksize + v] * in[(size_t)yy * n_im + xx];
+                }
+            }
+            out[(size_t)y * n_im + x] = s;
+        }
+}
+
 /* Photon and sky noise (noise = sqrt(counts), sky subtracted in expectation) and magnitudes.
  * F' = F + sqrt(max(F + sky, 0)) z_b, z from Box-Muller of the pixel's NOISE call for band pair
  * b >> 1 (cos for even b, sin for odd b).  m_b = ZP_b - 2.5 log10(F'_b / t_b) in FP64, rounded

@@ -53,7 +53,7 @@ class pcmd_config(ctypes.Structure):
         ("hess_width", ctypes.c_double),
         ("max_im", ctypes.c_int), ("max_sets", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
-        ("imf", ctypes.c_int),
+        ("imf", ctypes.c_int), ("psf_grid", ctypes.c_int),
     ]
 
 
@@ -295,7 +295,11 @@ class Simulator:
             cfg.r_ext[b] = w.r_ext[b]
         cfg.f_dust, cfg.mdf_cut = w.f_dust, w.mdf_cut
         if w.psf is not None:
-            psf = np.ascontiguousarray(w.psf[:w.n_bands], np.float32)
+            if w.psf.ndim == 4:       # sub-pixel grid [16][B][S][S]
+                psf = np.ascontiguousarray(w.psf[:, :w.n_bands], np.float32)
+                cfg.psf_grid = 4
+            else:
+                psf = np.ascontiguousarray(w.psf[:w.n_bands], np.float32)
             self._keep.append(psf)
             cfg.psf = psf.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
             cfg.psf_size = psf.shape[-1]

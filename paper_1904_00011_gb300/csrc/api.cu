@@ -395,6 +395,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
     if (!(c.hess_width > 0.0) || !is_fin(c.hess_c_lo) || !is_fin(c.hess_m_lo)) return PCMD_ERR_ARG;
     if (c.max_im < 1 || c.max_im > 16384 || c.max_sets < 1 || c.max_sets > 65535) return PCMD_ERR_ARG;
     if (c.psf && (c.psf_size < 1 || c.psf_size > PCMD_MAX_PSF || (c.psf_size & 1) == 0)) return PCMD_ERR_ARG;
+    if (c.psf_grid != 0 && c.psf_grid != 1 && c.psf_grid != 4) return PCMD_ERR_ARG;
     const size_t P = (size_t)c.n_ages * c.n_feh * c.n_mass;
     for (int b = 0; b < c.n_bands; ++b)
         if (!(c.exptime[b] > 0.0) || !is_fin(c.zeropoint[b]) || !is_fin(c.sky[b]) || c.sky[b] < 0.0 ||
@@ -437,8 +438,9 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
     ctx->cfg.log_age = nullptr;
     ctx->cfg.psf = nullptr;
     if (c.psf) {
-        ctx->psf.assign(c.psf, c.psf + (size_t)c.n_bands * c.psf_size * c.psf_size);
-        if (c.psf_size == 25) {
+        const size_t n_kern = c.psf_grid == 4 ? 16 : 1;
+        ctx->psf.assign(c.psf, c.psf + n_kern * c.n_bands * c.psf_size * c.psf_size);
+        if (c.psf_size == 25 && n_kern == 1) {
             ctx->psf25.assign((size_t)kMaxBands * 625, 0.0f);
             std::copy(ctx->psf.begin(), ctx->psf.end(), ctx->psf25.begin());
         }
@@ -621,6 +623,7 @@ pcmd_status pcmd_hess(pcmd_ctx *ctx, uint32_t *d_hess, double *d_moments, uint32
     h.n_bands = ctx->model.n_bands;
     h.psf = ctx->psf.empty() ? nullptr : ctx->psf_d.as<float>();
     h.psf_size = ctx->psf.empty() ? 0 : ctx->cfg.psf_size;
+    h.psf_grid = ctx->cfg.psf_grid == 4 ? 4 : 1;
     h.hess = hh;
     h.counters = cc;
     h.cta_moments = ctx->partials.as<double>();

@@ -36,7 +36,10 @@ __device__ __forceinline__ float conv_pixel(const float *tile_b, int hx, int ty,
 }
 
 // KS: 0 = no PSF, 25 = 25x25 weights from the kernel parameter, -1 = any odd size from smem.
-template <int B, int KS>
+// GRID: the sub-pixel PSF grid (Section 2.2): output pixel (y, x) takes the kernel of region
+// (4y/N, 4x/N), read from global memory (the region is uniform over most warps, so the loads
+// are broadcasts from L1).
+template <int B, int KS, bool GRID>
 __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constant__ HessArgs a,
                                                             const __grid_constant__ PsfW pw) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
         (reinterpret_cast<uintptr_t>(wsm + (KS < 0 ? B * ks * ks : 0)) + 7u) & ~uintptr_t(7));
     const int tid = threadIdx.x;
     for (int i = tid; i < nbins; i += kHessThreads) hist[i] = 0u;
-    if (KS < 0)
+    if (KS < 0 && !GRID)
         for (int i = tid; i < B * ks * ks; i += kHessThreads) wsm[i] = a.psf[i];
     __syncthreads();
 
@@ -88,9 +91,15 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
             if (in) {
                 const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
                 float F[B];
+                const float *gk = nullptr;
+                if (GRID) {
+                    const int region = ((4 * y) / N) * 4 + (4 * x) / N;
+                    gk = a.psf + (size_t)region * B * ks * ks;
+                }
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     if (KS == 0) F[b] = __ldg(img + (size_t)b * npix + p);
+                    else if (GRID) F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, gk + b * ks * ks, ks);
                     else if (KS > 0) F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, pw.w[b], ks);
                     else F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, wsm + b * ks * ks, ks);
                 }
@@ -163,10 +172,10 @@ size_t hess_smem_bytes(int nb, int psf_size, int nx, int ny) {
     return s;
 }
 
-template <int B, int KS>
+template <int B, int KS, bool GRID>
 static cudaError_t launch_hess_t(const HessArgs &a, const PsfW &w, size_t smem, cudaStream_t st) {
     static size_t configured = 0;
-    auto k = hess_kernel<B, KS>;
+    auto k = hess_kernel<B, KS, GRID>;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -179,9 +188,13 @@ static cudaError_t launch_hess_t(const HessArgs &a, const PsfW &w, size_t smem, 
 
 template <int B>
 static cudaError_t launch_hess_b(const HessArgs &a, const PsfW &w, size_t smem, cudaStream_t st) {
-    if (!a.psf || a.psf_size == 0) return launch_hess_t<B, 0>(a, w, smem, st);
-    if (a.psf_size == 25) return launch_hess_t<B, 25>(a, w, smem, st);
-    return launch_hess_t<B, -1>(a, w, smem, st);
+    if (!a.psf || a.psf_size == 0) return launch_hess_t<B, 0, false>(a, w, smem, st);
+    if (a.psf_grid == 4) {
+        if (a.psf_size == 25) return launch_hess_t<B, 25, true>(a, w, smem, st);
+        return launch_hess_t<B, -1, true>(a, w, smem, st);
+    }
+    if (a.psf_size == 25) return launch_hess_t<B, 25, false>(a, w, smem, st);
+    return launch_hess_t<B, -1, false>(a, w, smem, st);
 }
 
 // The 25x25 weights travel as a kernel parameter (constant bank, compile-time offsets);

@@ -105,8 +105,9 @@ struct HessArgs {
     const float *image;         // raw images
     const SetDesc *desc;        // for n_im, set_id, img_off
     int n_sets, n_bands;
-    const float *psf;           // device [B][S][S] or nullptr
+    const float *psf;           // device [B][S][S] (or [16][B][S][S] with psf_grid 4), or nullptr
     int psf_size;
+    int psf_grid;               // 1, or 4: a 4x4 grid of regions with their own kernels
     uint32_t *hess;             // [n_sets][ny][nx]
     uint32_t *counters;         // [n_sets][2]
     double *cta_moments;        // [n_sets][ctas_per_set][3]

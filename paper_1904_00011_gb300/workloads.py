@@ -95,7 +95,7 @@ class Workload:
     r_ext: Sequence[float] = R_EXT
     f_dust: float = 0.5
     mdf_cut: float = 0.01
-    psf: Optional[np.ndarray] = None          # [n_bands, S, S] float32, or None
+    psf: Optional[np.ndarray] = None          # [n_bands, S, S] or [16, n_bands, S, S] float32, or None
     hess_nx: int = 100
     hess_ny: int = 100
     hess_c_lo: float = 0.0
@@ -185,6 +185,18 @@ def moffat_psf(size: int, fwhm: Sequence[float], beta: float = 2.5,
     return out
 
 
+def subpixel_psf_grid(size: int, fwhm: Sequence[float], beta: float = 2.5,
+                      n_bands: int = 2) -> np.ndarray:
+    """The 4x4 grid of sub-pixel PSFs (Section 2.2): region (ry, rx) of the image gets the Moffat
+    PSF shifted by ((rx + 1/2)/4 - 1/2, (ry + 1/2)/4 - 1/2) pixels; [16, n_bands, S, S]."""
+    out = np.zeros((16, n_bands, size, size), np.float32)
+    for ry in range(4):
+        for rx in range(4):
+            out[4 * ry + rx] = moffat_psf(size, fwhm, beta, n_bands,
+                                          shift=((rx + 0.5) / 4 - 0.5, (ry + 0.5) / 4 - 0.5))
+    return out
+
+
 def constant_sfr_log_sfh(log_age_edges: Sequence[float], npix: float) -> np.ndarray:
     """log10 stars/pixel per bin for a constant star-formation rate summing to npix."""
     e = 10.0 ** np.asarray(log_age_edges, np.float64)
@@ -221,7 +233,7 @@ def _edges(mid: Sequence[float], top: float = 10.15) -> List[float]:
 
 
 def full(seed: int = 2, n_im: int = 256, log_npix: float = 2.0, sky: float = 0.0,
-         noise: bool = True, psf: bool = True, dust: bool = True) -> Workload:
+         noise: bool = True, psf: bool = True, dust: bool = True, psf_grid: bool = False) -> Workload:
     iso = make_isochrones(seed=12, log_ages=FULL_LOG_AGES, fehs=FULL_FEH, n_mass=300, n_bands=2)
     npix = 10.0 ** log_npix
     dmod = 25.0 + 2.5 * (log_npix - 2.0)   # Npix ~ d^2 (Eq. 1): fixed surface brightness
@@ -229,7 +241,8 @@ def full(seed: int = 2, n_im: int = 256, log_npix: float = 2.0, sky: float = 0.0
                feh_sigma=0.2, log_ebv=-0.5, dust_sigma=0.1 if dust else 0.0, dmod=dmod)
     flags = (FLAG_DUST if dust else 0) | (FLAG_NOISE if noise else 0)
     return Workload("full", iso, 2, n_im, [p], [n_im],
-                    psf=moffat_psf(25, (2.0, 1.8)) if psf else None,
+                    psf=(subpixel_psf_grid(25, (2.0, 1.8)) if psf_grid else moffat_psf(25, (2.0, 1.8)))
+                    if psf else None,
                     sky=(sky, sky, 0.0, 0.0), hess_c_lo=-1.0, hess_m_lo=21.5, seed=seed,
                     flags=flags)
 

@@ -311,3 +311,45 @@ def test_loglike_hand_computed():
         g["poisson"], rel=1e-12)
     # identical diagrams and moments: the Gaussian term and C vanish
     assert O.loglike(d, md, 12, d, md, 12) == 0.0
+
+
+# ------------------------------------------------------------------- sub-pixel PSF grid
+
+def test_psf_grid_of_identical_kernels_is_the_single_psf():
+    rng = np.random.default_rng(21)
+    img = rng.uniform(0, 5, size=(2, 40 * 40))
+    k = W.moffat_psf(7, (2.0, 1.6))
+    grid = np.repeat(k[None], 16, axis=0)
+    assert np.array_equal(O.psf(img, grid, 40), O.psf(img, k, 40))
+
+
+@pytest.mark.parametrize("n_im", [32, 37])
+def test_psf_grid_uses_each_regions_kernel(n_im):
+    """Region (4y/N, 4x/N) of the output equals the whole-image convolution with that region's
+    kernel, for every region (ragged N puts uneven regions on the grid)."""
+    rng = np.random.default_rng(22)
+    img = rng.uniform(0, 5, size=(2, n_im * n_im))
+    grid = W.subpixel_psf_grid(9, (2.0, 1.7))
+    out = O.psf(img, grid, n_im).reshape(2, n_im, n_im)
+    y, x = np.mgrid[0:n_im, 0:n_im]
+    region = (4 * y // n_im) * 4 + (4 * x // n_im)
+    for r in range(16):
+        whole = O.psf(img, grid[r], n_im).reshape(2, n_im, n_im)
+        m = region == r
+        assert m.any()
+        assert np.array_equal(out[:, m], whole[:, m])
+
+
+def test_subpixel_psfs_are_shifted_moffats():
+    """Kernel 4 ry + rx is centred at ((rx + 1/2)/4 - 1/2, (ry + 1/2)/4 - 1/2) pixels: its
+    first moments, unit sum."""
+    grid = W.subpixel_psf_grid(25, (2.0, 1.8))
+    r = 12
+    yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
+    for ry in range(4):
+        for rx in range(4):
+            k = grid[4 * ry + rx, 0].astype(np.float64)
+            assert abs(k.sum() - 1.0) < 1e-6
+            # the Moffat's wings are truncated by the grid, so the centroid is only close
+            assert abs((k * xx).sum() - ((rx + 0.5) / 4 - 0.5)) < 0.05
+            assert abs((k * yy).sum() - ((ry + 0.5) / 4 - 0.5)) < 0.05
