@@ -51,7 +51,7 @@ def _args():
     ap.add_argument("--launch", default="", help="block,split,chunk: skip the autotuner")
     ap.add_argument("--surrogate-sims", type=int, default=262144,
                     help="simulations the surrogate is trained on in the extras")
-    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp", "lmax", "psf_grid"],
+    ap.add_argument("--only", default="", choices=["", "batched", "large", "surrogate", "mlp", "lmax", "psf_grid", "pool"],
                     help="run one extra section alone and print its JSON (profiling runs)")
     ap.add_argument("--large-n-im", type=int, default=1024, help="image edge of the large-Npix line")
     return ap.parse_args()
@@ -319,6 +319,7 @@ def run_gb300(args, world, rank, local):
         extras["large_npix"] = run_large(P, W, torch, n_im=args.large_n_im)
         extras["lmax"] = run_lmax(P, W, torch)
         extras["psf_grid"] = run_psf_grid(P, W, torch)
+        extras["pool"] = run_pool(P, W, torch)
         extras["surrogate"] = run_surrogate(torch, n_sims=args.surrogate_sims)
 
     if rank != 0:
@@ -573,6 +574,37 @@ def run_psf_grid(P, W, torch, reps: int = 10):
             "hess_roofline": hess_roofline(hess_ms, w.n_bands, n * n, 25, w.hess_nx * w.hess_ny)}
 
 
+def run_pool(P, W, torch, reps: int = 20):
+    """The full model (256x256, log10 Npix 2) with the total-count sampler for the points below
+    lambda 10: per pixel and half one Poisson total and ~Npix / 2 star assignments instead of
+    14 700 per-point draws; same law of the image, another RNG stream."""
+    import dataclasses
+    w0 = W.full()
+    w = dataclasses.replace(w0, flags=w0.flags | W.FLAG_POOL)
+    n = w.n_im
+    sim = P.Simulator(w, max_sets=1)
+    from paper_1904_00011_gb300 import autotune
+    tuned = autotune.tune(sim, w.params, [n], reps=3, use_cache=False)
+    sim.simulate(w.params, [n], 5_000_000)
+    h, m, _, _ = sim.hess(1, [n])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    for i in range(3):
+        sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=1 + i)
+    torch.cuda.synchronize()
+    sim.profile(True)
+    t0 = time.perf_counter()
+    for i in range(reps):
+        sim.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=10 + i)
+    dt = (time.perf_counter() - t0) / reps
+    kt = sim.kernel_times()
+    sim.profile(False)
+    return {"workload": "full model 256x256, log10 Npix 2, total-count sampler (PCMD_FLAG_POOL)",
+            "ms_per_eval": 1e3 * dt, "model_pixels_per_s": n * n / dt,
+            "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kt.items() if v[1]},
+            "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
+
+
 def run_mlp(torch, batch: int = 4096, reps: int = 20):
     """Surrogate network alone (random init, no training): the 5-layer inference forward and the
     fused forward + likelihood on a batch of parameter points; GEMM roofline."""
@@ -639,6 +671,8 @@ def main():
             out = run_lmax(P, W, torch)
         elif args.only == "psf_grid":
             out = run_psf_grid(P, W, torch)
+        elif args.only == "pool":
+            out = run_pool(P, W, torch)
         else:
             out = run_surrogate(torch, n_sims=args.surrogate_sims)
         print(json.dumps({"section": args.only, **out}), flush=True)

@@ -34,6 +34,7 @@ LL_POISSON = 1
 FLAG_DUST = 1
 FLAG_NOISE = 2
 FLAG_SIGMA_SQRTSUM = 8
+FLAG_POOL = 16
 
 
 def build(force: bool = False) -> str:
@@ -93,7 +94,8 @@ def lib():
             L.or_simulate.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f64p, ctypes.c_int,
                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_double, f64p, f64p, u32p, ctypes.c_int]
+                                      ctypes.c_double, f64p, f64p, u32p, ctypes.c_int,
+                                      ctypes.c_int]
             L.or_simulate.restype = ctypes.c_int
             L.or_psf.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f64p, f64p]
             L.or_psf.restype = None
@@ -223,9 +225,12 @@ def tables(w, set_index: int = 0):
 
 def simulate(w, set_index: int = 0, set_id: Optional[int] = None, pix_begin: int = 0,
              pix_end: Optional[int] = None, counts: bool = False, n_threads: int = 1,
-             n_im: Optional[int] = None):
+             n_im: Optional[int] = None, pool: Optional[bool] = None):
     """Raw (pre-PSF) image [n_bands, N*N] FP64 for pixels [pix_begin, pix_end) and, when asked,
-    the counts [pixels, 2, n_points] (uint32)."""
+    the counts [pixels, 2, n_points] (uint32).  pool: the total-count sampler for the points
+    below lambda 10 (default: the workload's FLAG_POOL)."""
+    if pool is None:
+        pool = bool(w.flags & FLAG_POOL)
     p = w.params[set_index]
     n_im = n_im if n_im is not None else w.n_ims[set_index]
     set_id = set_index if set_id is None else set_id
@@ -243,7 +248,7 @@ def simulate(w, set_index: int = 0, set_id: Optional[int] = None, pix_begin: int
                             pix_begin, pix_end, set_id, w.seed, int(bool(w.flags & FLAG_DUST)),
                             p.log_ebv, p.dust_sigma, _p(r_ext, ctypes.c_double),
                             _p(image, ctypes.c_double),
-                            _p(cnt, ctypes.c_uint32) if counts else None, n_threads)
+                            _p(cnt, ctypes.c_uint32) if counts else None, n_threads, int(bool(pool)))
     if err:
         raise RuntimeError("oracle sampler attempt cap reached")
     return (image, cnt) if counts else image

@@ -429,13 +429,75 @@ static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_ban
  * per pixel, draws for every entry of both halves, flux sums per band in FP64, the dust factor
  * on the behind half.  counts (optional) receives n for every (pixel, half, point) as
  * counts[(p - pix_begin) * 2 * n_pts + h * n_pts + i].  Returns nonzero on a sampler overrun. */
+/* Total-count sampler (Section 2.1 footnote: a sum of Poisson counts is Poisson with the summed
+ * mean, and conversely a Poisson total split over the points by their weights gives independent
+ * Poisson counts).  The pool of one half is every point with 0 < lambda < 10 in point order;
+ * Lambda = sum of (double) lambda over the pool, accumulated in point order.  Star assignment
+ * thresholds: T_j = min(floor(C_j / Lambda * 2^32), 2^32 - 1) with C_j the running sum through
+ * pool entry j; a star with word u goes to the first pool entry with u < T_j, or to the last. */
+typedef struct {
+    uint32_t n;            /* pool size */
+    uint32_t *idx;         /* point of each pool entry */
+    uint32_t *thr;         /* T_j (the last entry's is unused) */
+    float lam;             /* (float) Lambda */
+} or_pool;
+
+static void or_pool_build(const float *lam, int n_pts, or_pool *pl)
+{
+    pl->n = 0;
+    pl->idx = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_pts > 0 ? n_pts : 1));
+    pl->thr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_pts > 0 ? n_pts : 1));
+    double total = 0.0;
+    for (int i = 0; i < n_pts; ++i)
+        if (lam[i] > 0.0f && lam[i] < 10.0f) {
+            pl->idx[pl->n++] = (uint32_t)i;
+            total = total + (double)lam[i];
+        }
+    double c = 0.0;
+    for (uint32_t j = 0; j < pl->n; ++j) {
+        c = c + (double)lam[pl->idx[j]];
+        double q = c / total;
+        double t = floor(q * 4294967296.0);
+        pl->thr[j] = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+    }
+    pl->lam = (float)total;
+}
+
+static uint32_t or_pool_pick(const or_pool *pl, uint32_t u)
+{
+    for (uint32_t j = 0; j + 1 < pl->n; ++j)
+        if (u < pl->thr[j]) return pl->idx[j];
+    return pl->idx[pl->n - 1];
+}
+
+/* Number of pool stars of (pixel, half): inversion on word 0 of Philox(p, 2^32 - 1, set, LO|h)
+ * below 10, transformed rejection with point index 2^32 - 1 at and above. */
+static uint32_t or_pool_total(const or_pool *pl, uint64_t seed, uint32_t pix, uint32_t set, uint32_t half,
+                              int *err)
+{
+    if (pl->n == 0) return 0u;
+    if (pl->lam < 10.0f) {
+        uint32_t w[4];
+        or_call(seed, pix, 0xFFFFFFFFu, set, or_tag(OR_KIND_LO, half, 0), w);
+        return or_poisson_inversion(pl->lam, w[0]);
+    }
+    float c6[6];
+    or_ptrs_setup(pl->lam, c6);
+    uint32_t n = or_poisson_ptrs(c6, seed, pix, 0xFFFFFFFFu, set, half, NULL);
+    if (n == UINT32_MAX) { if (err) *err = 1; return 0u; }
+    return n;
+}
+
 int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, int n_im,
                 uint32_t pix_begin, uint32_t pix_end, uint32_t set, uint64_t seed, int dust,
                 double log_ebv, double dust_sigma, const double *r_ext, double *image,
-                uint32_t *counts, int n_threads)
+                uint32_t *counts, int n_threads, int pool)
 {
     int err = 0;
     size_t npix = (size_t)n_im * (size_t)n_im;
+    or_pool pools[2];
+    if (pool)
+        for (int h = 0; h < 2; ++h) or_pool_build(lam_h + (size_t)h * n_pts, n_pts, &pools[h]);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
@@ -444,9 +506,10 @@ int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, 
         uint32_t p = (uint32_t)pl;
         double F[2][8];
         memset(F, 0, sizeof F);
-        for (uint32_t h = 0; h < 2; ++h)
+        for (uint32_t h = 0; h < 2; ++h) {
             for (uint32_t i = 0; i < (uint32_t)n_pts; ++i) {
                 float lam = lam_h[(size_t)h * n_pts + i];
+                if (pool && lam < 10.0f) continue;      /* drawn through the pool below */
                 int e = 0;
                 uint32_t n = or_draw(lam, seed, p, i, set, h, &e);
                 err |= e;
@@ -454,6 +517,22 @@ int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, 
                 if (n == 0u) continue;
                 for (int b = 0; b < n_bands; ++b) F[h][b] += (double)n * flux[(size_t)i * n_bands + b];
             }
+            if (!pool) continue;
+            if (counts)
+                for (uint32_t j = 0; j < pools[h].n; ++j)
+                    counts[(size_t)(p - pix_begin) * 2u * n_pts + h * n_pts + pools[h].idx[j]] = 0u;
+            int e = 0;
+            uint32_t n_star = or_pool_total(&pools[h], seed, p, set, h, &e);
+            err |= e;
+            uint32_t w[4];
+            for (uint32_t st = 0; st < n_star; ++st) {
+                if ((st & 3u) == 0u)
+                    or_call(seed, p, 0x80000000u | (st >> 2), set, or_tag(OR_KIND_HI, h, 0), w);
+                uint32_t i = or_pool_pick(&pools[h], w[st & 3u]);
+                if (counts) counts[(size_t)(p - pix_begin) * 2u * n_pts + h * n_pts + i] += 1u;
+                for (int b = 0; b < n_bands; ++b) F[h][b] += flux[(size_t)i * n_bands + b];
+            }
+        }
         double fac[8];
         if (dust) or_dust_factors(seed, p, set, n_bands, log_ebv, dust_sigma, r_ext, fac);
         for (int b = 0; b < n_bands; ++b) {
@@ -461,6 +540,8 @@ int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, 
             if (image) image[(size_t)b * npix + p] = v;
         }
     }
+    if (pool)
+        for (int h = 0; h < 2; ++h) { free(pools[h].idx); free(pools[h].thr); }
     (void)n_threads;
     return err;
 }

@@ -25,7 +25,7 @@ PCMD_MAX_SFH = 32
 
 STATUS = {0: "PCMD_OK", 1: "PCMD_ERR_ARG", 2: "PCMD_ERR_CUDA", 3: "PCMD_ERR_OOM",
           4: "PCMD_ERR_SAMPLER_LIMIT", 5: "PCMD_ERR_STATE", 6: "PCMD_ERR_TIMEOUT"}
-PCMD_FLAG_DUST, PCMD_FLAG_NOISE, PCMD_FLAG_KAHAN, PCMD_FLAG_SIGMA_SQRTSUM = 1, 2, 4, 8
+PCMD_FLAG_DUST, PCMD_FLAG_NOISE, PCMD_FLAG_KAHAN, PCMD_FLAG_SIGMA_SQRTSUM, PCMD_FLAG_POOL = 1, 2, 4, 8, 16
 PCMD_LL_PAPER, PCMD_LL_POISSON = 0, 1
 PCMD_IMF_POWER, PCMD_IMF_KROUPA = 0, 1
 PCMD_SFH_SSP, PCMD_SFH_CONSTANT, PCMD_SFH_TAU, PCMD_SFH_DELAYED_TAU = 1, 2, 3, 4

@@ -80,7 +80,7 @@ struct pcmd_ctx {
     DevBuf tables, desc, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
-    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll;
+    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll, h_pool;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     TabLayout layout;
@@ -267,6 +267,9 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
             d.ptrs_off[h] = tin[s].base + L.ptrs_off[h];
         }
         d.tail_off = tin[s].base + L.tail_off;
+        d.flux_off = tin[s].base + L.flux_off;
+        d.pool_on = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 1u : 0u;
+        for (int h = 0; h < 2; ++h) d.pool_off[h] = tin[s].base + L.pool_off[h];
         // dust screen of this model (Section 2.2): E = 10^log_ebv exp(sigma z)
         d.dust_on = m.dust ? 1u : 0u;
         d.dust_a = (float)(std::log(10.0) * p[s].log_ebv);
@@ -307,6 +310,23 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->cfg.flags & PCMD_FLAG_POOL) {
+        // total-count sampler: lambda of every point (the device builder's FP64 products), one
+        // pool region per model and half, copied into the model's table
+        const uint64_t rb = pool_region_bytes(P);
+        CK(ctx->h_pool.ensure((size_t)rb * 2 * n_sets));
+        std::vector<float> lam(P);
+        for (int s = 0; s < n_sets; ++s) {
+            const double *w = wts + (size_t)s * nw;
+            for (int h = 0; h < 2; ++h) {
+                for (uint32_t i = 0; i < P; ++i) lam[i] = (float)((w[i / m.n_mass] * m.imf[i]) * hf[h]);
+                uint8_t *dst = ctx->h_pool.as<uint8_t>() + ((size_t)s * 2 + h) * rb;
+                build_pool(lam.data(), P, dst);
+                CK(cudaMemcpyAsync(ctx->tables.as<uint8_t>() + tin[s].base + L.pool_off[h], dst, rb,
+                                   cudaMemcpyHostToDevice, ctx->st));
+            }
+        }
+    }
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
 
@@ -495,7 +515,8 @@ void pcmd_destroy(pcmd_ctx *ctx) {
                       &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
                       &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
     for (DevBuf *b : bufs) b->release();
-    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
+    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll,
+                     &ctx->h_pool};
     for (HostBuf *b : hb) b->release();
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);

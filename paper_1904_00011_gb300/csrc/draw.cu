@@ -321,6 +321,52 @@ __device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &
     }
 }
 
+
+// Total-count sampler of half H (Section 2.1 footnote: Poisson totals split by weight give
+// independent Poisson counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
+// by inversion (Lambda < 10) or by transformed rejection with point index 2^32 - 1; star s takes
+// word s & 3 of Philox(p, 2^31 | s >> 2, set, HI|H) and goes to the first pool entry with
+// u < T_j (the last takes the rest), found from the guide table of the top 12 bits.
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
+                                             int sidx, Acc<B, KAHAN> &acc) {
+    if (!ic.active || sidx != H % a.split) return;
+    const uint8_t *pr = a.tables + d.pool_off[H];
+    const PoolHdr hdr = *reinterpret_cast<const PoolHdr *>(pr);
+    if (hdr.mode == 0u || hdr.n == 0u) return;
+    uint32_t n_star;
+    if (hdr.mode == 1u) {
+        const uint32_t x = philox_rk(ic.pix, 0xFFFFFFFFu, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1).x;
+        const uint32_t *z = reinterpret_cast<const uint32_t *>(pr + kPoolZOff);
+        n_star = 0u;
+        while (n_star < hdr.n_z && x > __ldg(z + n_star)) ++n_star;
+    } else {
+        const PtrsRec rec = load_ptrs(reinterpret_cast<const PtrsRec *>(pr + kPoolPtrsOff), 0u);
+        n_star = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
+    }
+    const uint32_t *guide = reinterpret_cast<const uint32_t *>(pr + kPoolGuideOff);
+    const uint32_t *idx = reinterpret_cast<const uint32_t *>(pr + kPoolIdxOff);
+    const uint32_t *thr = idx + hdr.n;
+    const float *flux = reinterpret_cast<const float *>(a.tables + d.flux_off);
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t st = 0; st < n_star; ++st) {
+        if ((st & 3u) == 0u)
+            w = philox_rk(ic.pix, 0x80000000u | (st >> 2), ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
+        const uint32_t u = word_of(w, st & 3u);
+        uint32_t j = __ldg(guide + (u >> (32 - kPoolGuideBits)));
+        while (j + 1u < hdr.n && u >= __ldg(thr + j)) ++j;
+        const uint32_t i = __ldg(idx + j);
+        float f[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) f[b] = __ldg(flux + (size_t)i * B + b);
+        acc.template add<H>(1.0f, f);
+        if (MODE == kModeCounts) {
+            if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + i] += 1u;
+        }
+    }
+}
+
 // Transformed-rejection points: every thread runs the attempt loop of each of its records.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic,
@@ -411,8 +457,9 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 0, 0), a.rk0, a.rk1),
             philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 1, 0), a.rk0, a.rk1)};
 
-        // ---- inversion points, streamed through shared memory chunk by chunk ----
-        const uint32_t ng0 = d.n_grp[0], ng1 = d.n_grp[1];
+        // ---- inversion points, streamed through shared memory chunk by chunk (or, with the
+        // total-count sampler, drawn through the pool) ----
+        const uint32_t ng0 = d.pool_on ? 0u : d.n_grp[0], ng1 = d.pool_on ? 0u : d.n_grp[1];
         const uint32_t nc0 = (ng0 + chunk - 1) / chunk, nc1 = (ng1 + chunk - 1) / chunk;
         const uint32_t nc = nc0 + nc1;
         if (tid == 0 && nc > 0) {
@@ -448,8 +495,13 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
         }
 
         // ---- dense inversion groups, then transformed-rejection points (lambda >= 10) ----
-        process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
-        process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        if (d.pool_on) {
+            process_pool<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+            process_pool<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        } else {
+            process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+            process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        }
         process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
         process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
 

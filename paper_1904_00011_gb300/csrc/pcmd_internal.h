@@ -63,8 +63,25 @@ struct __align__(16) SetDesc {
     float dust_a;           // ln(10) * log_ebv
     float dust_sigma;
     float dust_c[kMaxBands];  // -0.4 R_b: factor_b = 10^(dust_c[b] * E)
-    uint32_t dust_on, pad0;
+    uint32_t dust_on;
+    uint32_t pool_on;       // total-count sampler for the points below lambda 10
+    uint64_t pool_off[2];   // PoolHdr + thresholds / guide / entries per half (host-built)
+    uint64_t flux_off;      // float [P][B] electrons per star of every point
 };
+
+// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 10): header,
+// then Z[64] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
+// table, the pool's point indices and their star-assignment thresholds T_j.
+constexpr int kPoolGuideBits = 12;
+struct __align__(16) PoolHdr {
+    float lam;              // (float) Lambda
+    uint32_t n;             // pool size
+    uint32_t n_z;           // thresholds of the total (mode 1)
+    uint32_t mode;          // 0 empty, 1 inversion (Lambda < 10), 2 transformed rejection
+};
+constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * 64, kPoolGuideOff = kPoolPtrsOff + 48;
+constexpr uint32_t kPoolIdxOff = kPoolGuideOff + 4 * (1u << kPoolGuideBits);
+__host__ __device__ constexpr uint64_t pool_region_bytes(uint32_t P) { return kPoolIdxOff + 8ull * P; }
 
 // Constants of the pixel stage (noise, magnitudes, Hess binning).
 struct PixelConsts {

@@ -294,6 +294,12 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         for (int b = 0; b < B; ++b) f[b] = fl[b];
     }
 
+    // per-point fluxes (the total-count sampler reads them by point index)
+    if (p.valid && h == 0) {
+        float *fo = reinterpret_cast<float *>(tab + L.flux_off) + (size_t)p.i * B;
+        for (int b = 0; b < B; ++b) fo[b] = fl[b];
+    }
+
     // inspection copies (parity export)
     if (a.insp_lam && p.valid && s == 0) {
         a.insp_lam[(size_t)h * a.P + p.i] = p.lam;
@@ -322,6 +328,8 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
         L.ptrs_off[h] = place((uint64_t)P * sizeof(PtrsRec));
     }
     L.tail_off = place(2ull * P * (kInvCap - 2) * 4u + 4u);
+    L.flux_off = place((uint64_t)P * n_bands * 4u);
+    for (int h = 0; h < 2; ++h) L.pool_off[h] = place(pool_region_bytes(P));
     L.bytes = off;
     return L;
 }

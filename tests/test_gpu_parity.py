@@ -146,11 +146,13 @@ def _end_to_end(w, n_threads=16):
     return s, h, m, c, px, ref
 
 
-@pytest.mark.parametrize("name", ["tiny", "full_small", "full", "psf_grid", "psf_grid_ragged"])
+@pytest.mark.parametrize("name", ["tiny", "full_small", "full", "psf_grid", "psf_grid_ragged", "pool"])
 def test_end_to_end_fluxes_bins_loglike(name):
     w = {"tiny": W.tiny, "full_small": lambda: W.full(n_im=128, sky=40.0),
          "full": W.full, "psf_grid": lambda: W.full(n_im=128, psf_grid=True),
-         "psf_grid_ragged": lambda: W.full(n_im=100, psf_grid=True, sky=10.0)}[name]()
+         "psf_grid_ragged": lambda: W.full(n_im=100, psf_grid=True, sky=10.0),
+         "pool": lambda: dataclasses.replace(W.full(n_im=128, sky=20.0),
+                                             flags=W.full().flags | W.FLAG_POOL)}[name]()
     n = w.n_im
     npix = n * n
     s, h, m, c, px, ref = _end_to_end(w)
