@@ -326,7 +326,8 @@ __device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &
 // independent Poisson counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
 // by inversion (Lambda < 10) or by transformed rejection with point index 2^32 - 1; star s takes
 // word s & 3 of Philox(p, 2^31 | s >> 2, set, HI|H) and goes to the first pool entry with
-// u < T_j (the last takes the rest), found from the guide table of the top 12 bits.
+// u < T_j (the last takes the rest): the top 14 bits of u select a guide bucket, a binary
+// search inside it finds the entry (bounded, so no lane walks a long run of tiny weights).
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                              int sidx, Acc<B, KAHAN> &acc) {
@@ -353,9 +354,16 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
         if ((st & 3u) == 0u)
             w = philox_rk(ic.pix, 0x80000000u | (st >> 2), ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
         const uint32_t u = word_of(w, st & 3u);
-        uint32_t j = __ldg(guide + (u >> (32 - kPoolGuideBits)));
-        while (j + 1u < hdr.n && u >= __ldg(thr + j)) ++j;
-        const uint32_t i = __ldg(idx + j);
+        // the entry lies in [guide[b], guide[b + 1]]: binary search for the first j with
+        // u < T_j (the last entry takes every remaining u)
+        const uint32_t b = u >> (32 - kPoolGuideBits);
+        uint32_t lo = __ldg(guide + b), hi = __ldg(guide + b + 1);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (u < __ldg(thr + mid)) hi = mid;
+            else lo = mid + 1u;
+        }
+        const uint32_t i = __ldg(idx + lo);
         float f[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) f[b] = __ldg(flux + (size_t)i * B + b);

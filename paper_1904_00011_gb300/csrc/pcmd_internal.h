@@ -71,8 +71,9 @@ struct __align__(16) SetDesc {
 
 // Total-count sampler of one dust half (the pool = every point with 0 < lambda < 10): header,
 // then Z[64] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
-// table, the pool's point indices and their star-assignment thresholds T_j.
-constexpr int kPoolGuideBits = 12;
+// table (guide[b] = first entry j with T_j > b 2^(32 - bits), guide[2^bits] = n - 1), the pool's
+// point indices and their star-assignment thresholds T_j.
+constexpr int kPoolGuideBits = 14;
 struct __align__(16) PoolHdr {
     float lam;              // (float) Lambda
     uint32_t n;             // pool size
@@ -80,7 +81,7 @@ struct __align__(16) PoolHdr {
     uint32_t mode;          // 0 empty, 1 inversion (Lambda < 10), 2 transformed rejection
 };
 constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * 64, kPoolGuideOff = kPoolPtrsOff + 48;
-constexpr uint32_t kPoolIdxOff = kPoolGuideOff + 4 * (1u << kPoolGuideBits);
+constexpr uint32_t kPoolIdxOff = kPoolGuideOff + 4 * ((1u << kPoolGuideBits) + 4);   // guide[2^bits + 1]
 __host__ __device__ constexpr uint64_t pool_region_bytes(uint32_t P) { return kPoolIdxOff + 8ull * P; }
 
 // Constants of the pixel stage (noise, magnitudes, Hess binning).

@@ -154,6 +154,7 @@ void build_pool(const float *lam, uint32_t P, uint8_t *dst) {
         while (hdr.n > 0 && j + 1 < hdr.n && (uint64_t)thr[j] <= lo) ++j;
         guide[b] = j;
     }
+    guide[1u << kPoolGuideBits] = hdr.n > 0 ? hdr.n - 1 : 0u;
     if (hdr.n > 0) {
         hdr.lam = (float)total;
         const double L = (double)hdr.lam;
