@@ -97,6 +97,8 @@ def lib():
                                       ctypes.c_double, f64p, f64p, u32p, ctypes.c_int,
                                       ctypes.c_int]
             L.or_simulate.restype = ctypes.c_int
+            L.or_pool_tables.argtypes = [f32p, ctypes.c_int, u32p, u32p, f32p]
+            L.or_pool_tables.restype = ctypes.c_int
             L.or_psf.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f64p, f64p]
             L.or_psf.restype = None
             L.or_psf_grid.argtypes = L.or_psf.argtypes
@@ -252,6 +254,18 @@ def simulate(w, set_index: int = 0, set_id: Optional[int] = None, pix_begin: int
     if err:
         raise RuntimeError("oracle sampler attempt cap reached")
     return (image, cnt) if counts else image
+
+
+def pool_tables(lam: np.ndarray) -> Tuple[np.ndarray, np.ndarray, float]:
+    """Total-count sampler pool of one half (FP32 lambdas): point indices, star-assignment
+    thresholds T_j and the total's mean Lambda."""
+    lam = np.ascontiguousarray(lam, np.float32)
+    idx = np.zeros(max(lam.size, 1), np.uint32)
+    thr = np.zeros(max(lam.size, 1), np.uint32)
+    tot = np.zeros(1, np.float32)
+    n = lib().or_pool_tables(_p(lam, ctypes.c_float), lam.size, _p(idx, ctypes.c_uint32),
+                             _p(thr, ctypes.c_uint32), _p(tot, ctypes.c_float))
+    return idx[:n].copy(), thr[:n].copy(), float(tot[0])
 
 
 def psf(image: np.ndarray, kernel: np.ndarray, n_im: int) -> np.ndarray:

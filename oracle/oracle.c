@@ -431,15 +431,18 @@ static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_ban
  * counts[(p - pix_begin) * 2 * n_pts + h * n_pts + i].  Returns nonzero on a sampler overrun. */
 /* Total-count sampler (Section 2.1 footnote: a sum of Poisson counts is Poisson with the summed
  * mean, and conversely a Poisson total split over the points by their weights gives independent
- * Poisson counts).  The pool of one half is every point with 0 < lambda < 10 in point order;
- * Lambda = sum of (double) lambda over the pool, accumulated in point order.  Star assignment
- * thresholds: T_j = min(floor(C_j / Lambda * 2^32), 2^32 - 1) with C_j the running sum through
- * pool entry j; a star with word u goes to the first pool entry with u < T_j, or to the last. */
+ * Poisson counts).  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 10
+ * (lambda_i 2^40 is exact in FP64), and the pool of one half is every point with L_i > 0, in
+ * point order (the others below 10 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
+ * are exact integers; the total's mean is Lambda = (float)(Lfix 2^-40), the FP64 conversion
+ * rounding to nearest.  Star assignment thresholds T_j = min(floor(C_j 2^32 / Lfix), 2^32 - 1)
+ * in exact integer arithmetic; a star with word u goes to the first pool entry with u < T_j,
+ * or to the last. */
 typedef struct {
     uint32_t n;            /* pool size */
     uint32_t *idx;         /* point of each pool entry */
     uint32_t *thr;         /* T_j (the last entry's is unused) */
-    float lam;             /* (float) Lambda */
+    float lam;             /* Lambda */
 } or_pool;
 
 static void or_pool_build(const float *lam, int n_pts, or_pool *pl)
@@ -447,20 +450,35 @@ static void or_pool_build(const float *lam, int n_pts, or_pool *pl)
     pl->n = 0;
     pl->idx = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_pts > 0 ? n_pts : 1));
     pl->thr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_pts > 0 ? n_pts : 1));
-    double total = 0.0;
-    for (int i = 0; i < n_pts; ++i)
-        if (lam[i] > 0.0f && lam[i] < 10.0f) {
-            pl->idx[pl->n++] = (uint32_t)i;
-            total = total + (double)lam[i];
-        }
-    double c = 0.0;
-    for (uint32_t j = 0; j < pl->n; ++j) {
-        c = c + (double)lam[pl->idx[j]];
-        double q = c / total;
-        double t = floor(q * 4294967296.0);
-        pl->thr[j] = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+    uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n_pts > 0 ? n_pts : 1));
+    uint64_t c = 0;
+    for (int i = 0; i < n_pts; ++i) {
+        if (!(lam[i] > 0.0f && lam[i] < 10.0f)) continue;
+        uint64_t w = (uint64_t)((double)lam[i] * 1099511627776.0);
+        if (w == 0) continue;
+        c += w;
+        pl->idx[pl->n] = (uint32_t)i;
+        cum[pl->n] = c;
+        pl->n++;
     }
-    pl->lam = (float)total;
+    for (uint32_t j = 0; j < pl->n; ++j) {
+        unsigned __int128 q = ((unsigned __int128)cum[j] << 32) / c;
+        pl->thr[j] = q >= 0xFFFFFFFFu ? 0xFFFFFFFFu : (uint32_t)q;
+    }
+    pl->lam = (float)ldexp((double)c, -40);
+    free(cum);
+}
+
+/* The pool of one half as arrays: n (returned), idx[n], thr[n], *lam_total = Lambda. */
+int or_pool_tables(const float *lam, int n_pts, uint32_t *idx, uint32_t *thr, float *lam_total)
+{
+    or_pool pl;
+    or_pool_build(lam, n_pts, &pl);
+    for (uint32_t j = 0; j < pl.n; ++j) { idx[j] = pl.idx[j]; thr[j] = pl.thr[j]; }
+    *lam_total = pl.lam;
+    free(pl.idx);
+    free(pl.thr);
+    return (int)pl.n;
 }
 
 static uint32_t or_pool_pick(const or_pool *pl, uint32_t u)

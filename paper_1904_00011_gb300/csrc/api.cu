@@ -80,7 +80,7 @@ struct pcmd_ctx {
     DevBuf tables, desc, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
-    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll, h_pool;
+    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     TabLayout layout;
@@ -299,7 +299,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
     CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
     CK(ctx->tab_in.ensure(in_bytes + w_bytes));
-    CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets));
+    const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
+    CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets * n_scr));
     CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->items.ensure(sizeof(uint2) * n_items));
     CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
@@ -310,23 +311,6 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
-    if (ctx->cfg.flags & PCMD_FLAG_POOL) {
-        // total-count sampler: lambda of every point (the device builder's FP64 products), one
-        // pool region per model and half, copied into the model's table
-        const uint64_t rb = pool_region_bytes(P);
-        CK(ctx->h_pool.ensure((size_t)rb * 2 * n_sets));
-        std::vector<float> lam(P);
-        for (int s = 0; s < n_sets; ++s) {
-            const double *w = wts + (size_t)s * nw;
-            for (int h = 0; h < 2; ++h) {
-                for (uint32_t i = 0; i < P; ++i) lam[i] = (float)((w[i / m.n_mass] * m.imf[i]) * hf[h]);
-                uint8_t *dst = ctx->h_pool.as<uint8_t>() + ((size_t)s * 2 + h) * rb;
-                build_pool(lam.data(), P, dst);
-                CK(cudaMemcpyAsync(ctx->tables.as<uint8_t>() + tin[s].base + L.pool_off[h], dst, rb,
-                                   cudaMemcpyHostToDevice, ctx->st));
-            }
-        }
-    }
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
 
@@ -349,6 +333,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     ta.insp_lam = insp_lam;
     ta.insp_flux = insp_flux;
     ta.insp_z0 = insp_z0;
+    ta.pool = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 1 : 0;
+    ta.pool_scratch = ta.pool ? ta.scratch + 2 * (size_t)G * n_sets : nullptr;
     {
         KTimer t(ctx, PCMD_K_TABLES, ctx->st);
         CK(launch_build_tables(ta, n_sets, ctx->st));
@@ -515,8 +501,7 @@ void pcmd_destroy(pcmd_ctx *ctx) {
                       &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
                       &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
     for (DevBuf *b : bufs) b->release();
-    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll,
-                     &ctx->h_pool};
+    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
     for (HostBuf *b : hb) b->release();
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);

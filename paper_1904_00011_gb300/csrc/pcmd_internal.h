@@ -82,7 +82,10 @@ struct __align__(16) PoolHdr {
 };
 constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * 64, kPoolGuideOff = kPoolPtrsOff + 48;
 constexpr uint32_t kPoolIdxOff = kPoolGuideOff + 4 * ((1u << kPoolGuideBits) + 4);   // guide[2^bits + 1]
-__host__ __device__ constexpr uint64_t pool_region_bytes(uint32_t P) { return kPoolIdxOff + 8ull * P; }
+// ... followed by the pool's fixed-point total (uint64, in a 16-byte slot)
+constexpr double kPoolFix = 1099511627776.0;   // 2^40: fixed-point scale of the pool weights
+__host__ __device__ constexpr uint64_t pool_fix_off(uint32_t P) { return ((kPoolIdxOff + 8ull * P) + 15) & ~15ull; }
+__host__ __device__ constexpr uint64_t pool_region_bytes(uint32_t P) { return pool_fix_off(P) + 16; }
 
 // Constants of the pixel stage (noise, magnitudes, Hess binning).
 struct PixelConsts {

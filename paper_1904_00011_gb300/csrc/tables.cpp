@@ -120,78 +120,6 @@ void stirlerr_table(float out[16]) {
     }
 }
 
-// Inversion thresholds of lambda: Z_k = ceil(F_k 2^32 - 1/2) - 1 (saturating), F_k the FP64
-// Poisson CDF by p_k = p_{k-1} lambda / k; stored through the first saturated one, at most 64.
-static uint32_t host_threshold(double F) {
-    const double y = F * 4294967296.0 - 0.5;
-    if (y >= 4294967295.0) return 0xFFFFFFFFu;
-    const uint64_t t = (uint64_t)y;
-    const uint64_t T = t + (y > (double)t ? 1u : 0u);
-    return (uint32_t)(T - 1u);
-}
-
-void build_pool(const float *lam, uint32_t P, uint8_t *dst) {
-    PoolHdr hdr{0.0f, 0u, 0u, 0u};
-    uint32_t *idx = reinterpret_cast<uint32_t *>(dst + kPoolIdxOff);
-    double total = 0.0;
-    for (uint32_t i = 0; i < P; ++i)
-        if (lam[i] > 0.0f && lam[i] < kPtrsThreshold) {
-            idx[hdr.n++] = i;
-            total = total + (double)lam[i];
-        }
-    uint32_t *thr = idx + hdr.n;
-    double c = 0.0;
-    for (uint32_t j = 0; j < hdr.n; ++j) {
-        c = c + (double)lam[idx[j]];
-        const double q = c / total;
-        const double t = std::floor(q * 4294967296.0);
-        thr[j] = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
-    }
-    uint32_t *guide = reinterpret_cast<uint32_t *>(dst + kPoolGuideOff);
-    uint32_t j = 0;
-    for (uint32_t b = 0; b < (1u << kPoolGuideBits); ++b) {
-        const uint64_t lo = (uint64_t)b << (32 - kPoolGuideBits);
-        while (hdr.n > 0 && j + 1 < hdr.n && (uint64_t)thr[j] <= lo) ++j;
-        guide[b] = j;
-    }
-    guide[1u << kPoolGuideBits] = hdr.n > 0 ? hdr.n - 1 : 0u;
-    if (hdr.n > 0) {
-        hdr.lam = (float)total;
-        const double L = (double)hdr.lam;
-        if (hdr.lam < kPtrsThreshold) {
-            hdr.mode = 1u;
-            uint32_t *z = reinterpret_cast<uint32_t *>(dst + kPoolZOff);
-            double p = std::exp(-L);
-            double F = p;
-            z[hdr.n_z++] = host_threshold(F);
-            for (int k = 1; k < 64 && z[hdr.n_z - 1] != 0xFFFFFFFFu; ++k) {
-                p = p * L;
-                p = p / (double)k;
-                F = F + p;
-                z[hdr.n_z++] = host_threshold(F);
-            }
-        } else {
-            hdr.mode = 2u;
-            PtrsRec r;
-            std::memset(&r, 0, sizeof r);
-            const double slam = std::sqrt(L);
-            const double b = 0.931 + 2.53 * slam;
-            const double a = -0.059 + 0.02483 * b;
-            const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
-            const double vr = 0.9277 - 3.6224 / (b - 2.0);
-            r.i = 0xFFFFFFFFu;
-            r.lam = hdr.lam;
-            r.b = (float)b;
-            r.a = (float)a;
-            r.twoa = (float)(2.0 * a);
-            r.vr = (float)vr;
-            r.log_ia = (float)std::log(inv_alpha);
-            std::memcpy(dst + kPoolPtrsOff, &r, sizeof r);
-        }
-    }
-    std::memcpy(dst, &hdr, sizeof hdr);
-}
-
 // Section 2.2 S1-S4.  Ages a in years, formation times t = T0 - a with T0 the oldest edge; the
 // mass formed in bin [a_lo, a_hi) is the integral of the rate over t in [T0 - a_hi, T0 - a_lo].
 bool sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *edges, double *out) {

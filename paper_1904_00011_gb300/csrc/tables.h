@@ -27,9 +27,6 @@ struct Model {
 };
 
 void stirlerr_table(float out[16]);
-// Total-count sampler region of one dust half (layout: PoolHdr in pcmd_internal.h) from the FP32
-// lambdas of its P points; dst holds pool_region_bytes(P) bytes.
-void build_pool(const float *lam, uint32_t P, uint8_t *dst);
 // Parametric SFH on an age grid (PCMD_SFH_*): log10 stars per bin; false on bad input.
 bool sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *edges, double *out);
 

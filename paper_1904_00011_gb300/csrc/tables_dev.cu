@@ -66,6 +66,28 @@ __device__ __forceinline__ uint32_t thresholds_dev(float lam_f, F &&f) {
     return z0;
 }
 
+// Transformed-rejection record of one Poisson mean (constants of the setup in FP64, stored FP32).
+__device__ __forceinline__ PtrsRec ptrs_record(float lam_f, uint32_t i, const float *fl, int nfl) {
+    const double lam = (double)lam_f;
+    const double slam = __dsqrt_rn(lam);
+    const double bb = __dadd_rn(0.931, __dmul_rn(2.53, slam));
+    const double aa = __dadd_rn(-0.059, __dmul_rn(0.02483, bb));
+    const double inv_alpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dsub_rn(bb, 3.4)));
+    const double vr = __dsub_rn(0.9277, __ddiv_rn(3.6224, __dsub_rn(bb, 2.0)));
+    PtrsRec r;
+    r.i = i;
+    r.lam = lam_f;
+    r.b = (float)bb;
+    r.a = (float)aa;
+    r.twoa = (float)__dmul_rn(2.0, aa);
+    r.vr = (float)vr;
+    r.log_ia = (float)log(inv_alpha);
+#pragma unroll
+    for (int b = 0; b < kMaxBands; ++b) r.flux[b] = b < nfl ? fl[b] : 0.0f;
+    r.pad = 0u;
+    return r;
+}
+
 // Per point: class (0 none, 1 inversion, 2 transformed rejection), tail length, lambda.
 struct PointCls {
     int cls;
@@ -108,6 +130,47 @@ __device__ __forceinline__ uint32_t group_scan(uint32_t v, int j, uint32_t &tota
     return s - v;
 }
 
+// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 10 (exact:
+// lambda 2^40 is exact in FP64), 0 otherwise; a point is in the pool when L > 0.
+__device__ __forceinline__ uint64_t pool_weight(const PointIn &p) {
+    if (!p.valid || !(p.lam > 0.0f) || !(p.lam < kPtrsThreshold)) return 0ull;
+    return __double2ull_rz(__dmul_rn((double)p.lam, kPoolFix));
+}
+
+// Inclusive prefix sum of a 64-bit value over the 16 lanes of a group, and the group total.
+__device__ __forceinline__ uint64_t group_scan64(uint64_t v, int j, uint64_t &total) {
+    uint64_t s = v;
+#pragma unroll
+    for (int o = 1; o < kGroup; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, s, o, kGroup);
+        if (j >= o) s += u;
+    }
+    total = __shfl_sync(0xffffffffu, s, kGroup - 1, kGroup);
+    return s;
+}
+
+// T = min(floor(C 2^32 / L), 2^32 - 1) for 0 <= C <= L, L > 0, exactly: an FP64 estimate (off
+// by less than 2), corrected against the exact 128-bit products.
+__device__ __forceinline__ uint32_t pool_threshold(uint64_t C, uint64_t L) {
+    const double e = floor(__dmul_rn(__ddiv_rn(__ull2double_rn(C), __ull2double_rn(L)), 4294967296.0));
+    uint64_t q = (uint64_t)e;
+    const unsigned __int128 num = (unsigned __int128)C << 32;
+    unsigned __int128 m = (unsigned __int128)q * L;
+    for (int it = 0; it < 4 && m > num; ++it) {
+        --q;
+        m -= L;
+    }
+    for (int it = 0; it < 4 && num - m >= L; ++it) {
+        ++q;
+        m += L;
+    }
+    return q >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)q;
+}
+
+__device__ __forceinline__ uint4 *pool_scratch(const TabArgs &a, int s, int h) {
+    return a.pool_scratch + ((size_t)s * 2 + h) * a.G;
+}
+
 __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const int h = blockIdx.y, s = blockIdx.z;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,6 +188,13 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     if (j == 0 && g < a.G) {
         const uint32_t cls = act == 0u ? 0u : (dense ? 2u : 1u);
         a.scratch[((size_t)s * 2 + h) * a.G + g] = make_uint4(cls, n_tail, n_ptrs, 0u);
+    }
+    if (a.pool) {
+        const uint64_t wq = pool_weight(p);
+        const uint32_t n = __popc(__ballot_sync(0xffffffffu, wq > 0ull) >> (threadIdx.x & 16u) & 0xFFFFu);
+        uint64_t sum;
+        group_scan64(wq, j, sum);
+        if (j == 0 && g < a.G) pool_scratch(a, s, h)[g] = make_uint4(n, (uint32_t)sum, (uint32_t)(sum >> 32), 0u);
     }
 }
 
@@ -170,6 +240,58 @@ __device__ __forceinline__ uint4 block_scan4(uint4 v, uint4 &total, uint4 *ws) {
     return r;
 }
 
+// Block-wide exclusive scan of a 64-bit value, 1024 threads.
+__device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t &total, uint64_t *ws) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t x = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += x;
+    }
+    if (lane == 31) ws[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t u = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0ull;
+        const uint64_t u0 = u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t x = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += x;
+        }
+        ws[lane] = u - u0;
+        if (lane == 31) ws[32] = u;
+    }
+    __syncthreads();
+    const uint64_t r = ws[w] + s - v;
+    total = ws[32];
+    __syncthreads();
+    return r;
+}
+
+// Header of a total-count sampler region: pool size n, Lambda = (float)(Lfix 2^-40) (the FP64
+// conversion rounds to nearest), the draw of the total (inversion thresholds below 10, a
+// transformed-rejection record at and above), and the fixed-point total itself.
+__device__ void write_pool_header(uint8_t *pr, uint32_t P, uint32_t n, uint64_t lfix) {
+    *reinterpret_cast<uint64_t *>(pr + pool_fix_off(P)) = lfix;
+    PoolHdr hdr{0.0f, n, 0u, 0u};
+    if (n > 0) {
+        hdr.lam = __double2float_rn(__dmul_rn(__ull2double_rn(lfix), 1.0 / kPoolFix));
+        if (hdr.lam < kPtrsThreshold) {
+            hdr.mode = 1u;
+            uint32_t *z = reinterpret_cast<uint32_t *>(pr + kPoolZOff);
+            thresholds_dev(hdr.lam, [&](int k, uint32_t zk) {
+                z[k] = zk;
+                hdr.n_z = (uint32_t)k + 1u;
+            });
+        } else {
+            hdr.mode = 2u;
+            *reinterpret_cast<PtrsRec *>(pr + kPoolPtrsOff) = ptrs_record(hdr.lam, 0xFFFFFFFFu, nullptr, 0);
+        }
+    }
+    *reinterpret_cast<PoolHdr *>(pr) = hdr;
+}
+
 // Per model and half: positions of the group records (sparse list, dense list), tail offsets
 // and transformed-rejection offsets, in group order; the list lengths go to the descriptor.
 __global__ void __launch_bounds__(1024) tab_scan_kernel(const TabArgs a) {
@@ -198,6 +320,27 @@ __global__ void __launch_bounds__(1024) tab_scan_kernel(const TabArgs a) {
         d->n_dense[h] = carry.y;
         d->n_ptrs[h] = carry.w;
     }
+    if (!a.pool) return;
+    // total-count sampler: pool positions and fixed-point cumulative sums of every group
+    __shared__ uint64_t ws64[33];
+    uint4 *ps = pool_scratch(a, s, h);
+    uint32_t pn = 0;
+    uint64_t pc = 0;
+    for (uint32_t g0 = 0; g0 < a.G; g0 += blockDim.x) {
+        const uint32_t g = g0 + threadIdx.x;
+        const uint4 c = g < a.G ? ps[g] : make_uint4(0, 0, 0, 0);
+        uint4 tot;
+        const uint4 e = block_scan4(make_uint4(c.x, 0, 0, 0), tot, ws);
+        uint64_t tot64;
+        const uint64_t e64 = block_scan64((uint64_t)c.y | (uint64_t)c.z << 32, tot64, ws64);
+        if (g < a.G) {
+            const uint64_t base = pc + e64;
+            ps[g] = make_uint4(pn + e.x, (uint32_t)base, (uint32_t)(base >> 32), 0u);
+        }
+        pn += tot.x;
+        pc += tot64;
+    }
+    if (threadIdx.x == 0) write_pool_header(a.tables + a.sets[s].base + a.layout.pool_off[h], a.P, pn, pc);
 }
 
 __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
@@ -255,23 +398,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
 
     // transformed-rejection record
     if (p.valid && p.lam >= kPtrsThreshold) {
-        const double lam = (double)p.lam;
-        const double slam = __dsqrt_rn(lam);
-        const double bb = __dadd_rn(0.931, __dmul_rn(2.53, slam));
-        const double aa = __dadd_rn(-0.059, __dmul_rn(0.02483, bb));
-        const double inv_alpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dsub_rn(bb, 3.4)));
-        const double vr = __dsub_rn(0.9277, __ddiv_rn(3.6224, __dsub_rn(bb, 2.0)));
-        PtrsRec r;
-        r.i = p.i;
-        r.lam = p.lam;
-        r.b = (float)bb;
-        r.a = (float)aa;
-        r.twoa = (float)__dmul_rn(2.0, aa);
-        r.vr = (float)vr;
-        r.log_ia = (float)log(inv_alpha);
-#pragma unroll
-        for (int b = 0; b < kMaxBands; ++b) r.flux[b] = fl[b];
-        r.pad = 0u;
+        const PtrsRec r = ptrs_record(p.lam, p.i, fl, kMaxBands);
         PtrsRec *dst = reinterpret_cast<PtrsRec *>(tab + L.ptrs_off[h]) + sc.w + my_ptrs;
         const uint4 *src4 = reinterpret_cast<const uint4 *>(&r);
         uint4 *dst4 = reinterpret_cast<uint4 *>(dst);
@@ -294,6 +421,25 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         for (int b = 0; b < B; ++b) f[b] = fl[b];
     }
 
+    // total-count sampler: this point's pool entry (point index, star-assignment threshold)
+    if (a.pool) {
+        const uint64_t wq = in_range ? pool_weight(p) : 0ull;
+        uint32_t n_in_group;
+        const uint32_t my_pos = group_scan(wq > 0ull ? 1u : 0u, j, n_in_group);
+        uint64_t w_in_group;
+        const uint64_t my_c = group_scan64(wq, j, w_in_group);
+        if (wq > 0ull) {
+            uint8_t *pr = tab + L.pool_off[h];
+            const uint4 ps = pool_scratch(a, s, h)[g];
+            const uint32_t n = reinterpret_cast<const PoolHdr *>(pr)->n;
+            const uint64_t lfix = *reinterpret_cast<const uint64_t *>(pr + pool_fix_off(a.P));
+            const uint64_t C = ((uint64_t)ps.y | (uint64_t)ps.z << 32) + my_c;
+            uint32_t *idx = reinterpret_cast<uint32_t *>(pr + kPoolIdxOff);
+            idx[ps.x + my_pos] = p.i;
+            idx[n + ps.x + my_pos] = pool_threshold(C, lfix);
+        }
+    }
+
     // per-point fluxes (the total-count sampler reads them by point index)
     if (p.valid && h == 0) {
         float *fo = reinterpret_cast<float *>(tab + L.flux_off) + (size_t)p.i * B;
@@ -307,6 +453,29 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         if (h == 0)
             for (int b = 0; b < B; ++b) a.insp_flux[(size_t)p.i * B + b] = fl[b];
     }
+}
+
+// Guide table of a total-count sampler region, one thread per pool entry.
+// guide[b] = first entry j < n - 1 with T_j > b 2^s (s = 32 - bits), else n - 1: entry j owns
+// the buckets with T_{j-1} <= b 2^s < T_j (T_{-1} = 0); buckets at or above T_{n-2} get n - 1.
+__global__ void __launch_bounds__(256) tab_pool_guide_kernel(const TabArgs a) {
+    const int h = blockIdx.y, s = blockIdx.z;
+    const TabSetIn in = a.sets[s];
+    uint8_t *pr = a.tables + in.base + a.layout.pool_off[h];
+    const uint32_t n = reinterpret_cast<const PoolHdr *>(pr)->n;
+    uint32_t *guide = reinterpret_cast<uint32_t *>(pr + kPoolGuideOff);
+    const uint32_t *thr = reinterpret_cast<const uint32_t *>(pr + kPoolIdxOff) + n;
+    constexpr uint32_t sh = 32 - kPoolGuideBits;
+    const uint32_t nbk = 1u << kPoolGuideBits;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t top = n > 1 ? ((uint64_t)thr[n - 2] + (1ull << sh) - 1) >> sh : 0;
+    if (t + 1 < n) {
+        const uint64_t t0 = t > 0 ? thr[t - 1] : 0u, t1 = thr[t];
+        const uint64_t b0 = (t0 + (1ull << sh) - 1) >> sh;
+        const uint64_t b1 = t1 > 0 ? ((t1 - 1) >> sh) + 1 : 0;
+        for (uint64_t b = b0; b < b1; ++b) guide[b] = t;
+    }
+    if (t <= nbk && (t >= top || t == nbk)) guide[t] = n > 0 ? n - 1 : 0u;
 }
 
 }  // namespace
@@ -340,6 +509,10 @@ cudaError_t launch_build_tables(const TabArgs &a, int n_sets, cudaStream_t st) {
     tab_count_kernel<<<grid, 256, 0, st>>>(a);
     tab_scan_kernel<<<dim3(2, n_sets), 1024, 0, st>>>(a);
     tab_write_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.pool) {
+        const uint32_t ng = (max(a.P, (1u << kPoolGuideBits) + 1) + 255) / 256;
+        tab_pool_guide_kernel<<<dim3(ng, 2, n_sets), 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ struct TabLayout {
     uint64_t ptrs_off[2];   // PtrsRec[P] per half
     uint64_t tail_off;      // uint32 [2][P][kInvCap - 2] tail thresholds
     uint64_t flux_off;      // float [P][B] electrons per star
-    uint64_t pool_off[2];   // total-count sampler regions (written by the host when used)
+    uint64_t pool_off[2];   // total-count sampler regions (written only when the sampler is used)
     uint64_t bytes;         // table size (256-byte multiple)
 };
 
@@ -43,6 +43,8 @@ struct TabArgs {
     float *insp_lam;            // optional parity copies of model 0: lambda [2][P]
     float *insp_flux;           //   flux [P][B]
     uint32_t *insp_z0;          //   Z_0 [2][P] (0xFFFFFFFF unless 0 < lambda < 10)
+    int pool;                   // also build the total-count sampler regions
+    uint4 *pool_scratch;        // [n_sets][2][G] pool entries and fixed-point sums (pool only)
 };
 
 TabLayout tab_layout(uint32_t P, int n_bands);

@@ -90,3 +90,34 @@ def test_pool_without_pool_points_draws_nothing_from_it():
         big = lam_h >= 10
         for h in range(2):
             assert np.array_equal(ca[:, h, big[h]], cb[:, h, big[h]])
+
+
+def test_pool_tables_assign_stars_in_proportion_to_lambda():
+    """Star-assignment thresholds: entry j takes the words in [T_{j-1}, T_j), so its probability
+    (T_j - T_{j-1}) / 2^32 is lambda_j / sum(lambda) up to the 2^-32 grid and the 2^-40 weights;
+    the pool is exactly the points with 0 < lambda < 10 (and lambda >= 2^-40), in point order."""
+    rng = np.random.default_rng(5)
+    lam = np.concatenate([rng.gamma(0.3, 0.5, 3000), [0.0, 12.0, 10.0, 9.999, 1e-13, 3e-12],
+                          10.0 ** rng.uniform(-9, 0.9, 2000)]).astype(np.float32)
+    rng.shuffle(lam)
+    idx, thr, tot = O.pool_tables(lam)
+    keep = np.flatnonzero((lam > 0) & (lam < 10) & (lam.astype(np.float64) >= 2.0 ** -40))
+    assert np.array_equal(idx, keep)
+    l64 = lam[idx].astype(np.float64)
+    assert abs(tot / l64.sum() - 1.0) < 1e-6
+    prev = np.concatenate([[0], thr[:-1].astype(np.int64)])
+    p = (thr.astype(np.int64) - prev) / 2.0 ** 32
+    p[-1] = 1.0 - prev[-1] / 2.0 ** 32                 # the last entry takes the rest
+    assert np.all(np.diff(thr[:-1].astype(np.int64)) >= 0)
+    assert np.all(np.abs(p - l64 / l64.sum()) <= 2.0 ** -31)
+
+
+def test_pool_tables_small_cases_are_exact():
+    """lambda = (1, 3): T_0 = 2^32 / 4 exactly; one entry: it takes every star; nothing below
+    2^-40 or at 10: an empty pool."""
+    idx, thr, tot = O.pool_tables(np.array([1.0, 3.0], np.float32))
+    assert list(idx) == [0, 1] and int(thr[0]) == 2 ** 30 and int(thr[1]) == 2 ** 32 - 1 and tot == 4.0
+    idx, thr, tot = O.pool_tables(np.array([0.0, 0.25, 20.0], np.float32))
+    assert list(idx) == [1] and tot == 0.25
+    idx, thr, tot = O.pool_tables(np.array([1e-13, 10.0, 0.0], np.float32))
+    assert idx.size == 0
