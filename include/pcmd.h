@@ -74,7 +74,7 @@ typedef struct {
     int n_bands;                 /* 2..PCMD_MAX_BANDS; band 0 = magnitude axis, colour = m1 - m0 */
     int n_ages, n_feh, n_mass;   /* isochrone grid: n_ages <= PCMD_MAX_SFH */
     const double *log_age;       /* h_[n_ages] log10 age of each SFH bin's isochrone (informational) */
-    const double *feh_grid;      /* h_[n_feh] [Fe/H] of the isochrones (Section 2.2 M2/M3) */
+    const double *feh_grid;      /* h_[n_feh] [Fe/H] of the isochrones, strictly ascending (Section 2.2) */
     const double *mass;          /* h_[n_ages][n_feh][n_mass] initial masses, ascending, > 0 */
     const double *abs_mag;       /* h_[n_ages][n_feh][n_mass][n_bands] absolute magnitudes */
     double imf_slope;            /* Salpeter 2.35 (Section 2.2) */
@@ -101,9 +101,13 @@ typedef struct {
                                   * holds [16][n_bands][psf_size][psf_size], region r = 4 ry + rx */
 } pcmd_config;
 
-/* Free parameters of one model (Table 1): S5 non-parametric SFH, M2/M3 Gaussian MDF
- * (feh_sigma <= 0: all weight on the grid [Fe/H] nearest feh_mean), E1-E3 dust screen,
- * D2 distance modulus. */
+/* Free parameters of one model (Table 1): S5 non-parametric SFH, M2/M3 Gaussian MDF, E1-E3
+ * dust screen, D2 distance modulus.  feh_sigma <= 0 selects M1 (Section 2.2, single [Fe/H]):
+ * every star has [Fe/H] = feh_mean, on an isochrone interpolated between the grid isochrones
+ * k and k + 1 around it (feh_grid[k] <= feh_mean < feh_grid[k + 1], t = (feh_mean -
+ * feh_grid[k]) / (feh_grid[k + 1] - feh_grid[k])): each mass point's initial mass and absolute
+ * magnitudes are (1 - t) x + t y of the same point of the two grid isochrones; outside the grid
+ * the end isochrone is used. */
 typedef struct {
     double log_sfh[PCMD_MAX_SFH];  /* log10 stars per pixel formed in each age bin (n_ages used) */
     double feh_mean, feh_sigma;

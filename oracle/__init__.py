@@ -178,11 +178,45 @@ def draw(lam: float, seed: int, pix: int, i: int, set_id: int, half: int) -> int
 # model tables
 # ----------------------------------------------------------------------------------------
 
+def m1_bracket(feh: np.ndarray, mu: float) -> Tuple[int, float]:
+    """M1, one [Fe/H] (Section 2.2: isochrones interpolated between grid metallicities): the
+    grid isochrone k with feh[k] <= mu < feh[k + 1] and the fraction t of the way to k + 1;
+    outside the grid, the end isochrone with t = 0."""
+    feh = np.asarray(feh, np.float64)
+    nf = feh.size
+    if nf == 1 or mu <= feh[0]:
+        return 0, 0.0
+    if mu >= feh[-1]:
+        return nf - 1, 0.0
+    k = int(np.nonzero(feh[:-1] <= mu)[0][-1])
+    return k, float((mu - feh[k]) / (feh[k + 1] - feh[k]))
+
+
+def model_isochrones(w, params) -> Tuple[np.ndarray, np.ndarray, float]:
+    """(mass, abs_mag, [Fe/H] selector) that the weights and fluxes of one parameter set use.
+    M2/M3 (feh_sigma > 0): the grid as it is.  M1 (feh_sigma <= 0): grid slot k holds the
+    isochrone at [Fe/H] = feh_mean, every mass point's initial mass and absolute magnitudes
+    linearly interpolated in [Fe/H] between the same point of grid isochrones k and k + 1,
+    and the selector is feh[k] (all weight on that slot)."""
+    iso = w.iso
+    mass = np.array(iso.mass, np.float64)
+    mags = np.array(iso.abs_mag, np.float64)
+    if params.feh_sigma > 0.0:
+        return mass, mags, params.feh_mean
+    k, t = m1_bracket(iso.feh, params.feh_mean)
+    if t > 0.0:
+        u = 1.0 - t
+        mass[:, k] = u * iso.mass[:, k] + t * iso.mass[:, k + 1]
+        mags[:, k] = u * iso.abs_mag[:, k] + t * iso.abs_mag[:, k + 1]
+    return mass, mags, float(iso.feh[k])
+
+
 def weights(w, params) -> np.ndarray:
     """FP64 lambda[n_ages, n_feh, n_mass] of one parameter set (sums to Npix)."""
     iso = w.iso
     na, nf, nm = iso.mass.shape
-    mass = np.ascontiguousarray(iso.mass, np.float64)
+    mass, _, feh_sel = model_isochrones(w, params)
+    mass = np.ascontiguousarray(mass)
     feh = np.ascontiguousarray(iso.feh, np.float64)
     sfh = np.ascontiguousarray(params.log_sfh, np.float64)
     if sfh.size != na:
@@ -190,7 +224,7 @@ def weights(w, params) -> np.ndarray:
     out = np.zeros((na, nf, nm))
     lib().or_weights(na, nf, nm, _p(mass, ctypes.c_double), w.imf_slope, int(getattr(w, "imf", 0)),
                      _p(feh, ctypes.c_double),
-                     _p(sfh, ctypes.c_double), params.feh_mean, params.feh_sigma, w.mdf_cut,
+                     _p(sfh, ctypes.c_double), feh_sel, params.feh_sigma, w.mdf_cut,
                      _p(out, ctypes.c_double))
     return out
 
@@ -198,7 +232,8 @@ def weights(w, params) -> np.ndarray:
 def fluxes(w, params) -> np.ndarray:
     """FP64 electrons per star [n_points, n_bands]."""
     nb = w.n_bands
-    mags = np.ascontiguousarray(w.iso.abs_mag.reshape(-1, nb), np.float64)
+    _, mags, _ = model_isochrones(w, params)
+    mags = np.ascontiguousarray(mags.reshape(-1, nb), np.float64)
     zp = np.ascontiguousarray(w.zeropoint[:nb], np.float64)
     et = np.ascontiguousarray(w.exptime[:nb], np.float64)
     out = np.zeros((mags.shape[0], nb))

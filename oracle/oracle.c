@@ -287,6 +287,7 @@ uint32_t or_draw(float lam, uint64_t seed, uint32_t pix, uint32_t i, uint32_t se
  *  SFH_j  = 10^log_sfh[j]                      (S5: log stars per pixel formed in bin j)
  *  MDF_k  = Gaussian density at the grid [Fe/H], normalised, weights < mdf_cut removed,
  *           renormalised (M2/M3); feh_sigma <= 0 puts all weight on the nearest grid point
+ *           (M1: the Python layer first puts the interpolated isochrone in that slot)
  *  IMF_i  = integral of m^-slope over the mass cell of point i (cells bounded by geometric
  *           midpoints), normalised over the isochrone (Salpeter slope 2.35).  */
 /* Kroupa (2001) IMF over [a, b]: dN/dm proportional to m^-0.3 below 0.08 Msun, m^-1.3 from 0.08 to

@@ -241,13 +241,38 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         CK(cudaEventSynchronize(ctx->staged));
         ctx->staged_pending = false;
     }
+    // M1 models whose [Fe/H] falls between grid points get their own interpolated isochrones
+    std::vector<int> m1_k(n_sets, -1);
+    std::vector<double> m1_t(n_sets, 0.0);
+    uint32_t n_m1 = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        if (p[s].feh_sigma > 0.0) continue;
+        double t;
+        const int k = m.m1_bracket(p[s].feh_mean, t);
+        if (t > 0.0) {
+            m1_k[s] = k;
+            m1_t[s] = t;
+            ++n_m1;
+        }
+    }
+    const size_t iso_pts = (size_t)m.n_ages * m.n_mass;
     const size_t in_bytes = sizeof(TabSetIn) * n_sets, w_bytes = sizeof(double) * (size_t)nw * n_sets;
-    CK(ctx->h_tab_in.ensure(in_bytes + w_bytes));
+    const size_t m1_bytes = sizeof(double) * iso_pts * (1 + B) * n_m1;
+    CK(ctx->h_tab_in.ensure(in_bytes + w_bytes + m1_bytes));
     TabSetIn *tin = ctx->h_tab_in.as<TabSetIn>();
     double *wts = reinterpret_cast<double *>(ctx->h_tab_in.as<uint8_t>() + in_bytes);
+    double *m1_imf = wts + (size_t)nw * n_sets, *m1_flux = m1_imf + iso_pts * n_m1;
     std::vector<double> mdf;
     uint64_t img_off = 0;
+    uint32_t m1_i = 0;
     for (int s = 0; s < n_sets; ++s) {
+        tin[s].m1_k = m1_k[s];
+        tin[s].m1_off = 0;
+        if (m1_k[s] >= 0) {
+            tin[s].m1_off = (uint32_t)(m1_i * iso_pts);
+            m.m1_isochrone(m1_k[s], m1_t[s], m1_imf + m1_i * iso_pts, m1_flux + m1_i * iso_pts * B);
+            ++m1_i;
+        }
         m.mdf_weights(p[s].feh_mean, p[s].feh_sigma, mdf);
         double *w = wts + (size_t)s * nw;
         for (int j = 0; j < m.n_ages; ++j) {
@@ -298,7 +323,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
     CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
-    CK(ctx->tab_in.ensure(in_bytes + w_bytes));
+    CK(ctx->tab_in.ensure(in_bytes + w_bytes + m1_bytes));
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
     CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets * n_scr));
     CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
@@ -307,7 +332,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::memcpy(ctx->h_desc.p, ctx->descs.data(), sizeof(SetDesc) * n_sets);
     std::memcpy(ctx->h_items.p, ctx->item_list.data(), sizeof(uint2) * n_items);
     std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
-    CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, in_bytes + w_bytes, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, in_bytes + w_bytes + m1_bytes, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
@@ -322,11 +347,14 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
     ta.imf = ctx->imf_d.as<double>();
     ta.base_flux = ctx->bflux_d.as<double>();
+    ta.m1_imf = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes + w_bytes);
+    ta.m1_flux = ta.m1_imf + iso_pts * n_m1;
     ta.hf[0] = hf[0];
     ta.hf[1] = hf[1];
     ta.P = P;
     ta.G = G;
     ta.n_mass = m.n_mass;
+    ta.n_feh = m.n_feh;
     ta.n_bands = B;
     ta.layout = L;
     ta.scratch = ctx->tab_scratch.as<uint4>();
@@ -414,7 +442,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
             if (!is_fin(c.abs_mag[i * c.n_bands + b])) return PCMD_ERR_ARG;
     }
     for (int k = 0; k < c.n_feh; ++k)
-        if (!is_fin(c.feh_grid[k])) return PCMD_ERR_ARG;
+        if (!is_fin(c.feh_grid[k]) || (k > 0 && !(c.feh_grid[k] > c.feh_grid[k - 1]))) return PCMD_ERR_ARG;
 
     pcmd_ctx *ctx = new pcmd_ctx();
     ctx->cfg = c;

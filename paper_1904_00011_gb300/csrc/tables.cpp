@@ -5,7 +5,8 @@
 // Weights (Section 2.1, Section 2.2): lambda_jki = SFH_j * MDF_k * IMF_jk,i with
 //   SFH_j  = 10^log_sfh_j                          (S5, stars per pixel formed in bin j)
 //   MDF_k  = exp(-((feh_k - mu)/sigma)^2 / 2) normalised over the grid, weights < mdf_cut
-//            removed and renormalised (M2/M3); sigma <= 0 selects the nearest grid point
+//            removed and renormalised (M2/M3); sigma <= 0 is M1: one [Fe/H], the isochrone
+//            interpolated between the two grid isochrones around it (m1_isochrone)
 //   IMF_i  = integral of m^-slope over [e_i, e_i+1], e the geometric midpoints of the masses
 //            (outer edges mirrored), normalised over the isochrone (Salpeter)
 #include "tables.h"
@@ -35,37 +36,42 @@ static double kroupa_cell(double a, double b) {
     return s;
 }
 
+// IMF weights of one isochrone's mass points: the integral of the IMF over each point's cell
+// (bounded by the geometric midpoints of neighbouring masses, outer edges mirrored),
+// normalised over the isochrone.
+static void imf_of_isochrone(const double *m, int n_mass, double slope, int kind, double *out) {
+    if (n_mass == 1) {
+        out[0] = 1.0;
+        return;
+    }
+    std::vector<double> omega(n_mass), edge(n_mass + 1);
+    for (int i = 1; i < n_mass; ++i) edge[i] = std::sqrt(m[i - 1] * m[i]);
+    edge[0] = m[0] * m[0] / edge[1];
+    edge[n_mass] = m[n_mass - 1] * m[n_mass - 1] / edge[n_mass - 1];
+    const double a1 = 1.0 - slope;
+    double s = 0.0;
+    for (int i = 0; i < n_mass; ++i) {
+        double w;
+        if (kind == PCMD_IMF_KROUPA) {
+            w = kroupa_cell(edge[i], edge[i + 1]);
+        } else if (a1 != 0.0) {
+            w = std::pow(edge[i + 1], a1) - std::pow(edge[i], a1);
+            w = w / a1;
+        } else {
+            w = std::log(edge[i + 1] / edge[i]);
+        }
+        omega[i] = w;
+        s = s + w;
+    }
+    for (int i = 0; i < n_mass; ++i) out[i] = omega[i] / s;
+}
+
 void Model::build_imf() {
     imf.assign((size_t)n_ages * n_feh * n_mass, 0.0);
-    std::vector<double> omega(n_mass), edge(n_mass + 1);
     for (int j = 0; j < n_ages; ++j)
         for (int k = 0; k < n_feh; ++k) {
-            const double *m = &mass[((size_t)j * n_feh + k) * n_mass];
-            double s = 0.0;
-            if (n_mass == 1) {
-                omega[0] = 1.0;
-                s = 1.0;
-            } else {
-                for (int i = 1; i < n_mass; ++i) edge[i] = std::sqrt(m[i - 1] * m[i]);
-                edge[0] = m[0] * m[0] / edge[1];
-                edge[n_mass] = m[n_mass - 1] * m[n_mass - 1] / edge[n_mass - 1];
-                const double a1 = 1.0 - imf_slope;
-                for (int i = 0; i < n_mass; ++i) {
-                    double w;
-                    if (imf_kind == PCMD_IMF_KROUPA) {
-                        w = kroupa_cell(edge[i], edge[i + 1]);
-                    } else if (a1 != 0.0) {
-                        w = std::pow(edge[i + 1], a1) - std::pow(edge[i], a1);
-                        w = w / a1;
-                    } else {
-                        w = std::log(edge[i + 1] / edge[i]);
-                    }
-                    omega[i] = w;
-                    s = s + w;
-                }
-            }
-            double *out = &imf[((size_t)j * n_feh + k) * n_mass];
-            for (int i = 0; i < n_mass; ++i) out[i] = omega[i] / s;
+            const size_t o = ((size_t)j * n_feh + k) * n_mass;
+            imf_of_isochrone(&mass[o], n_mass, imf_slope, imf_kind, &imf[o]);
         }
 }
 
@@ -87,13 +93,47 @@ void Model::mdf_weights(double mu, double sigma, std::vector<double> &w) const {
         }
         for (int k = 0; k < n_feh; ++k) w[k] = w[k] / s2;
     } else {
-        int best = 0;
-        for (int k = 1; k < n_feh; ++k)
-            if (std::fabs(feh[k] - mu) < std::fabs(feh[best] - mu)) best = k;
-        w[best] = 1.0;
+        double t;
+        w[m1_bracket(mu, t)] = 1.0;
     }
 }
 
+// M1 (Section 2.2): the grid isochrone k at or below mu and the fraction t in [0, 1) of the way
+// to isochrone k + 1; mu outside the grid takes the end isochrone (t = 0).
+int Model::m1_bracket(double mu, double &t) const {
+    t = 0.0;
+    if (n_feh == 1 || mu <= feh[0]) return 0;
+    if (mu >= feh[n_feh - 1]) return n_feh - 1;
+    int k = 0;
+    while (k + 2 < n_feh && feh[k + 1] <= mu) ++k;
+    t = (mu - feh[k]) / (feh[k + 1] - feh[k]);
+    return k;
+}
+
+// The isochrones of [Fe/H] = feh_k + t (feh_k+1 - feh_k), one per age: every mass point's
+// initial mass and absolute magnitudes interpolated linearly in [Fe/H] between the same mass
+// point of the two grid isochrones, then the IMF weights and the electrons per star of those
+// points.  imf_out[n_ages][n_mass], bflux_out[n_ages][n_mass][n_bands].
+void Model::m1_isochrone(int k, double t, double *imf_out, double *bflux_out) const {
+    std::vector<double> mi(n_mass);
+    const double u = 1.0 - t;
+    for (int j = 0; j < n_ages; ++j) {
+        const size_t o0 = ((size_t)j * n_feh + k) * n_mass, o1 = o0 + n_mass;
+        for (int i = 0; i < n_mass; ++i) mi[i] = u * mass[o0 + i] + t * mass[o1 + i];
+        imf_of_isochrone(mi.data(), n_mass, imf_slope, imf_kind, imf_out + (size_t)j * n_mass);
+        for (int i = 0; i < n_mass; ++i)
+            for (int b = 0; b < n_bands; ++b) {
+                const double mag = u * abs_mag[(o0 + i) * n_bands + b] + t * abs_mag[(o1 + i) * n_bands + b];
+                bflux_out[((size_t)j * n_mass + i) * n_bands + b] = electrons_per_star(mag, b);
+            }
+    }
+}
+
+double Model::electrons_per_star(double mag, int b) const {
+    double s = mag - zeropoint[b];
+    s = -0.4 * s;
+    return exptime[b] * std::pow(10.0, s);
+}
 
 // Electrons per star: t_b 10^(-0.4 (M_b + dmod - ZP_b)) = [t_b 10^(-0.4 (M_b - ZP_b))] 10^(-0.4 dmod);
 // the bracket is computed once per context (base_flux), the distance factor once per model.
@@ -101,11 +141,7 @@ void Model::build_base_flux() {
     const size_t P = (size_t)n_points();
     base_flux.assign(P * n_bands, 0.0);
     for (size_t i = 0; i < P; ++i)
-        for (int b = 0; b < n_bands; ++b) {
-            double s = abs_mag[i * n_bands + b] - zeropoint[b];
-            s = -0.4 * s;
-            base_flux[i * n_bands + b] = exptime[b] * std::pow(10.0, s);
-        }
+        for (int b = 0; b < n_bands; ++b) base_flux[i * n_bands + b] = electrons_per_star(abs_mag[i * n_bands + b], b);
 }
 
 void stirlerr_table(float out[16]) {

@@ -23,7 +23,10 @@ struct Model {
     int n_points() const { return n_ages * n_feh * n_mass; }
     void build_imf();
     void build_base_flux();
+    double electrons_per_star(double mag, int band) const;
     void mdf_weights(double mu, double sigma, std::vector<double> &w) const;
+    int m1_bracket(double mu, double &t) const;
+    void m1_isochrone(int k, double t, double *imf_out, double *bflux_out) const;
 };
 
 void stirlerr_table(float out[16]);

@@ -26,6 +26,23 @@ __device__ __forceinline__ uint32_t threshold_dev(double F) {
     return (uint32_t)(T - 1u);
 }
 
+// IMF weight and electrons per star (distance modulus 0) of point i: the context's arrays,
+// except in the grid slot an M1 model's interpolated isochrone replaces.
+__device__ __forceinline__ int m1_point(const TabArgs &a, const TabSetIn &in, uint32_t i) {
+    if (in.m1_k < 0) return -1;
+    const uint32_t jk = i / (uint32_t)a.n_mass;
+    if ((int)(jk % (uint32_t)a.n_feh) != in.m1_k) return -1;
+    return (int)(in.m1_off + (jk / (uint32_t)a.n_feh) * (uint32_t)a.n_mass + i % (uint32_t)a.n_mass);
+}
+__device__ __forceinline__ double imf_of(const TabArgs &a, const TabSetIn &in, uint32_t i) {
+    const int q = m1_point(a, in, i);
+    return q < 0 ? a.imf[i] : a.m1_imf[q];
+}
+__device__ __forceinline__ double base_flux_of(const TabArgs &a, const TabSetIn &in, uint32_t i, int b) {
+    const int q = m1_point(a, in, i);
+    return q < 0 ? a.base_flux[(size_t)i * a.n_bands + b] : a.m1_flux[(size_t)q * a.n_bands + b];
+}
+
 struct PointIn {
     float lam;
     uint32_t i;
@@ -39,7 +56,7 @@ __device__ __forceinline__ PointIn point_of(const TabArgs &a, const TabSetIn &in
     p.lam = 0.0f;
     if (p.valid) {
         const double w = a.weights[in.w_off + p.i / (uint32_t)a.n_mass];
-        const double lam = __dmul_rn(w, a.imf[p.i]);
+        const double lam = __dmul_rn(w, imf_of(a, in, p.i));
         p.lam = (float)__dmul_rn(lam, a.hf[h]);
     }
     return p;
@@ -393,7 +410,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     if (p.valid) {
 #pragma unroll
         for (int b = 0; b < kMaxBands; ++b)
-            if (b < B) fl[b] = (float)__dmul_rn(a.base_flux[(size_t)p.i * B + b], in.flux_factor);
+            if (b < B) fl[b] = (float)__dmul_rn(base_flux_of(a, in, p.i, b), in.flux_factor);
     }
 
     // transformed-rejection record

@@ -25,6 +25,8 @@ struct TabSetIn {
     uint64_t base;          // byte offset of the model's table in the table buffer
     double flux_factor;     // 10^(-0.4 dmod)
     uint32_t w_off;         // first weight w_jk = SFH_j MDF_k of the model in `weights`
+    int32_t m1_k;           // M1 interpolated isochrone: the grid slot it replaces, or -1
+    uint32_t m1_off;        // its first point in `m1_imf` (n_ages * n_mass points per model)
     uint32_t pad;
 };
 
@@ -35,9 +37,11 @@ struct TabArgs {
     const double *weights;      // [n_sets][n_ages * n_feh]
     const double *imf;          // [P] IMF weight of each point (per context)
     const double *base_flux;    // [P][B] electrons per star at distance modulus 0 (per context)
+    const double *m1_imf;       // [models with M1 interpolation][n_ages][n_mass] IMF weights
+    const double *m1_flux;      //   [..][n_ages][n_mass][B] electrons per star at modulus 0
     double hf[2];               // dust-half factors of lambda: (1, 0), (0, 1) or (1 - F, F)
     uint32_t P, G;
-    int n_mass, n_bands;
+    int n_mass, n_feh, n_bands;
     TabLayout layout;
     uint4 *scratch;             // [n_sets][2][G]
     float *insp_lam;            // optional parity copies of model 0: lambda [2][P]

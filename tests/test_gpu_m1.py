@@ -1,0 +1,94 @@
+"""M1, one [Fe/H] on an interpolated isochrone (Section 2.2), through the C ABI against the
+oracle: tables (FP32 means bit-exact, fluxes within one FP32 unit, inversion boundaries), star
+counts bit-exact on sampled pixels of the 256x256 full model, and a batch mixing M1 and M2
+models equal to the per-model path."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1904_00011_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_00011_gb300 import build
+    build.build()
+    O.build()
+
+
+def _m1(w, mu):
+    p = dataclasses.replace(w.params[0], feh_mean=mu, feh_sigma=0.0)
+    return W.with_params(w, [p], [w.n_im])
+
+
+@pytest.mark.parametrize("mu", [-0.43, -0.8, -0.21, -0.5])
+def test_m1_tables_match_oracle(mu):
+    import paper_1904_00011_gb300 as P
+    w = _m1(W.full(), mu)
+    s = P.Simulator(w, max_sets=1)
+    lam, flux, z0 = s.tables(w.params[0])
+    lam_o, flux_o, _ = O.tables(w)
+    assert np.array_equal(lam, lam_o)
+    f32 = flux_o.astype(np.float32)
+    assert np.all(np.abs(flux.view(np.int32) - f32.view(np.int32)) <= 1)
+    rng = np.random.default_rng(1)
+    for h in range(2):
+        idx = np.nonzero((lam[h] > 0) & (lam[h] < 10))[0]
+        for i in rng.choice(idx, size=min(40, idx.size), replace=False):
+            assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i])) == 0
+            if z0[h, i] < 0xFFFFFFFF:
+                assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i]) + 1) >= 1
+
+
+def test_m1_counts_full_sampled_pixels():
+    import paper_1904_00011_gb300 as P
+    w = _m1(W.full(), -0.43)
+    s = P.Simulator(w, max_sets=1, max_im=256)
+    for (p0, n) in [(0, 64), (40000, 64), (65536 - 50, 50)]:
+        got = s.counts(w.params[0], 256, 5, p0, n).cpu().numpy().view(np.uint32)
+        _, ref = O.simulate(w, 0, 5, pix_begin=p0, pix_end=p0 + n, counts=True, n_im=256, n_threads=8)
+        bad = np.argwhere(got != ref)
+        assert bad.size == 0, bad[:5]
+
+
+def test_m1_and_m2_models_in_one_batch_equal_the_per_model_path():
+    import paper_1904_00011_gb300 as P
+    w = W.full(n_im=64)
+    base = w.params[0]
+    ps = [dataclasses.replace(base, feh_mean=-0.43, feh_sigma=0.0),
+          dataclasses.replace(base, feh_mean=-0.45, feh_sigma=0.2),
+          dataclasses.replace(base, feh_mean=-0.71, feh_sigma=0.0),
+          dataclasses.replace(base, feh_mean=-0.5, feh_sigma=0.0),
+          dataclasses.replace(base, feh_mean=-0.26, feh_sigma=0.0)]
+    wb = W.with_params(w, ps, [64, 48, 64, 32, 64])
+    s = P.Simulator(wb, max_sets=len(ps))
+    wm = W.with_params(w, [base], [64])
+    ms = P.Simulator(wm, max_sets=1, max_im=64)
+    ms.simulate([base], [64], 99)
+    h, m, _, _ = ms.hess(1, [64])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    ll_b = s.evaluate(wb.params, wb.n_ims, mock, mom, 64 * 64, W.LL_POISSON, first_set_id=20)
+    ll_1 = [s.evaluate([wb.params[k]], [wb.n_ims[k]], mock, mom, 64 * 64, W.LL_POISSON,
+                       first_set_id=20 + k)[0] for k in range(len(ps))]
+    assert np.allclose(ll_b, ll_1, rtol=1e-12, atol=0.0)
+    # the M1 model between grid points differs from its grid neighbours
+    assert len({round(float(x), 6) for x in ll_b}) == len(ps)
+
+
+def test_descending_metallicity_grid_is_rejected():
+    import paper_1904_00011_gb300 as P
+    w = W.full(n_im=32)
+    iso = w.iso
+    rev = W.Isochrones(iso.log_age, iso.feh[::-1].copy(), iso.mass[:, ::-1].copy(),
+                       iso.abs_mag[:, ::-1].copy())
+    with pytest.raises(P.PcmdError) as e:
+        P.Simulator(dataclasses.replace(w, iso=rev), max_sets=1)
+    assert e.value.code == 1

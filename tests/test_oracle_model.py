@@ -62,10 +62,10 @@ def test_mdf_gaussian_weights_and_cut():
     ref = ref / ref.sum()
     assert keep.sum() < len(g)          # the cut removes something here
     assert np.allclose(per_feh, ref, rtol=1e-12, atol=1e-15)
-    # zero width -> nearest grid point only
+    # zero width -> M1: every star in one slot (grid -0.4, holding the isochrone at -0.33)
     p0 = dataclasses.replace(w.params[0], feh_mean=-0.33, feh_sigma=0.0)
     per0 = O.weights(w, p0).sum(axis=(0, 2))
-    assert per0[5] == pytest.approx(per0.sum()) and np.count_nonzero(per0) == 1
+    assert per0[4] == pytest.approx(per0.sum()) and np.count_nonzero(per0) == 1
 
 
 def test_flux_zero_point_closed_form():
