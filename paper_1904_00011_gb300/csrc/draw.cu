@@ -234,24 +234,22 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
         const uint4 w = philox_from_prefix_rk(pf, gid, a.rk0, a.rk1);
         const uint32_t m0 = ge_bytes(w.x, z7.x, zh.x), m1 = ge_bytes(w.y, z7.y, zh.y);
         const uint32_t m2 = ge_bytes(w.z, z7.z, zh.z), m3 = ge_bytes(w.w, z7.w, zh.w);
-        if ((m0 | m1 | m2 | m3) & 0x80808080u) {
-            const uint32_t mw[4] = {m0 & 0x80808080u, m1 & 0x80808080u, m2 & 0x80808080u, m3 & 0x80808080u};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t m = mw[k];
-                while (m) {
-                    const uint32_t bit = (uint32_t)(__ffs(m) - 1);
-                    m &= m - 1u;
-                    if (qn == kQueueCap) {
-                        drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
-                        qn = 0;
-                    }
-                    const uint32_t j = 4u * (uint32_t)k + (bit >> 3);
-                    const uint32_t hb = (word_of(w, (uint32_t)k) >> (bit - 7u)) & 0xFFu;
-                    queue[qn * blockDim.x + threadIdx.x] = (g << 12) | (j << 8) | hb;
-                    ++qn;
-                }
+        // maybe-hits of the 16 points in one word: bit 8q + k is byte q of word k (point 4k + q)
+        uint32_t hm = ((m0 & 0x80808080u) >> 7) | ((m1 & 0x80808080u) >> 6) |
+                      ((m2 & 0x80808080u) >> 5) | ((m3 & 0x80808080u) >> 4);
+        if (hm) {
+            if (qn + __popc(hm) > kQueueCap) {
+                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+                qn = 0;
             }
+            do {
+                const uint32_t bit = (uint32_t)(__ffs(hm) - 1);
+                hm &= hm - 1u;
+                const uint32_t k = bit & 7u, q = bit >> 3;
+                const uint32_t hb = (word_of(w, k) >> (8u * q)) & 0xFFu;
+                queue[qn * blockDim.x + threadIdx.x] = (g << 12) | ((4u * k + q) << 8) | hb;
+                ++qn;
+            } while (hm);
         }
     }
     if (qn) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
