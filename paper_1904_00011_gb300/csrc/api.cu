@@ -24,11 +24,13 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    uint64_t gen = 0;       // bumped on every (re)allocation: contents of an older one are gone
     cudaError_t ensure(size_t bytes) {
         if (bytes <= cap && p) return cudaSuccess;
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
+        ++gen;
         const size_t want = std::max<size_t>(bytes, 256);
         cudaError_t e = cudaMalloc(&p, want);
         if (e == cudaSuccess) cap = want;
@@ -38,6 +40,7 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
+        ++gen;
     }
     template <class T>
     T *as() const { return reinterpret_cast<T *>(p); }
@@ -97,6 +100,14 @@ struct pcmd_ctx {
     double *mom_ptr = nullptr;
     uint32_t *ctr_ptr = nullptr;
 
+    // last content uploaded to small per-shape device arrays (the upload is skipped when equal)
+    struct Uploaded {
+        const void *dev = nullptr;
+        uint64_t gen = 0;
+        std::vector<uint8_t> bytes;
+    };
+    Uploaded up_items, up_order, up_part_begin, up_part_count, up_pix_off;
+
     // graph of the fused evaluation
     cudaGraphExec_t gexec = nullptr;
     size_t gkey[12] = {0};
@@ -135,6 +146,23 @@ struct KTimer {
             return e_ == cudaErrorMemoryAllocation ? PCMD_ERR_OOM : PCMD_ERR_CUDA;  \
         }                                                                           \
     } while (0)
+
+// Asynchronous upload of a small per-shape array from pinned memory, skipped when the device
+// buffer already holds exactly these bytes.
+static cudaError_t upload_if_changed(pcmd_ctx::Uploaded &u, const DevBuf &dst, const void *src, size_t n,
+                                     cudaStream_t st) {
+    if (u.dev == dst.p && u.gen == dst.gen && u.bytes.size() == n && std::memcmp(u.bytes.data(), src, n) == 0)
+        return cudaSuccess;
+    const cudaError_t e = cudaMemcpyAsync(dst.p, src, n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        u.dev = dst.p;
+        u.gen = dst.gen;
+        u.bytes.assign(static_cast<const uint8_t *>(src), static_cast<const uint8_t *>(src) + n);
+    } else {
+        u.dev = nullptr;
+    }
+    return e;
+}
 
 static pcmd_status arg_error(pcmd_ctx *ctx, const std::string &why) {
     if (ctx) ctx->err_text = why;
@@ -334,8 +362,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
     CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, in_bytes + w_bytes + m1_bytes, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * n_items, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * n_items, cudaMemcpyHostToDevice, ctx->st));
+    CK(upload_if_changed(ctx->up_items, ctx->items, ctx->h_items.p, sizeof(uint2) * n_items, ctx->st));
+    CK(upload_if_changed(ctx->up_order, ctx->order, ctx->h_order.p, sizeof(uint32_t) * n_items, ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
 
@@ -498,7 +526,7 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
             if (ctx->psf_d.ensure(ctx->psf.size() * 4) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
             if (cudaMemcpy(ctx->psf_d.p, ctx->psf.data(), ctx->psf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) { rc = PCMD_ERR_CUDA; break; }
         }
-        if (ctx->h_ll.ensure(sizeof(double) * c.max_sets) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
+        if (ctx->h_ll.ensure(sizeof(double) * c.max_sets + 16) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
         if (ctx->imf_d.ensure(sizeof(double) * P) != cudaSuccess ||
             ctx->bflux_d.ensure(sizeof(double) * P * c.n_bands) != cudaSuccess) { rc = PCMD_ERR_OOM; break; }
         if (cudaMemcpy(ctx->imf_d.p, m.imf.data(), sizeof(double) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -642,9 +670,9 @@ pcmd_status pcmd_hess(pcmd_ctx *ctx, uint32_t *d_hess, double *d_moments, uint32
     CK(ctx->part_count.ensure(sizeof(uint32_t) * n_sets));
     CK(ctx->pix_off.ensure(sizeof(uint64_t) * n_sets));
     CK(ctx->partials.ensure(sizeof(double) * 3 * (size_t)cps * n_sets));
-    CK(cudaMemcpyAsync(ctx->part_begin.p, hb, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->part_count.p, hc, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->pix_off.p, hp, sizeof(uint64_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(upload_if_changed(ctx->up_part_begin, ctx->part_begin, hb, sizeof(uint32_t) * n_sets, ctx->st));
+    CK(upload_if_changed(ctx->up_part_count, ctx->part_count, hc, sizeof(uint32_t) * n_sets, ctx->st));
+    CK(upload_if_changed(ctx->up_pix_off, ctx->pix_off, hp, sizeof(uint64_t) * n_sets, ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
     CK(cudaMemsetAsync(hh, 0, sizeof(uint32_t) * nbins * n_sets, ctx->st));
@@ -700,6 +728,25 @@ pcmd_status pcmd_sync(pcmd_ctx *ctx) {
     return PCMD_OK;
 }
 
+// Likelihoods and the kernels' error word back to pinned host memory in one stream round trip.
+static pcmd_status fetch_ll(pcmd_ctx *ctx, int n_sets, double *h_ll) {
+    double *hl = ctx->h_ll.as<double>();
+    uint32_t *he = reinterpret_cast<uint32_t *>(hl + n_sets);
+    CK(cudaMemcpyAsync(hl, ctx->ll.p, sizeof(double) * n_sets, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(he, ctx->err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const uint32_t e = *he;
+    std::memcpy(h_ll, hl, sizeof(double) * n_sets);
+    if (!e) return PCMD_OK;
+    CK(cudaMemset(ctx->err.p, 0, sizeof(uint32_t)));
+    if (e & kErrTimeout) {
+        ctx->err_text = "a bounded wait inside a kernel ran out";
+        return PCMD_ERR_TIMEOUT;
+    }
+    ctx->err_text = "transformed rejection reached its attempt cap";
+    return PCMD_ERR_SAMPLER_LIMIT;
+}
+
 static pcmd_status check_mock(pcmd_ctx *ctx, const uint32_t *d_mock, const double *mom, double npix,
                               int mode, double *h_ll) {
     if (!d_mock || !mom || !h_ll) return arg_error(ctx, "mock Hess, mock moments and h_ll are required");
@@ -728,10 +775,7 @@ pcmd_status pcmd_loglike(pcmd_ctx *ctx, const uint32_t *d_mock_hess, const doubl
                           ctx->st));
         t.done(ctx->st);
     }
-    CK(cudaMemcpyAsync(ctx->h_ll.p, ctx->ll.p, sizeof(double) * n_sets, cudaMemcpyDeviceToHost, ctx->st));
-    rc = pcmd_sync(ctx);
-    std::memcpy(h_ll, ctx->h_ll.p, sizeof(double) * n_sets);
-    return rc;
+    return fetch_ll(ctx, n_sets, h_ll);
 }
 
 // Fused evaluation without a PSF: one persistent draw launch does draws, dust, noise,
@@ -754,8 +798,8 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         hb[s] = ctx->descs[s].item_begin;
         hb[n_sets + s] = ctx->descs[s].n_items;
     }
-    CK(cudaMemcpyAsync(ctx->part_begin.p, hb, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->part_count.p, hb + n_sets, sizeof(uint32_t) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(upload_if_changed(ctx->up_part_begin, ctx->part_begin, hb, sizeof(uint32_t) * n_sets, ctx->st));
+    CK(upload_if_changed(ctx->up_part_count, ctx->part_count, hb + n_sets, sizeof(uint32_t) * n_sets, ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
 
@@ -834,10 +878,7 @@ pcmd_status pcmd_evaluate(pcmd_ctx *ctx, const pcmd_params *h_params, int n_sets
     if (rc != PCMD_OK) return rc;
     rc = evaluate_fused(ctx, n_sets, d_mock_hess, h_mock_moments, mock_n_pix, mode);
     if (rc != PCMD_OK) return rc;
-    CK(cudaMemcpyAsync(ctx->h_ll.p, ctx->ll.p, sizeof(double) * n_sets, cudaMemcpyDeviceToHost, ctx->st));
-    rc = pcmd_sync(ctx);
-    std::memcpy(h_ll, ctx->h_ll.p, sizeof(double) * n_sets);
-    return rc;
+    return fetch_ll(ctx, n_sets, h_ll);
 }
 
 pcmd_status pcmd_sfh_bins(int model, const double *theta, int n_theta, int n_bins, const double *log_age_edges,
@@ -886,8 +927,8 @@ pcmd_status pcmd_counts(pcmd_ctx *ctx, const pcmd_params *h_params, int n_im, ui
     ctx->staged_pending = false;
     std::memcpy(ctx->h_items.p, sub.data(), sizeof(uint2) * sub.size());
     for (size_t i = 0; i < sub.size(); ++i) ctx->h_order.as<uint32_t>()[i] = (uint32_t)i;
-    CK(cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, sizeof(uint2) * sub.size(), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->order.p, ctx->h_order.p, sizeof(uint32_t) * sub.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(upload_if_changed(ctx->up_items, ctx->items, ctx->h_items.p, sizeof(uint2) * sub.size(), ctx->st));
+    CK(upload_if_changed(ctx->up_order, ctx->order, ctx->h_order.p, sizeof(uint32_t) * sub.size(), ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
     ctx->staged_pending = true;
     const size_t P = (size_t)ctx->model.n_points();
