@@ -80,10 +80,11 @@ struct pcmd_ctx {
     int device = 0, n_sm = 1;
     int block = 256, split = 4, chunk = 64;
 
-    DevBuf tables, desc, items, order, partials, part_begin, part_count, image, pix_off, hess,
+    SetDesc *desc_d = nullptr;  // the models' descriptors (inside tab_in, uploaded with it)
+    DevBuf tables, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
-    HostBuf h_tab_in, h_desc, h_items, h_order, h_meta, h_ll;
+    HostBuf h_tab_in, h_items, h_order, h_meta, h_ll;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     TabLayout layout;
@@ -110,7 +111,7 @@ struct pcmd_ctx {
 
     // graph of the fused evaluation
     cudaGraphExec_t gexec = nullptr;
-    size_t gkey[12] = {0};
+    std::vector<size_t> gkey;   // shape, launch and every device pointer the graph captured
 
     // kernel timing (pcmd_profile)
     bool profiling = false;
@@ -286,7 +287,9 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     const size_t iso_pts = (size_t)m.n_ages * m.n_mass;
     const size_t in_bytes = sizeof(TabSetIn) * n_sets, w_bytes = sizeof(double) * (size_t)nw * n_sets;
     const size_t m1_bytes = sizeof(double) * iso_pts * (1 + B) * n_m1;
-    CK(ctx->h_tab_in.ensure(in_bytes + w_bytes + m1_bytes));
+    const size_t desc_off = (in_bytes + w_bytes + m1_bytes + 255) & ~size_t(255);
+    const size_t up_bytes = desc_off + sizeof(SetDesc) * n_sets;   // one upload: inputs + descriptors
+    CK(ctx->h_tab_in.ensure(up_bytes));
     TabSetIn *tin = ctx->h_tab_in.as<TabSetIn>();
     double *wts = reinterpret_cast<double *>(ctx->h_tab_in.as<uint8_t>() + in_bytes);
     double *m1_imf = wts + (size_t)nw * n_sets, *m1_flux = m1_imf + iso_pts * n_m1;
@@ -347,21 +350,19 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         });
     }
     const uint32_t G = (P + kGroup - 1u) / kGroup;
-    CK(ctx->h_desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
     CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
-    CK(ctx->tab_in.ensure(in_bytes + w_bytes + m1_bytes));
+    CK(ctx->tab_in.ensure(up_bytes));
+    ctx->desc_d = reinterpret_cast<SetDesc *>(ctx->tab_in.as<uint8_t>() + desc_off);
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
     CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets * n_scr));
-    CK(ctx->desc.ensure(sizeof(SetDesc) * n_sets));
     CK(ctx->items.ensure(sizeof(uint2) * n_items));
     CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
-    std::memcpy(ctx->h_desc.p, ctx->descs.data(), sizeof(SetDesc) * n_sets);
+    std::memcpy(ctx->h_tab_in.as<uint8_t>() + desc_off, ctx->descs.data(), sizeof(SetDesc) * n_sets);
     std::memcpy(ctx->h_items.p, ctx->item_list.data(), sizeof(uint2) * n_items);
     std::memcpy(ctx->h_order.p, ctx->order_list.data(), sizeof(uint32_t) * n_items);
-    CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, in_bytes + w_bytes + m1_bytes, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->desc.p, ctx->h_desc.p, sizeof(SetDesc) * n_sets, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tab_in.p, ctx->h_tab_in.p, up_bytes, cudaMemcpyHostToDevice, ctx->st));
     CK(upload_if_changed(ctx->up_items, ctx->items, ctx->h_items.p, sizeof(uint2) * n_items, ctx->st));
     CK(upload_if_changed(ctx->up_order, ctx->order, ctx->h_order.p, sizeof(uint32_t) * n_items, ctx->st));
     CK(cudaEventRecord(ctx->staged, ctx->st));
@@ -370,7 +371,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     TabArgs ta;
     std::memset(&ta, 0, sizeof ta);
     ta.tables = ctx->tables.as<uint8_t>();
-    ta.desc = ctx->desc.as<SetDesc>();
+    ta.desc = ctx->desc_d;
     ta.sets = ctx->tab_in.as<TabSetIn>();
     ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
     ta.imf = ctx->imf_d.as<double>();
@@ -405,7 +406,7 @@ static DrawArgs base_draw_args(pcmd_ctx *ctx) {
     DrawArgs a;
     std::memset(&a, 0, sizeof a);
     a.tables = ctx->tables.as<uint8_t>();
-    a.desc = ctx->desc.as<SetDesc>();
+    a.desc = ctx->desc_d;
     a.items = ctx->items.as<uint2>();
     a.order = ctx->order.as<uint32_t>();
     a.n_items = (uint32_t)ctx->item_list.size();
@@ -552,12 +553,12 @@ void pcmd_destroy(pcmd_ctx *ctx) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
-    DevBuf *bufs[] = {&ctx->tables, &ctx->desc, &ctx->items, &ctx->order, &ctx->partials,
+    DevBuf *bufs[] = {&ctx->tables, &ctx->items, &ctx->order, &ctx->partials,
                       &ctx->part_begin, &ctx->part_count, &ctx->image, &ctx->pix_off, &ctx->hess,
                       &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
                       &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
     for (DevBuf *b : bufs) b->release();
-    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_desc, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
+    HostBuf *hb[] = {&ctx->h_tab_in, &ctx->h_items, &ctx->h_order, &ctx->h_meta, &ctx->h_ll};
     for (HostBuf *b : hb) b->release();
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
@@ -680,7 +681,7 @@ pcmd_status pcmd_hess(pcmd_ctx *ctx, uint32_t *d_hess, double *d_moments, uint32
     HessArgs h;
     std::memset(&h, 0, sizeof h);
     h.image = ctx->img_ptr;
-    h.desc = ctx->desc.as<SetDesc>();
+    h.desc = ctx->desc_d;
     h.n_sets = n_sets;
     h.n_bands = ctx->model.n_bands;
     h.psf = ctx->psf.empty() ? nullptr : ctx->psf_d.as<float>();
@@ -768,7 +769,7 @@ pcmd_status pcmd_loglike(pcmd_ctx *ctx, const uint32_t *d_mock_hess, const doubl
     CK(ctx->ll.ensure(sizeof(double) * n_sets));
     {
         KTimer t(ctx, PCMD_K_LOGLIKE, ctx->st);
-        CK(launch_loglike(ctx->hess_ptr, ctx->mom_ptr, ctx->desc.as<SetDesc>(), n_sets,
+        CK(launch_loglike(ctx->hess_ptr, ctx->mom_ptr, ctx->desc_d, n_sets,
                           ctx->cfg.hess_nx * ctx->cfg.hess_ny, d_mock_hess, h_mock_moments[0],
                           h_mock_moments[1], h_mock_moments[2], mock_n_pix, mode,
                           (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
@@ -814,11 +815,13 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     std::memcpy(&mk[1], &mom[1], 8);
     std::memcpy(&mk[2], &mom[2], 8);
     std::memcpy(&mk[3], &npix, 8);
-    const size_t key[12] = {(size_t)n_sets, n_items, (size_t)grid, (size_t)mode,
-                            (size_t)ctx->tables.p, (size_t)ctx->hess.p, (size_t)d_mock,
-                            (size_t)ctx->block * 1000003u + ctx->split * 1009u + ctx->chunk,
-                            mk[0], mk[1], mk[2], mk[3]};
-    if (ctx->gexec && std::memcmp(ctx->gkey, key, sizeof key) != 0) {
+    const std::vector<size_t> key = {
+        (size_t)n_sets, n_items, (size_t)grid, (size_t)mode, (size_t)ctx->block, (size_t)ctx->split,
+        (size_t)ctx->chunk, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
+        (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
+        (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
+        (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p};
+    if (ctx->gexec && ctx->gkey != key) {
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
     }
@@ -836,7 +839,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
                                 ctx->part_count.as<uint32_t>(), n_sets, ctx->moments.as<double>(),
                                 ctx->cap_st);
-        launch_loglike(ctx->hess.as<uint32_t>(), ctx->moments.as<double>(), ctx->desc.as<SetDesc>(),
+        launch_loglike(ctx->hess.as<uint32_t>(), ctx->moments.as<double>(), ctx->desc_d,
                        n_sets, nbins, d_mock, mom[0], mom[1], mom[2], npix, mode,
                        (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
                        ctx->cap_st);
@@ -844,7 +847,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         cudaError_t ec = cudaGraphInstantiate(&ctx->gexec, g, 0);
         cudaGraphDestroy(g);
         CK(ec);
-        std::memcpy(ctx->gkey, key, sizeof key);
+        ctx->gkey = key;
     }
     {
         KTimer t(ctx, PCMD_K_GRAPH, ctx->st);
