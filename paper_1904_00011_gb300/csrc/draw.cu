@@ -174,19 +174,39 @@ __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint
     return k;
 }
 
-// Resolve the queued maybe-hits of this thread: entry = g << 12 | slot << 8 | byte, g the
-// group's index in the staged chunk.  n = 1 when the byte is above Z_0 >> 24 and below
-// Z_1 >> 24; otherwise the LO call of the slot's quad completes the 32-bit word (kept for the
-// following entries of the same quad) and the full thresholds decide.
-template <int B, bool KAHAN, int MODE, int H>
-__device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic,
-                                            const uint8_t *cb, const uint32_t *queue, int qn,
-                                            Acc<B, KAHAN> &acc) {
+// Resolve the queued maybe-hits of the warp's 32 pixels together: entry = g << 12 | slot << 8 |
+// byte, g the group's index in the staged chunk.  The lanes' queues are enumerated as one list
+// (lane order, then queue order) and every lane resolves every 32nd entry: n = 1 when the byte
+// is above Z_0 >> 24 and below Z_1 >> 24, otherwise the LO call of the slot's quad (for the
+// entry owner's pixel) completes the 32-bit word and the full thresholds decide.  The count
+// replaces the byte in place.  Called by all 32 lanes of the warp.
+template <int B, int MODE, int H>
+__device__ __forceinline__ void resolve_warp(const DrawArgs &a, uint32_t pix, uint32_t set,
+                                          const SlowRec *slow, const uint32_t *tail,
+                                          const uint8_t *cb, uint32_t *queue, int qn) {
     constexpr uint32_t rec = group_rec_bytes(B);
-    uint32_t lo_q = 0xFFFFFFFFu;
-    uint4 wlo = make_uint4(0, 0, 0, 0);
-    for (int q = 0; q < qn; ++q) {
-        const uint32_t e = queue[q * blockDim.x + threadIdx.x];
+    const uint32_t lane = threadIdx.x & 31u, wbase = threadIdx.x & ~31u;
+    uint32_t inc = (uint32_t)qn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t off = inc - (uint32_t)qn;            // first list index of this lane's entries
+    for (uint32_t v0 = 0; v0 < total; v0 += 32u) {
+        const uint32_t v = v0 + lane;
+        uint32_t o = 0;                                  // owner: last lane with off <= v
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t t = __shfl_sync(0xffffffffu, off, o + (uint32_t)st);
+            if (t <= v) o += (uint32_t)st;
+        }
+        const uint32_t opix = __shfl_sync(0xffffffffu, pix, o);
+        const uint32_t oq = v - __shfl_sync(0xffffffffu, off, o);
+        if (v >= total) continue;
+        uint32_t *slot = queue + oq * blockDim.x + wbase + o;
+        const uint32_t e = *slot;
         const uint32_t g = e >> 12, j = (e >> 8) & 15u, hi = e & 0xFFu;
         const uint8_t *r = cb + g * rec;
         const uint32_t zc0 = r[kRecZ7 + j] | r[kRecZh + j];
@@ -197,22 +217,37 @@ __device__ __forceinline__ void drain_queue(const DrawArgs &a, const ItemCtx &ic
         if (hi > zc0 && hi < zc1) {
             n = 1u;
         } else {
-            if ((i >> 2) != lo_q) {
-                lo_q = i >> 2;
-                wlo = philox_rk(ic.pix, lo_q, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
-            }
+            const uint4 wlo = philox_rk(opix, i >> 2, set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
             const uint32_t x = (hi << 24) | (word_of(wlo, j & 3u) >> 8);
-            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + i);
-            n = count_from_thresholds(x, sr, ic.tail);
+            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(slow) + i);
+            n = count_from_thresholds(x, sr, tail);
         }
-        if (n) {
-            acc.template add<H>((float)n, reinterpret_cast<const float *>(r + kRecFlux) + j * B);
-            if (MODE == kModeCounts) {
-                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
-            }
+        *slot = (e & ~0xFFu) | n;                        // n <= kInvCap < 256
+        if (MODE == kModeCounts && n) {
+            if (opix >= a.count_pix0 && opix - a.count_pix0 < a.count_npix)
+                a.counts[((size_t)(opix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
         }
     }
+    __syncwarp();
+}
+
+// The warp's queued maybe-hits: resolved together, then every lane adds the fluxes of its own
+// entries in queue order (each pixel's sums accumulate in the order its lane queued them).
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void drain_warp(const DrawArgs &a, const ItemCtx &ic,
+                                           const uint8_t *cb, uint32_t *queue, int qn,
+                                           Acc<B, KAHAN> &acc) {
+    constexpr uint32_t rec = group_rec_bytes(B);
+    resolve_warp<B, MODE, H>(a, ic.pix, ic.set, ic.slow[H], ic.tail, cb, queue, qn);
+    for (int q = 0; q < qn; ++q) {
+        const uint32_t e = queue[q * blockDim.x + threadIdx.x];
+        const uint32_t n = e & 0xFFu;
+        if (n) {
+            const uint32_t g = e >> 12, j = (e >> 8) & 15u;
+            acc.template add<H>((float)n, reinterpret_cast<const float *>(cb + g * rec + kRecFlux) + j * B);
+        }
+    }
+    __syncwarp();
 }
 
 // One staged chunk of groups: the HI call of every (pixel, group) from the pixel's Philox
@@ -237,11 +272,11 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
         // maybe-hits of the 16 points in one word: bit 8q + k is byte q of word k (point 4k + q)
         uint32_t hm = ((m0 & 0x80808080u) >> 7) | ((m1 & 0x80808080u) >> 6) |
                       ((m2 & 0x80808080u) >> 5) | ((m3 & 0x80808080u) >> 4);
+        if (__any_sync(0xffffffffu, qn + __popc(hm) > kQueueCap)) {
+            drain_warp<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+            qn = 0;
+        }
         if (hm) {
-            if (qn + __popc(hm) > kQueueCap) {
-                drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
-                qn = 0;
-            }
             do {
                 const uint32_t bit = (uint32_t)(__ffs(hm) - 1);
                 hm &= hm - 1u;
@@ -252,7 +287,7 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
             } while (hm);
         }
     }
-    if (qn) drain_queue<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+    if (__any_sync(0xffffffffu, qn > 0)) drain_warp<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
 }
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
