@@ -84,6 +84,7 @@ struct pcmd_ctx {
     DevBuf tables, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
+    DevBuf ll_part, ll_ticket;                          // likelihood partials and per-set tickets
     HostBuf h_tab_in, h_items, h_order, h_meta, h_ll;
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
@@ -553,7 +554,7 @@ void pcmd_destroy(pcmd_ctx *ctx) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
-    DevBuf *bufs[] = {&ctx->tables, &ctx->items, &ctx->order, &ctx->partials,
+    DevBuf *bufs[] = {&ctx->ll_part, &ctx->ll_ticket, &ctx->tables, &ctx->items, &ctx->order, &ctx->partials,
                       &ctx->part_begin, &ctx->part_count, &ctx->image, &ctx->pix_off, &ctx->hess,
                       &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
                       &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
@@ -729,6 +730,18 @@ pcmd_status pcmd_sync(pcmd_ctx *ctx) {
     return PCMD_OK;
 }
 
+// Partials and tickets of the likelihood launch; tickets are zeroed when (re)allocated and
+// left at zero by every launch.
+static pcmd_status ensure_ll_scratch(pcmd_ctx *ctx, int n_sets) {
+    const int nbins = ctx->cfg.hess_nx * ctx->cfg.hess_ny;
+    const int ctas = loglike_ctas_per_set(n_sets, nbins);
+    CK(ctx->ll_part.ensure(sizeof(double) * (size_t)ctas * n_sets));
+    const uint64_t gen = ctx->ll_ticket.gen;
+    CK(ctx->ll_ticket.ensure(sizeof(uint32_t) * (size_t)n_sets));
+    if (ctx->ll_ticket.gen != gen) CK(cudaMemsetAsync(ctx->ll_ticket.p, 0, ctx->ll_ticket.cap, ctx->st));
+    return PCMD_OK;
+}
+
 // Likelihoods and the kernels' error word back to pinned host memory in one stream round trip.
 static pcmd_status fetch_ll(pcmd_ctx *ctx, int n_sets, double *h_ll) {
     double *hl = ctx->h_ll.as<double>();
@@ -767,13 +780,15 @@ pcmd_status pcmd_loglike(pcmd_ctx *ctx, const uint32_t *d_mock_hess, const doubl
     }
     const int n_sets = ctx->n_sets;
     CK(ctx->ll.ensure(sizeof(double) * n_sets));
+    rc = ensure_ll_scratch(ctx, n_sets);
+    if (rc != PCMD_OK) return rc;
     {
         KTimer t(ctx, PCMD_K_LOGLIKE, ctx->st);
         CK(launch_loglike(ctx->hess_ptr, ctx->mom_ptr, ctx->desc_d, n_sets,
                           ctx->cfg.hess_nx * ctx->cfg.hess_ny, d_mock_hess, h_mock_moments[0],
                           h_mock_moments[1], h_mock_moments[2], mock_n_pix, mode,
-                          (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
-                          ctx->st));
+                          (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll_part.as<double>(),
+                          ctx->ll_ticket.as<uint32_t>(), ctx->ll.as<double>(), ctx->st));
         t.done(ctx->st);
     }
     return fetch_ll(ctx, n_sets, h_ll);
@@ -793,6 +808,8 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     CK(ctx->part_begin.ensure(sizeof(uint32_t) * n_sets));
     CK(ctx->part_count.ensure(sizeof(uint32_t) * n_sets));
     CK(ctx->ll.ensure(sizeof(double) * n_sets));
+    const pcmd_status lrc = ensure_ll_scratch(ctx, n_sets);
+    if (lrc != PCMD_OK) return lrc;
     CK(ctx->h_meta.ensure(sizeof(uint32_t) * 2 * n_sets + 16));
     uint32_t *hb = ctx->h_meta.as<uint32_t>();
     for (int s = 0; s < n_sets; ++s) {
@@ -820,7 +837,8 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         (size_t)ctx->chunk, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
         (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
         (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
-        (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p};
+        (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p,
+        (size_t)ctx->ll_part.p, (size_t)ctx->ll_ticket.p};
     if (ctx->gexec && ctx->gkey != key) {
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
@@ -841,8 +859,8 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
                                 ctx->cap_st);
         launch_loglike(ctx->hess.as<uint32_t>(), ctx->moments.as<double>(), ctx->desc_d,
                        n_sets, nbins, d_mock, mom[0], mom[1], mom[2], npix, mode,
-                       (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll.as<double>(),
-                       ctx->cap_st);
+                       (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll_part.as<double>(),
+                       ctx->ll_ticket.as<uint32_t>(), ctx->ll.as<double>(), ctx->cap_st);
         CK(cudaStreamEndCapture(ctx->cap_st, &g));
         cudaError_t ec = cudaGraphInstantiate(&ctx->gexec, g, 0);
         cudaGraphDestroy(g);

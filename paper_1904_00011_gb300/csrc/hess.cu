@@ -264,27 +264,37 @@ cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *v
 }
 
 // One thread per set sums its partials in index order: deterministic moments.
+// One warp per set: lane l adds partials l, l + 32, ... in order, then a fixed xor tree.
 __global__ void moments_finalize_kernel(const double *partials, const uint32_t *begin,
                                         const uint32_t *count, int n_sets, double *moments) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     if (s >= n_sets) return;
+    const uint32_t lane = threadIdx.x & 31u;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     const double *p = partials + (size_t)begin[s] * 3;
-    for (uint32_t i = 0; i < count[s]; ++i) {
+    for (uint32_t i = lane; i < count[s]; i += 32u) {
         a0 += p[i * 3 + 0];
         a1 += p[i * 3 + 1];
         a2 += p[i * 3 + 2];
     }
-    moments[s * 3 + 0] = a0;
-    moments[s * 3 + 1] = a1;
-    moments[s * 3 + 2] = a2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+        moments[s * 3 + 0] = a0;
+        moments[s * 3 + 1] = a1;
+        moments[s * 3 + 2] = a2;
+    }
 }
 
 cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part_begin,
                                     const uint32_t *part_count, int n_sets, double *moments,
                                     cudaStream_t st) {
-    moments_finalize_kernel<<<(n_sets + 127) / 128, 128, 0, st>>>(partials, part_begin, part_count,
-                                                                 n_sets, moments);
+    moments_finalize_kernel<<<(n_sets + 3) / 4, 128, 0, st>>>(partials, part_begin, part_count,
+                                                             n_sets, moments);
     return cudaGetLastError();
 }
 

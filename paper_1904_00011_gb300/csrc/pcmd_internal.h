@@ -153,10 +153,13 @@ cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *v
 cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part_begin,
                                     const uint32_t *part_count, int n_sets, double *moments,
                                     cudaStream_t st);
+// CTAs per set of the likelihood (several when few sets leave SMs idle); `part` holds
+// [n_sets][ctas] partial sums, `ticket` [n_sets] counters that are zero between launches.
+int loglike_ctas_per_set(int n_sets, int nbins);
 cudaError_t launch_loglike(const uint32_t *hess, const double *moments, const SetDesc *desc,
                            int n_sets, int nbins, const uint32_t *mock, double mock_sc,
                            double mock_sm, double mock_nv, double mock_npix, int mode,
-                           int sqrtsum, double *ll, cudaStream_t st);
+                           int sqrtsum, double *part, uint32_t *ticket, double *ll, cudaStream_t st);
 cudaError_t upload_stirlerr(const float *tab16);
 
 }  // namespace pcmd
