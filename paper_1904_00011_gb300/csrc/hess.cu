@@ -35,6 +35,31 @@ __device__ __forceinline__ float conv_pixel(const float *tile_b, int hx, int ty,
     return acc;
 }
 
+// Four vertically adjacent outputs (rows ty0 .. ty0 + 3, column tx) of a KS x KS kernel with
+// compile-time weights: every input value read from shared memory feeds up to four outputs.
+// The input rows are walked from the bottom up, so each output accumulates its terms in the
+// same order as conv_pixel (kernel row u ascending, then column v ascending).
+template <int KS>
+__device__ __forceinline__ void conv_col4(const float *tile_b, int hx, int ty0, int tx,
+                                          const float *w, float out[4]) {
+    constexpr int R = KS / 2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = 0.0f;
+#pragma unroll
+    for (int r = KS + 2; r >= 0; --r) {
+        const float *row = tile_b + (ty0 + r) * hx + tx + 2 * R;
+#pragma unroll
+        for (int v = 0; v < KS; ++v) {
+            const float x = row[-v];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int u = k + 2 * R - r;
+                if (u >= 0 && u < KS) out[k] = fmaf(w[u * KS + v], x, out[k]);
+            }
+        }
+    }
+}
+
 // KS: 0 = no PSF, 25 = 25x25 weights from the kernel parameter, -1 = any odd size from smem.
 // GRID: the sub-pixel PSF grid (Section 2.2): output pixel (y, x) takes the kernel of region
 // (4y/N, 4x/N), read from global memory (the region is uniform over most warps, so the loads
@@ -71,19 +96,62 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int y0 = (t / tiles_x) * kTile, x0 = (t % tiles_x) * kTile;
         if (KS != 0) {
-            for (int i = tid; i < hx * hy; i += kHessThreads) {
-                const int ty = i / hx, tx = i - ty * hx;
-                int gy = (y0 - R + ty) % N;
-                gy += gy < 0 ? N : 0;
-                int gx = (x0 - R + tx) % N;
-                gx += gx < 0 ? N : 0;
-                const size_t src = (size_t)gy * N + gx;
+            // one warp per halo row, lanes along it; periodic wrap by whole images
+            for (int ty = tid >> 5; ty < hy; ty += kHessThreads / 32) {
+                int gy = y0 - R + ty;
+                while (gy < 0) gy += N;
+                while (gy >= N) gy -= N;
+                for (int tx = tid & 31; tx < hx; tx += 32) {
+                    int gx = x0 - R + tx;
+                    while (gx < 0) gx += N;
+                    while (gx >= N) gx -= N;
+                    const size_t src = (size_t)gy * N + gx;
 #pragma unroll
-                for (int b = 0; b < B; ++b) tile[b * hx * hy + i] = __ldg(img + (size_t)b * npix + src);
+                    for (int b = 0; b < B; ++b) tile[b * hx * hy + ty * hx + tx] = __ldg(img + (size_t)b * npix + src);
+                }
             }
             __syncthreads();
         }
         const int tx = tid & 31;
+        // noise, magnitudes, moments, optional pixel output and histogram of one output pixel
+        // (called by every lane of the warp: the histogram add is warp-aggregated)
+        auto finish = [&](int y, int x, float (&F)[B]) {
+            int bin = -1;
+            if (y < N && x < N) {
+                const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
+                const PixelOut o = pixel_stage<B>(F, p, d.set_id, a.pc);
+                if (o.valid) {
+                    cs += (double)__fsub_rn(o.col, a.pc.c_lo);
+                    ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
+                    nv += 1.0;
+                    bin = o.bin;
+                    if (bin < 0) ++novf;
+                } else {
+                    ++ninv;
+                }
+                if (pout) {
+#pragma unroll
+                    for (int b = 0; b < B; ++b) pout[(size_t)b * npix + p] = F[b];
+                    pout[(size_t)B * npix + p] = o.valid ? o.mag : __int_as_float(0x7fc00000);
+                    pout[(size_t)(B + 1) * npix + p] = o.valid ? o.col : __int_as_float(0x7fc00000);
+                }
+            }
+            hist_add_warp(hist, nullptr, nullptr, bin, 0u);
+        };
+        if (KS > 0 && !GRID) {
+            // each warp: four adjacent rows of the tile (8 warps x 4 rows = 32)
+            const int ty0 = (tid >> 5) * 4;
+            float Fk[4][B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                float o[4];
+                conv_col4<(KS > 0 ? KS : 1)>(tile + b * hx * hy, hx, ty0, tx, pw.w[b], o);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Fk[k][b] = o[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) finish(y0 + ty0 + k, x0 + tx, Fk[k]);
+        } else
         for (int ty = tid >> 5; ty < kTile; ty += kHessThreads / 32) {
             const int y = y0 + ty, x = x0 + tx;
             const bool in = y < N && x < N;
@@ -263,7 +331,6 @@ cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *v
     return cudaGetLastError();
 }
 
-// One thread per set sums its partials in index order: deterministic moments.
 // One warp per set: lane l adds partials l, l + 32, ... in order, then a fixed xor tree.
 __global__ void moments_finalize_kernel(const double *partials, const uint32_t *begin,
                                         const uint32_t *count, int n_sets, double *moments) {
