@@ -14,7 +14,7 @@
 #include "tables_dev.h"
 
 namespace pcmd {
-int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int block, size_t smem);
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool ptrs, int block, size_t smem);
 }
 
 using namespace pcmd;
@@ -95,6 +95,7 @@ struct pcmd_ctx {
     std::vector<uint32_t> order_list;
 
     int n_sets = 0;
+    bool may_ptrs = true;       // a staged model may have points at lambda >= 10
     std::vector<int> n_im;
     float *img_ptr = nullptr;
     bool have_images = false, have_hess = false;
@@ -297,6 +298,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::vector<double> mdf;
     uint64_t img_off = 0;
     uint32_t m1_i = 0;
+    bool may_ptrs = false;
     for (int s = 0; s < n_sets; ++s) {
         tin[s].m1_k = m1_k[s];
         tin[s].m1_off = 0;
@@ -310,6 +312,20 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         for (int j = 0; j < m.n_ages; ++j) {
             const double sfh = std::pow(10.0, p[s].log_sfh[j]);
             for (int k = 0; k < m.n_feh; ++k) w[j * m.n_feh + k] = sfh * mdf[k];
+        }
+        {   // an upper bound of the largest lambda: is the transformed-rejection path needed?
+            double bound = 0.0;
+            for (int j = 0; j < m.n_ages; ++j)
+                for (int k = 0; k < m.n_feh; ++k) {
+                    double im = m.imf_max[(size_t)j * m.n_feh + k];
+                    if (k == m1_k[s]) {
+                        im = 0.0;
+                        const double *mi = m1_imf + (size_t)tin[s].m1_off + (size_t)j * m.n_mass;
+                        for (int i = 0; i < m.n_mass; ++i) im = std::max(im, mi[i]);
+                    }
+                    bound = std::max(bound, w[j * m.n_feh + k] * im);
+                }
+            if (bound * std::max(hf[0], hf[1]) >= 0.999 * (double)kPtrsThreshold) may_ptrs = true;
         }
         tin[s].base = (uint64_t)s * L.bytes;
         tin[s].flux_factor = std::pow(10.0, -0.4 * p[s].dmod);
@@ -399,6 +415,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         t.done(ctx->st);
     }
     ctx->n_sets = n_sets;
+    ctx->may_ptrs = may_ptrs;
     ctx->n_im.assign(n_im, n_im + n_sets);
     return PCMD_OK;
 }
@@ -430,13 +447,13 @@ static pcmd_status launch_draw_mode(pcmd_ctx *ctx, DrawArgs &a, int mode) {
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, mode, ctx->cfg.hess_nx,
                                         ctx->cfg.hess_ny);
-    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->block, smem);
+    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->may_ptrs, ctx->block, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = std::min<int>((int)a.n_items, per_sm * ctx->n_sm);
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->st));
     KTimer t(ctx, PCMD_K_DRAW, ctx->st);
-    CK(launch_draw(a, B, kahan, mode, grid, ctx->block, smem, ctx->st));
+    CK(launch_draw(a, B, kahan, mode, ctx->may_ptrs, grid, ctx->block, smem, ctx->st));
     t.done(ctx->st);
     return PCMD_OK;
 }
@@ -825,7 +842,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, kModeFused,
                                         ctx->cfg.hess_nx, ctx->cfg.hess_ny);
-    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->block, smem));
+    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->may_ptrs, ctx->block, smem));
     const int grid = std::max(1, std::min<int>((int)n_items, per_sm * ctx->n_sm));
     uint64_t mk[4];
     std::memcpy(&mk[0], &mom[0], 8);
@@ -834,7 +851,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     std::memcpy(&mk[3], &npix, 8);
     const std::vector<size_t> key = {
         (size_t)n_sets, n_items, (size_t)grid, (size_t)mode, (size_t)ctx->block, (size_t)ctx->split,
-        (size_t)ctx->chunk, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
+        (size_t)ctx->chunk, (size_t)ctx->may_ptrs, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
         (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
         (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
         (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p,
@@ -853,7 +870,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         cudaMemsetAsync(ctx->hess.p, 0, sizeof(uint32_t) * nbins * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->counters.p, 0, sizeof(uint32_t) * 2 * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->cap_st);
-        launch_draw(a, B, kahan, kModeFused, grid, ctx->block, smem, ctx->cap_st);
+        launch_draw(a, B, kahan, kModeFused, ctx->may_ptrs, grid, ctx->block, smem, ctx->cap_st);
         launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
                                 ctx->part_count.as<uint32_t>(), n_sets, ctx->moments.as<double>(),
                                 ctx->cap_st);

@@ -155,6 +155,16 @@ struct ItemCtx {
 
 constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
 
+// The chunk double buffer, large enough to hold the transformed-rejection test queues
+// (64 tasks of 16 bytes per warp) that use it between items.
+__host__ __device__ constexpr uint32_t chunk_region_bytes(uint32_t chunk, uint32_t rec, uint32_t block) {
+    return 2u * chunk * rec > block * 32u ? 2u * chunk * rec : block * 32u;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // n = #{k : x > Z_k} from the slow record of a slot: Z_0, Z_1 in the record, Z_2.. in the tail
 // (saturated beyond its length).  The search starts at the record's start index k_s (near
 // lambda) and walks up or down; the count equals the linear scan's.
@@ -409,15 +419,144 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
 }
 
 // Transformed-rejection points: every thread runs the attempt loop of each of its records.
+// Transformed-rejection points of half H, one lane per pixel, each draw's attempts in turn
+// (for launches whose models have few or none of these points).
 template <int B, bool KAHAN, int MODE, int H>
-__device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic,
-                                             const SetDesc &d, int sidx, Acc<B, KAHAN> &acc) {
+__device__ __forceinline__ void process_ptrs_lane(const DrawArgs &a, const ItemCtx &ic,
+                                                  const SetDesc &d, int sidx, Acc<B, KAHAN> &acc) {
     const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
     const uint32_t n_rec = ic.active ? d.n_ptrs[H] : 0u;
     for (uint32_t q = (uint32_t)sidx; q < n_rec; q += (uint32_t)a.split) {
         const PtrsRec rec = load_ptrs(pr, q);
         const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
         ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, n, acc);
+    }
+}
+
+// Transformed-rejection points (lambda >= 10) of half H: every lane (pixel) runs the records
+// q = sidx, sidx + split, ... one attempt per iteration of a warp-wide loop, so lanes do not
+// wait for each other's rejections.  An attempt whose squeeze is inconclusive parks its draw:
+// its log-form test goes to the warp's queue and the lane moves on; the warp evaluates the
+// queued tests 32 at a time, then each lane settles its parked draws in the order it parked
+// them (accepted: fluxes added; rejected: resumed at the next attempt before any new record).
+// Every draw makes exactly the decisions of the per-draw attempt loop.  The parked draws use
+// the lane's hit-queue space, the test queue the (idle) chunk buffers.  Called by all 32 lanes.
+constexpr int kPark = kQueueCap / 2;        // parked draws per lane: (record, attempt | slot)
+constexpr uint32_t kLogQ = 64;              // log tests per warp
+constexpr uint32_t kNoSlot = 0xFFFFu;
+
+struct LogTask {
+    float kf, us, V;
+    uint32_t meta;   // record | owner lane << 24 | accepted << 31
+};
+
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
+                                             int sidx, uint32_t *park, LogTask *wq, Acc<B, KAHAN> &acc) {
+    const uint32_t n_rec = d.n_ptrs[H];
+    if (n_rec == 0u) return;
+    const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
+    const uint32_t lane = threadIdx.x & 31u, stride = blockDim.x;
+    uint32_t *pq = park + threadIdx.x;                   // entry e: pq[2e * stride], pq[(2e + 1) * stride]
+    uint32_t qi = ic.active ? (uint32_t)sidx : n_rec;    // next new record of this lane
+    uint32_t cur_q = 0u, cur_at = 0u;
+    bool has_cur = false;
+    int rh = 0, nr = 0, np = 0;                          // resumable [rh, nr), parked [nr, np)
+    uint32_t wn = 0u;                                    // tests queued (warp-uniform)
+
+    auto settle = [&]() {
+        for (uint32_t v = lane; v < wn; v += 32u) {
+            const LogTask t = wq[v];
+            const PtrsRec rec = load_ptrs(pr, t.meta & 0xFFFFFFu);
+            PtrsTry tt;
+            tt.kf = t.kf;
+            tt.us = t.us;
+            tt.V = t.V;
+            tt.status = 2;
+            if (ptrs_log_accept(rec, tt)) wq[v].meta = t.meta | 0x80000000u;
+        }
+        __syncwarp();
+        int keep = 0;
+        for (int e = rh; e < np; ++e) {
+            const uint32_t q = pq[2 * e * stride], m = pq[(2 * e + 1) * stride];
+            uint32_t at = m & 0xFFFFu;
+            const uint32_t slot = m >> 16;
+            if (slot != kNoSlot) {
+                const LogTask t = wq[slot];
+                if (t.meta >> 31) {
+                    ptrs_resolved<B, KAHAN, MODE, H>(a, ic, load_ptrs(pr, q), (uint32_t)t.kf, acc);
+                    continue;
+                }
+                if (++at >= kPtrsMaxAttempts) {
+                    atomicOr(a.err, kErrSampler);
+                    continue;
+                }
+            }
+            pq[2 * keep * stride] = q;
+            pq[(2 * keep + 1) * stride] = at | (kNoSlot << 16);
+            ++keep;
+        }
+        rh = 0;
+        nr = np = keep;
+        wn = 0u;
+        __syncwarp();
+    };
+
+    for (;;) {
+        if (!has_cur) {
+            if (rh < nr) {
+                cur_q = pq[2 * rh * stride];
+                cur_at = pq[(2 * rh + 1) * stride] & 0xFFFFu;
+                ++rh;
+                has_cur = true;
+            } else if (qi < n_rec) {
+                cur_q = qi;
+                cur_at = 0u;
+                qi += (uint32_t)a.split;
+                has_cur = true;
+            }
+        }
+        if (!__any_sync(0xffffffffu, has_cur)) {
+            if (wn == 0u) break;
+            settle();
+            continue;
+        }
+        bool push = false;
+        PtrsTry t;
+        t.kf = t.us = t.V = 0.0f;
+        if (has_cur) {
+            const PtrsRec rec = load_ptrs(pr, cur_q);
+            const uint4 w = ptrs_words(rec, ic.pix, ic.set, H, cur_at, a.rk0, a.rk1);
+            t = ptrs_cheap(rec, (cur_at & 1u) ? w.z : w.x, (cur_at & 1u) ? w.w : w.y);
+            if (t.status == 0) {
+                ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, (uint32_t)t.kf, acc);
+                has_cur = false;
+            } else if (t.status == 2 && np < kPark) {
+                push = true;
+            } else if (t.status == 2 && ptrs_log_accept(rec, t)) {   // no parking space: test here
+                ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, (uint32_t)t.kf, acc);
+                has_cur = false;
+            } else if (++cur_at >= kPtrsMaxAttempts) {
+                atomicOr(a.err, kErrSampler);
+                has_cur = false;
+            }
+        }
+        const uint32_t pushers = __ballot_sync(0xffffffffu, push);
+        if (push) {
+            const uint32_t slot = wn + __popc(pushers & ((1u << lane) - 1u));
+            LogTask lt;
+            lt.kf = t.kf;
+            lt.us = t.us;
+            lt.V = t.V;
+            lt.meta = cur_q | (lane << 24);
+            wq[slot] = lt;
+            pq[2 * np * stride] = cur_q;
+            pq[(2 * np + 1) * stride] = cur_at | (slot << 16);
+            ++np;
+            has_cur = false;
+        }
+        wn += (uint32_t)__popc(pushers);
+        if (wn > kLogQ - 32u || __any_sync(0xffffffffu, np >= kPark)) settle();
     }
 }
 
@@ -437,7 +576,10 @@ __device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uin
     for (int b = 0; b < B; ++b) fac[b] = exp10f(d.dust_c[b] * e);
 }
 
-template <int B, bool KAHAN, int MODE>
+// PTRS: the launch's models may have many transformed-rejection points (lambda >= 10): they
+// are drawn warp-cooperatively; otherwise each lane draws its few in turn.  Either gives the
+// same counts.
+template <int B, bool KAHAN, int MODE, bool PTRS>
 __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t rec = group_rec_bytes(B);
@@ -446,7 +588,7 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
     volatile uint32_t *s_item = reinterpret_cast<volatile uint32_t *>(smem + 16);
     uint32_t *s_ntouch = reinterpret_cast<uint32_t *>(smem + 20);
     uint8_t *bufs = smem + 32;
-    uint32_t *queue = reinterpret_cast<uint32_t *>(bufs + 2u * chunk * rec);
+    uint32_t *queue = reinterpret_cast<uint32_t *>(bufs + chunk_region_bytes(chunk, rec, blockDim.x));
     float *red = reinterpret_cast<float *>(queue + (size_t)kQueueCap * blockDim.x);
     const int tid = threadIdx.x;
     const int ppc = blockDim.x / a.split;
@@ -543,8 +685,18 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
             process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
         }
-        process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
-        process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        if (PTRS) {
+            LogTask *wq = reinterpret_cast<LogTask *>(bufs) + (size_t)(tid >> 5) * kLogQ;
+            process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, queue, wq, acc);
+            process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, queue, wq, acc);
+            // the test queue overlays the chunk buffers: order these generic accesses before
+            // the next item's bulk copies into them
+            fence_proxy_async_smem();
+            __syncthreads();
+        } else {
+            process_ptrs_lane<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+            process_ptrs_lane<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        }
 
         // ---- combine the splits of each pixel in a fixed order ----
         float v0[B], v1[B];
@@ -667,7 +819,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
 }
 
 size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx, int ny) {
-    size_t s = 32 + 2 * (size_t)chunk * group_rec_bytes(nb) + (size_t)kQueueCap * block * 4 +
+    size_t s = 32 + chunk_region_bytes((uint32_t)chunk, group_rec_bytes(nb), (uint32_t)block) +
+               (size_t)kQueueCap * block * 4 +
                (size_t)block * 2 * nb * 4;
     if (mode == kModeFused) {
         s += (size_t)nx * ny * 4 + (size_t)(block / split) * 4;
@@ -679,11 +832,11 @@ size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx
 
 // Opt in to the dynamic shared memory of each instantiation once per process (before any
 // stream capture: the first call of every configuration goes through draw_max_blocks_per_sm).
-template <int B, bool KAHAN, int MODE>
+template <int B, bool KAHAN, int MODE, bool PTRS>
 static cudaError_t configure_t(size_t smem) {
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(draw_kernel<B, KAHAN, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(draw_kernel<B, KAHAN, MODE, PTRS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
@@ -691,59 +844,72 @@ static cudaError_t configure_t(size_t smem) {
     return cudaSuccess;
 }
 
-template <int B, bool KAHAN, int MODE>
+template <int B, bool KAHAN, int MODE, bool PTRS>
 static cudaError_t launch_t(const DrawArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-    cudaError_t e = configure_t<B, KAHAN, MODE>(smem);
+    cudaError_t e = configure_t<B, KAHAN, MODE, PTRS>(smem);
     if (e != cudaSuccess) return e;
-    draw_kernel<B, KAHAN, MODE><<<grid, block, smem, st>>>(a);
+    draw_kernel<B, KAHAN, MODE, PTRS><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int B, bool KAHAN, int MODE>
+template <int B, bool KAHAN, int MODE, bool PTRS>
 static int occupancy_t(int block, size_t smem) {
-    if (configure_t<B, KAHAN, MODE>(smem) != cudaSuccess) return 0;
+    if (configure_t<B, KAHAN, MODE, PTRS>(smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, draw_kernel<B, KAHAN, MODE>, block, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, draw_kernel<B, KAHAN, MODE, PTRS>, block, smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
 
-template <int B, bool KAHAN>
+template <int B, bool KAHAN, bool PTRS>
 static int occupancy_m(int mode, int block, size_t smem) {
     switch (mode) {
-        case kModeImage: return occupancy_t<B, KAHAN, kModeImage>(block, smem);
-        case kModeCounts: return occupancy_t<B, KAHAN, kModeCounts>(block, smem);
-        default: return occupancy_t<B, KAHAN, kModeFused>(block, smem);
-    }
-}
-
-int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int block, size_t smem) {
-    switch (nb) {
-        case 2: return kahan ? occupancy_m<2, true>(mode, block, smem) : occupancy_m<2, false>(mode, block, smem);
-        case 3: return kahan ? occupancy_m<3, true>(mode, block, smem) : occupancy_m<3, false>(mode, block, smem);
-        default: return kahan ? occupancy_m<4, true>(mode, block, smem) : occupancy_m<4, false>(mode, block, smem);
+        case kModeImage: return occupancy_t<B, KAHAN, kModeImage, PTRS>(block, smem);
+        case kModeCounts: return occupancy_t<B, KAHAN, kModeCounts, PTRS>(block, smem);
+        default: return occupancy_t<B, KAHAN, kModeFused, PTRS>(block, smem);
     }
 }
 
 template <int B, bool KAHAN>
+static int occupancy_p(int mode, bool ptrs, int block, size_t smem) {
+    return ptrs ? occupancy_m<B, KAHAN, true>(mode, block, smem) : occupancy_m<B, KAHAN, false>(mode, block, smem);
+}
+
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool ptrs, int block, size_t smem) {
+    switch (nb) {
+        case 2: return kahan ? occupancy_p<2, true>(mode, ptrs, block, smem) : occupancy_p<2, false>(mode, ptrs, block, smem);
+        case 3: return kahan ? occupancy_p<3, true>(mode, ptrs, block, smem) : occupancy_p<3, false>(mode, ptrs, block, smem);
+        default: return kahan ? occupancy_p<4, true>(mode, ptrs, block, smem) : occupancy_p<4, false>(mode, ptrs, block, smem);
+    }
+}
+
+template <int B, bool KAHAN, bool PTRS>
 static cudaError_t launch_m(const DrawArgs &a, int mode, int grid, int block, size_t smem,
                             cudaStream_t st) {
     switch (mode) {
-        case kModeImage: return launch_t<B, KAHAN, kModeImage>(a, grid, block, smem, st);
-        case kModeCounts: return launch_t<B, KAHAN, kModeCounts>(a, grid, block, smem, st);
-        default: return launch_t<B, KAHAN, kModeFused>(a, grid, block, smem, st);
+        case kModeImage: return launch_t<B, KAHAN, kModeImage, PTRS>(a, grid, block, smem, st);
+        case kModeCounts: return launch_t<B, KAHAN, kModeCounts, PTRS>(a, grid, block, smem, st);
+        default: return launch_t<B, KAHAN, kModeFused, PTRS>(a, grid, block, smem, st);
     }
 }
 
-cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, int grid, int block,
+template <int B, bool KAHAN>
+static cudaError_t launch_p(const DrawArgs &a, int mode, bool ptrs, int grid, int block, size_t smem,
+                            cudaStream_t st) {
+    return ptrs ? launch_m<B, KAHAN, true>(a, mode, grid, block, smem, st)
+                : launch_m<B, KAHAN, false>(a, mode, grid, block, smem, st);
+}
+
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool ptrs, int grid, int block,
                         size_t smem, cudaStream_t st) {
     switch (n_bands) {
-        case 2: return kahan ? launch_m<2, true>(a, mode, grid, block, smem, st)
-                             : launch_m<2, false>(a, mode, grid, block, smem, st);
-        case 3: return kahan ? launch_m<3, true>(a, mode, grid, block, smem, st)
-                             : launch_m<3, false>(a, mode, grid, block, smem, st);
-        default: return kahan ? launch_m<4, true>(a, mode, grid, block, smem, st)
-                              : launch_m<4, false>(a, mode, grid, block, smem, st);
+        case 2: return kahan ? launch_p<2, true>(a, mode, ptrs, grid, block, smem, st)
+                             : launch_p<2, false>(a, mode, ptrs, grid, block, smem, st);
+        case 3: return kahan ? launch_p<3, true>(a, mode, ptrs, grid, block, smem, st)
+                             : launch_p<3, false>(a, mode, ptrs, grid, block, smem, st);
+        default: return kahan ? launch_p<4, true>(a, mode, ptrs, grid, block, smem, st)
+                              : launch_p<4, false>(a, mode, ptrs, grid, block, smem, st);
     }
 }
 

@@ -139,7 +139,9 @@ struct HessArgs {
 };
 
 // launchers (implemented in the .cu files)
-cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, int grid,
+// ptrs: the models may have transformed-rejection points (lambda >= 10): the warp-cooperative
+// rejection loop instead of the per-lane one (same counts either way)
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool ptrs, int grid,
                         int block, size_t smem, cudaStream_t st);
 size_t draw_smem_bytes(int n_bands, int chunk, int block, int split, int mode, int nx, int ny);
 enum { kModeImage = 0, kModeCounts = 1, kModeFused = 2 };

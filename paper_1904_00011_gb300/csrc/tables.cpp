@@ -11,6 +11,7 @@
 //            (outer edges mirrored), normalised over the isochrone (Salpeter)
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -68,10 +69,12 @@ static void imf_of_isochrone(const double *m, int n_mass, double slope, int kind
 
 void Model::build_imf() {
     imf.assign((size_t)n_ages * n_feh * n_mass, 0.0);
+    imf_max.assign((size_t)n_ages * n_feh, 0.0);
     for (int j = 0; j < n_ages; ++j)
         for (int k = 0; k < n_feh; ++k) {
             const size_t o = ((size_t)j * n_feh + k) * n_mass;
             imf_of_isochrone(&mass[o], n_mass, imf_slope, imf_kind, &imf[o]);
+            for (int i = 0; i < n_mass; ++i) imf_max[(size_t)j * n_feh + k] = std::max(imf_max[(size_t)j * n_feh + k], imf[o + i]);
         }
 }
 
