@@ -432,9 +432,12 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 102
     w = W.large(log_npix=log_npix, n_im=n_im)
     n = w.n_im
     sim = P.Simulator(w, max_sets=1)
-    # launch shape tuned on a 256x256 image of the same model (same per-pixel work)
+    # launch shape tuned on the image itself (work items per CTA change the best split),
+    # one timed run per shape over the shapes that suit long transformed-rejection lists
     from paper_1904_00011_gb300 import autotune
-    tuned = autotune.tune(sim, w.params, [min(n, 256)], reps=2, use_cache=False)
+    tuned = autotune.tune(sim, w.params, [n], reps=1, use_cache=False,
+                          candidates=[(256, 1, 32), (256, 2, 32), (256, 4, 32), (256, 1, 64),
+                                      (256, 2, 64), (256, 4, 64), (128, 1, 32), (128, 2, 32)])
     sim.simulate(w.params, [n], 2_000_000)
     h, m, c, _ = sim.hess(1, [n])
     torch.cuda.synchronize()
