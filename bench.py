@@ -36,6 +36,9 @@ WORKLOAD = ("plain full model: 256x256, 2 bands, 7 SFH x 7 [Fe/H] x 300 masses (
 METRIC = "model pixels/s (plain full model, one likelihood evaluation per step)"
 # Each step evaluates a new parameter point (a sampler-like random walk) with a new RNG set id.
 PEAK_ISSUE_PER_SM_CLK = 128          # 4 schedulers x 32 lanes: thread-instructions per clock
+# dram__bytes_read.sum + dram__bytes_write.sum of one draw launch on the headline workload
+# (ncu, launch shape 256/4/64): the point tables are read once, the image stays in L2
+DRAW_TRAFFIC_BYTES = 971776 + 0
 OPS_PER_INV_DRAW = 3.5               # 1/16 Philox4x32-10 block (40 instr) + one byte compare
 OPS_PER_PTRS_DRAW = 60.0             # 1/2 Philox block + ~40 FP32 ops of the squeeze test
 
@@ -352,7 +355,9 @@ def run_gb300(args, world, rank, local):
                    "autotune_sweep_ms": tuned.get("sweep")},
         "loglike_evals_per_s": evals,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "draw_kernel<2,false,IMAGE>",
+                     "frac": achieved / peak, "traffic": DRAW_TRAFFIC_BYTES,
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu capture of this kernel on this workload)",
+                     "kernel": "draw_kernel<2,false,IMAGE,false>",
                      "avg_launch_ms": avg_draw_s * 1e3,
                      "algorithmic": "%g instr/pixel = %d inversion draws x %g + %d PTRS draws x %g"
                                     % (ops, n_inv, OPS_PER_INV_DRAW, n_ptrs, OPS_PER_PTRS_DRAW),
