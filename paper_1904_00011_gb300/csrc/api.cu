@@ -663,10 +663,7 @@ pcmd_status pcmd_hess(pcmd_ctx *ctx, uint32_t *d_hess, double *d_moments, uint32
     double *mm = d_moments ? d_moments : ctx->moments.as<double>();
     uint32_t *cc = d_counters ? d_counters : ctx->counters.as<uint32_t>();
     int max_tiles = 1;
-    for (int s = 0; s < n_sets; ++s) {
-        const int tx = (ctx->n_im[s] + 31) / 32;
-        max_tiles = std::max(max_tiles, tx * tx);
-    }
+    for (int s = 0; s < n_sets; ++s) max_tiles = std::max(max_tiles, hess_tiles(ctx->n_im[s]));
     int cps = std::max(1, (2 * ctx->n_sm + n_sets - 1) / n_sets);
     cps = std::min(cps, max_tiles);
     // per-set partial ranges and pixel-output offsets (pinned host staging, then device)

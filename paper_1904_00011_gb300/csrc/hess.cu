@@ -1,13 +1,16 @@
 // psf_noise_mag_hess: periodic PSF convolution from a shared-memory tile with halo, sky and
 // photon noise, magnitudes and colour, and a Hess diagram privatised in shared memory
-// (Section 2.1 panels E-F, Section 2.5).  Persistent over 32x32 output tiles of one image per
-// blockIdx.y; each CTA flushes its histogram once and writes one moments partial.
+// (Section 2.1 panels E-F, Section 2.5).  Persistent over 32-wide x 16-tall output tiles of one
+// image per blockIdx.y (a 256x256 image gives 128 tiles); each CTA flushes its histogram once
+// and writes one moments partial.
 #include "common.cuh"
 
 namespace pcmd {
 
-constexpr int kTile = 32;
-constexpr int kHessThreads = 256;
+constexpr int kTileW = 32, kTileH = 16;     // output tile; a warp covers 32 columns x 4 rows
+constexpr int kHessThreads = 128;           // 4 warps x 4 rows = kTileH
+
+int hess_tiles(int n_im) { return ((n_im + kTileW - 1) / kTileW) * ((n_im + kTileH - 1) / kTileH); }
 
 struct PsfW {
     float w[kMaxBands][625];   // 25x25 weights per band (compile-time indexed: constant bank)
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
     const uint32_t npix = (uint32_t)N * (uint32_t)N;
     const int ks = KS > 0 ? KS : (KS == 0 ? 0 : a.psf_size);
     const int R = ks / 2;
-    const int hx = kTile + 2 * R, hy = kTile + 2 * R;
+    const int hx = kTileW + 2 * R, hy = kTileH + 2 * R;
     const int nbins = a.pc.nx * a.pc.ny;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     float *tile = reinterpret_cast<float *>(hist + nbins);
@@ -89,12 +92,12 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
 
     const float *img = a.image + d.img_off;
     float *pout = a.pixels ? a.pixels + a.pix_off[set] : nullptr;
-    const int tiles_x = (N + kTile - 1) / kTile;
-    const int n_tiles = tiles_x * tiles_x;
+    const int tiles_x = (N + kTileW - 1) / kTileW;
+    const int n_tiles = tiles_x * ((N + kTileH - 1) / kTileH);
     double cs = 0.0, ms = 0.0, nv = 0.0;
     uint32_t novf = 0u, ninv = 0u;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int y0 = (t / tiles_x) * kTile, x0 = (t % tiles_x) * kTile;
+        const int y0 = (t / tiles_x) * kTileH, x0 = (t % tiles_x) * kTileW;
         if (KS != 0) {
             // one warp per halo row, lanes along it; periodic wrap by whole images
             for (int ty = tid >> 5; ty < hy; ty += kHessThreads / 32) {
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
             hist_add_warp(hist, nullptr, nullptr, bin, 0u);
         };
         if (KS > 0 && !GRID) {
-            // each warp: four adjacent rows of the tile (8 warps x 4 rows = 32)
+            // each warp: four adjacent rows of the tile (4 warps x 4 rows = kTileH)
             const int ty0 = (tid >> 5) * 4;
             float Fk[4][B];
 #pragma unroll
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
 #pragma unroll
             for (int k = 0; k < 4; ++k) finish(y0 + ty0 + k, x0 + tx, Fk[k]);
         } else
-        for (int ty = tid >> 5; ty < kTile; ty += kHessThreads / 32) {
+        for (int ty = tid >> 5; ty < kTileH; ty += kHessThreads / 32) {
             const int y = y0 + ty, x = x0 + tx;
             const bool in = y < N && x < N;
             int bin = -1;
@@ -231,9 +234,8 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
 
 size_t hess_smem_bytes(int nb, int psf_size, int nx, int ny) {
     const int R = psf_size / 2;
-    const int h = kTile + 2 * R;
     size_t s = (size_t)nx * ny * 4;
-    if (psf_size > 0) s += (size_t)nb * h * h * 4;
+    if (psf_size > 0) s += (size_t)nb * (kTileW + 2 * R) * (kTileH + 2 * R) * 4;
     if (psf_size > 0 && psf_size != 25) s += (size_t)nb * psf_size * psf_size * 4;
     s = (s + 7) & ~size_t(7);
     s += (kHessThreads / 32) * 3 * 8;

@@ -88,8 +88,7 @@ extern "C" pcmd_status pcmd_hess_noalloc(const pcmd_pixel_config *cfg, const flo
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return PCMD_ERR_CUDA;
-    const int tiles_x = (n_im + 31) / 32;
-    int ctas = std::min(2 * n_sm, tiles_x * tiles_x);
+    int ctas = std::min(2 * n_sm, hess_tiles(n_im));
     if (ctas > kNoallocMaxCtas) ctas = kNoallocMaxCtas;
     if (ctas < 1) ctas = 1;
 

@@ -148,6 +148,7 @@ enum { kModeImage = 0, kModeCounts = 1, kModeFused = 2 };
 
 cudaError_t launch_hess(const HessArgs &a, const float *psf25_host, cudaStream_t st);
 size_t hess_smem_bytes(int n_bands, int psf_size, int nx, int ny);
+int hess_tiles(int n_im);   // output tiles of an n_im x n_im image in the Hess stage
 cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *valid, uint32_t n,
                             uint32_t *hess, uint32_t *counters, double *moments,
                             const PixelConsts &pc, uint32_t *err, cudaStream_t st);
