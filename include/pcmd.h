@@ -53,8 +53,9 @@ enum {
     PCMD_FLAG_NOISE = 2,          /* sky + photon noise (Section 2.1) */
     PCMD_FLAG_KAHAN = 4,          /* compensated FP32 flux sums (large Npix) */
     PCMD_FLAG_SIGMA_SQRTSUM = 8,  /* Eq. 3 read as max(sqrt(d + m), 2) instead of as printed */
-    PCMD_FLAG_POOL = 16           /* total-count sampler for the points with lambda < 10 (Section
-                                   * 2.1 footnote): per pixel and dust half N ~ Poisson(sum of
+    PCMD_FLAG_POOL = 16           /* total-count sampler for the points with lambda < 10 (the
+                                   * Poisson additivity of the Section 2.1 footnote, used in
+                                   * reverse): per pixel and dust half N ~ Poisson(sum of
                                    * their lambdas) stars, each assigned to a point with
                                    * probability lambda_i / sum by inverting the cumulative
                                    * weights; the counts have the same joint law (independent

@@ -430,9 +430,10 @@ static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_ban
  * per pixel, draws for every entry of both halves, flux sums per band in FP64, the dust factor
  * on the behind half.  counts (optional) receives n for every (pixel, half, point) as
  * counts[(p - pix_begin) * 2 * n_pts + h * n_pts + i].  Returns nonzero on a sampler overrun. */
-/* Total-count sampler (Section 2.1 footnote: a sum of Poisson counts is Poisson with the summed
- * mean, and conversely a Poisson total split over the points by their weights gives independent
- * Poisson counts).  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 10
+/* Total-count sampler.  The Section 2.1 footnote states that a sum of Poisson counts is Poisson
+ * with the summed mean; the sampler uses the converse (the standard splitting property, not
+ * stated in the paper): a Poisson total split over the points by their weights gives
+ * independent Poisson counts.  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 10
  * (lambda_i 2^40 is exact in FP64), and the pool of one half is every point with L_i > 0, in
  * point order (the others below 10 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
  * are exact integers; the total's mean is Lambda = (float)(Lfix 2^-40), the FP64 conversion

@@ -365,8 +365,9 @@ __device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &
 }
 
 
-// Total-count sampler of half H (Section 2.1 footnote: Poisson totals split by weight give
-// independent Poisson counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
+// Total-count sampler of half H (the Section 2.1 footnote's additivity of Poisson counts, used
+// in reverse: a Poisson total split over the points by their weights gives independent Poisson
+// counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
 // by inversion (Lambda < 10) or by transformed rejection with point index 2^32 - 1; star s takes
 // word s & 3 of Philox(p, 2^31 | s >> 2, set, HI|H) and goes to the first pool entry with
 // u < T_j (the last takes the rest): the top 14 bits of u select a guide bucket, a binary

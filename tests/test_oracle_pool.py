@@ -1,4 +1,5 @@
-"""The total-count (pool) sampler of the oracle (Section 2.1 footnote): per pixel and half the
+"""The total-count (pool) sampler of the oracle (the Poisson additivity of the Section 2.1
+footnote, used in reverse as the splitting property): per pixel and half the
 points below lambda 10 get N ~ Poisson(sum lambda) stars assigned by their weights.  Pins: the
 per-point counts are independent Poisson(lambda_i) (means, variances, zero fractions, pairwise
 covariances, a joint chi-square), the total is Poisson, the image mean equals the per-point
