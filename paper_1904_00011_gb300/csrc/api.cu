@@ -373,7 +373,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(ctx->tab_in.ensure(up_bytes));
     ctx->desc_d = reinterpret_cast<SetDesc *>(ctx->tab_in.as<uint8_t>() + desc_off);
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
-    CK(ctx->tab_scratch.ensure(sizeof(uint4) * 2 * (size_t)G * n_sets * n_scr));
+    const size_t grp_scr = 2 * (size_t)G * n_sets * n_scr, pt_scr = 2 * (size_t)G * kGroup * n_sets;
+    CK(ctx->tab_scratch.ensure(sizeof(uint4) * (grp_scr + pt_scr)));
     CK(ctx->items.ensure(sizeof(uint2) * n_items));
     CK(ctx->order.ensure(sizeof(uint32_t) * n_items));
     std::memcpy(ctx->h_tab_in.as<uint8_t>() + desc_off, ctx->descs.data(), sizeof(SetDesc) * n_sets);
@@ -409,6 +410,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     ta.insp_z0 = insp_z0;
     ta.pool = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 1 : 0;
     ta.pool_scratch = ta.pool ? ta.scratch + 2 * (size_t)G * n_sets : nullptr;
+    ta.pt_scratch = ta.scratch + grp_scr;
     {
         KTimer t(ctx, PCMD_K_TABLES, ctx->st);
         CK(launch_build_tables(ta, n_sets, ctx->st));

@@ -196,6 +196,8 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const TabSetIn in = a.sets[s];
     const PointIn p = g < a.G ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
     const PointCls c = classify(p);
+    if (g < a.G)   // the write pass reads these instead of running the threshold series again
+        a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t] = make_uint4(c.z0, c.z1, c.tail, (uint32_t)c.cls);
     uint32_t n_tail, n_ptrs;
     group_scan(c.cls == 1 ? c.tail : 0u, j, n_tail);
     group_scan(c.cls == 2 ? 1u : 0u, j, n_ptrs);
@@ -377,7 +379,14 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     uint32_t z0 = 0xFFFFFFFFu, z1 = 0xFFFFFFFFu, len = 0u;
     const bool inv = p.valid && p.lam > 0.0f && p.lam < kPtrsThreshold;
     // this lane's tail length first (for the in-group offsets), then the values
-    const PointCls c = inv ? classify(p) : PointCls{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    if (inv) {   // as the count pass classified it
+        const uint4 pc = a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t];
+        c.z0 = pc.x;
+        c.z1 = pc.y;
+        c.tail = pc.z;
+        c.cls = (int)pc.w;
+    }
     uint32_t tot;
     const uint32_t my_tail = group_scan(c.cls == 1 ? c.tail : 0u, j, tot);
     const uint32_t my_ptrs = group_scan(p.valid && p.lam >= kPtrsThreshold ? 1u : 0u, j, tot);
@@ -387,6 +396,8 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         z0 = c.z0;
         z1 = c.z1;
         len = c.tail;
+    }
+    if (c.cls == 1 && c.tail > 0u) {
         bool sat = false;
         uint32_t n = 0;
         thresholds_dev(p.lam, [&](int k, uint32_t z) {

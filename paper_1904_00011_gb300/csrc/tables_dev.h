@@ -49,6 +49,7 @@ struct TabArgs {
     uint32_t *insp_z0;          //   Z_0 [2][P] (0xFFFFFFFF unless 0 < lambda < 10)
     int pool;                   // also build the total-count sampler regions
     uint4 *pool_scratch;        // [n_sets][2][G] pool entries and fixed-point sums (pool only)
+    uint4 *pt_scratch;          // [n_sets][2][16 G] per point: Z_0, Z_1, tail length, class
 };
 
 TabLayout tab_layout(uint32_t P, int n_bands);
