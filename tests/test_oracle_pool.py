@@ -122,3 +122,24 @@ def test_pool_tables_small_cases_are_exact():
     assert list(idx) == [1] and tot == 0.25
     idx, thr, tot = O.pool_tables(np.array([1e-13, 10.0, 0.0], np.float32))
     assert idx.size == 0
+
+
+def test_pool_counts_of_both_dust_halves_have_their_own_poisson_means():
+    """Full model with the dust screen (F_dust = 0.5): each half's pool gets N ~ Poisson(its
+    Lambda); per point the counts of half h average lambda_h,i and the per-pixel totals of
+    each half have Poisson mean and variance."""
+    w = dataclasses.replace(W.full(n_im=64, psf=False), flags=W.full().flags | W.FLAG_POOL)
+    lam_h, _, _ = O.tables(w)
+    n_pix = 1500
+    _, cnt = O.simulate(w, 0, 9, counts=True, pix_end=n_pix, n_threads=8)
+    for h in range(2):
+        lam = lam_h[h].astype(np.float64)
+        pool = (lam > 0) & (lam < 10)
+        c = cnt[:, h, :].astype(np.float64)
+        top = np.argsort(np.where(pool, lam, 0.0))[-8:]
+        se = np.sqrt(lam[top] / n_pix)
+        assert np.all(np.abs(c[:, top].mean(axis=0) - lam[top]) < 5 * se)
+        tot = c[:, pool].sum(axis=1)
+        lt = lam[pool].sum()
+        assert abs(tot.mean() - lt) < 5 * math.sqrt(lt / n_pix)
+        assert abs(tot.var() / lt - 1.0) < 0.15
