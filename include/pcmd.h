@@ -265,8 +265,9 @@ typedef struct {
  * the whole device, or a latency-sensitive loop where cudaMalloc / cudaFree would synchronise the
  * device and stall other streams.  It does what pcmd_hess does for one image (periodic PSF
  * convolution, sky and photon noise, magnitudes, Hess diagram, moments) without a context and
- * without allocating: its working memory is one fixed array of about 34 KB that the library keeps
- * on every device it runs on until the process exits.
+ * without allocating: the image size, set id and PSF weights travel in the kernel parameters, and
+ * its only working memory is one fixed 24 KB array (per-CTA moment partials) that the library
+ * keeps on every device it runs on until the process exits.
  *  cfg        pixel-stage settings (host)
  *  d_image    [n_bands][n_im][n_im] raw fluxes (device, e.g. from pcmd_simulate)
  *  n_im       image edge, 1..PCMD_NOALLOC_MAX_IM; larger images return PCMD_ERR_ARG
@@ -277,8 +278,9 @@ typedef struct {
  * Results equal pcmd_hess's for the same image, settings and set id.  Asynchronous.
  * The first call on each device looks up the array's device address (make that first call
  * before capturing a stream).  All calls on a device share the array: calls that overlap on the
- * GPU (different streams without ordering between them) race and corrupt each other's moments;
- * order them on one stream or with events. */
+ * GPU (different streams without ordering between them) race and corrupt each other's moments
+ * (never their histograms, counters or memory accesses); order them on one stream or with
+ * events.  A non-finite setting or PSF weight returns PCMD_ERR_ARG. */
 pcmd_status pcmd_hess_noalloc(const pcmd_pixel_config *cfg, const float *d_image, int n_im,
                               uint32_t *d_hess, double *d_moments, uint32_t *d_counters,
                               void *stream);

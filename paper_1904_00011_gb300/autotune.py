@@ -9,6 +9,7 @@ shape; only the FP32 summation order of the fluxes does.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 from typing import Dict, Iterable, List, Optional, Sequence, Tuple
@@ -23,13 +24,30 @@ DEFAULT_CANDIDATES: List[Tuple[int, int, int]] = [
 ]
 
 
-def _key(sim, n_ims: Sequence[int], fused: bool) -> str:
+def _digest(values) -> str:
+    h = hashlib.sha1()
+    for v in values:
+        h.update(repr(v).encode())
+    return h.hexdigest()[:16]
+
+
+def _key(sim, n_ims: Sequence[int], fused: bool, params=()) -> str:
+    """Workload signature: GPU, points, bands, flags, every image size (hashed) and every
+    parameter set's values (hashed: Npix, distance and dust set the mix of sparse, dense and
+    transformed-rejection draws, hence the best shape)."""
     import torch
     name = torch.cuda.get_device_name()
-    sizes = sorted(set(int(n) for n in n_ims))
-    sig = "%s|P=%d|B=%d|flags=%d|sets=%d|sizes=%s|fused=%d" % (
-        name, sim.n_points, sim.w.n_bands, sim.w.flags, len(n_ims),
-        ",".join(map(str, sizes[:4] + sizes[-2:])), int(fused))
+    sizes = [int(n) for n in n_ims]
+    pvals = []
+    for p in params:
+        if hasattr(p, "log_sfh"):
+            pvals.append(tuple(round(float(x), 6) for x in list(p.log_sfh) +
+                               [p.feh_mean, p.feh_sigma, p.log_ebv, p.dust_sigma, p.dmod]))
+        else:
+            pvals.append(repr(p))
+    sig = "%s|P=%d|B=%d|flags=%d|sets=%d|sizes=%s|params=%s|fused=%d" % (
+        name, sim.n_points, sim.w.n_bands, sim.w.flags, len(n_ims), _digest(sizes),
+        _digest(pvals), int(fused))
     return sig
 
 
@@ -56,7 +74,7 @@ def tune(sim, params, n_ims: Sequence[int], candidates: Optional[Iterable[Tuple[
     """Pick and apply the fastest launch shape for ``sim`` on this workload.  ``fused`` times the
     fused batched evaluation (needs ``mock`` = (hess tensor, moments, n_pix, mode)) instead of
     the image-mode draw kernel."""
-    key = _key(sim, n_ims, fused)
+    key = _key(sim, n_ims, fused, params)
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
         best = cache[key]
@@ -80,6 +98,8 @@ def tune(sim, params, n_ims: Sequence[int], candidates: Optional[Iterable[Tuple[
         ms, cnt = kt["graph"] if fused else kt["draw"]
         if cnt:
             results.append((ms / cnt, block, split, chunk))
+    if not results:
+        raise RuntimeError("autotune: no candidate launch shape could be run on this workload")
     results.sort()
     t, block, split, chunk = results[0]
     sim.set_launch(block, split, chunk)

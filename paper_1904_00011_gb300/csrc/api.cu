@@ -475,13 +475,15 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
     if (c.imf != PCMD_IMF_POWER && c.imf != PCMD_IMF_KROUPA) return PCMD_ERR_ARG;
     if (!is_fin(c.mdf_cut) || c.mdf_cut < 0.0 || c.mdf_cut >= 1.0) return PCMD_ERR_ARG;
     if (c.hess_nx < 1 || c.hess_ny < 1 || (long long)c.hess_nx * c.hess_ny > 40000) return PCMD_ERR_ARG;
-    if (!(c.hess_width > 0.0) || !is_fin(c.hess_c_lo) || !is_fin(c.hess_m_lo)) return PCMD_ERR_ARG;
+    if (!(c.hess_width > 0.0) || !is_fin(c.hess_width) || !is_fin(c.hess_c_lo) || !is_fin(c.hess_m_lo))
+        return PCMD_ERR_ARG;
     if (c.max_im < 1 || c.max_im > 16384 || c.max_sets < 1 || c.max_sets > 65535) return PCMD_ERR_ARG;
     if (c.psf && (c.psf_size < 1 || c.psf_size > PCMD_MAX_PSF || (c.psf_size & 1) == 0)) return PCMD_ERR_ARG;
     if (c.psf_grid != 0 && c.psf_grid != 1 && c.psf_grid != 4) return PCMD_ERR_ARG;
     const size_t P = (size_t)c.n_ages * c.n_feh * c.n_mass;
     for (int b = 0; b < c.n_bands; ++b)
-        if (!(c.exptime[b] > 0.0) || !is_fin(c.zeropoint[b]) || !is_fin(c.sky[b]) || c.sky[b] < 0.0 ||
+        if (!(c.exptime[b] > 0.0) || !is_fin(c.exptime[b]) || !is_fin(c.zeropoint[b]) ||
+            !is_fin(c.sky[b]) || c.sky[b] < 0.0 ||
             !is_fin(c.r_ext[b]))
             return PCMD_ERR_ARG;
     for (size_t i = 0; i < P; ++i) {

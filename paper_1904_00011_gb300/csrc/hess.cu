@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
                                                             const __grid_constant__ PsfW pw) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int set = blockIdx.y;
-    const SetDesc &d = a.desc[set];
-    const int N = (int)d.n_im;
+    const SetDesc *dp = a.desc ? a.desc + set : nullptr;
+    const int N = dp ? (int)dp->n_im : (int)a.one_n_im;
+    const uint32_t set_id = dp ? dp->set_id : a.one_set_id;
+    const uint64_t img_off = dp ? dp->img_off : 0ull;
     const uint32_t npix = (uint32_t)N * (uint32_t)N;
     const int ks = KS > 0 ? KS : (KS == 0 ? 0 : a.psf_size);
     const int R = ks / 2;
@@ -87,10 +89,11 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
     const int tid = threadIdx.x;
     for (int i = tid; i < nbins; i += kHessThreads) hist[i] = 0u;
     if (KS < 0 && !GRID)
-        for (int i = tid; i < B * ks * ks; i += kHessThreads) wsm[i] = a.psf[i];
+        for (int i = tid; i < B * ks * ks; i += kHessThreads)
+            wsm[i] = a.psf ? a.psf[i] : (&pw.w[0][0])[i];
     __syncthreads();
 
-    const float *img = a.image + d.img_off;
+    const float *img = a.image + img_off;
     float *pout = a.pixels ? a.pixels + a.pix_off[set] : nullptr;
     const int tiles_x = (N + kTileW - 1) / kTileW;
     const int n_tiles = tiles_x * ((N + kTileH - 1) / kTileH);
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
             int bin = -1;
             if (y < N && x < N) {
                 const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
-                const PixelOut o = pixel_stage<B>(F, p, d.set_id, a.pc);
+                const PixelOut o = pixel_stage<B>(F, p, set_id, a.pc);
                 if (o.valid) {
                     cs += (double)__fsub_rn(o.col, a.pc.c_lo);
                     ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
                     else if (KS > 0) F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, pw.w[b], ks);
                     else F[b] = conv_pixel<B, KS>(tile + b * hx * hy, hx, ty, tx, wsm + b * ks * ks, ks);
                 }
-                const PixelOut o = pixel_stage<B>(F, p, d.set_id, a.pc);
+                const PixelOut o = pixel_stage<B>(F, p, set_id, a.pc);
                 if (o.valid) {
                     cs += (double)__fsub_rn(o.col, a.pc.c_lo);
                     ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
@@ -258,7 +261,7 @@ static cudaError_t launch_hess_t(const HessArgs &a, const PsfW &w, size_t smem, 
 
 template <int B>
 static cudaError_t launch_hess_b(const HessArgs &a, const PsfW &w, size_t smem, cudaStream_t st) {
-    if (!a.psf || a.psf_size == 0) return launch_hess_t<B, 0, false>(a, w, smem, st);
+    if ((!a.psf && !a.psf_in_param) || a.psf_size == 0) return launch_hess_t<B, 0, false>(a, w, smem, st);
     if (a.psf_grid == 4) {
         if (a.psf_size == 25) return launch_hess_t<B, 25, true>(a, w, smem, st);
         return launch_hess_t<B, -1, true>(a, w, smem, st);
@@ -268,9 +271,11 @@ static cudaError_t launch_hess_b(const HessArgs &a, const PsfW &w, size_t smem, 
 }
 
 // The 25x25 weights travel as a kernel parameter (constant bank, compile-time offsets);
-// psf25_host is the context's host copy [kMaxBands][625] (or nullptr).
+// psf25_host is the context's host copy [kMaxBands][625] (or nullptr).  With psf_in_param the
+// same array holds packed [B][S][S] weights of any size S (identical layout for S = 25).
 cudaError_t launch_hess(const HessArgs &a, const float *psf25_host, cudaStream_t st) {
-    const size_t smem = hess_smem_bytes(a.n_bands, a.psf ? a.psf_size : 0, a.pc.nx, a.pc.ny);
+    const bool has_psf = (a.psf || a.psf_in_param) && a.psf_size > 0;
+    const size_t smem = hess_smem_bytes(a.n_bands, has_psf ? a.psf_size : 0, a.pc.nx, a.pc.ny);
     PsfW w;
     for (int b = 0; b < kMaxBands; ++b)
         for (int i = 0; i < 625; ++i) w.w[b][i] = psf25_host ? psf25_host[b * 625 + i] : 0.0f;
@@ -334,14 +339,17 @@ cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *v
 }
 
 // One warp per set: lane l adds partials l, l + 32, ... in order, then a fixed xor tree.
+// begin == nullptr: one set, partials [0, one_count).
 __global__ void moments_finalize_kernel(const double *partials, const uint32_t *begin,
-                                        const uint32_t *count, int n_sets, double *moments) {
+                                        const uint32_t *count, int n_sets, double *moments,
+                                        uint32_t one_count) {
     const int s = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     if (s >= n_sets) return;
     const uint32_t lane = threadIdx.x & 31u;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    const double *p = partials + (size_t)begin[s] * 3;
-    for (uint32_t i = lane; i < count[s]; i += 32u) {
+    const double *p = partials + (begin ? (size_t)begin[s] * 3 : 0);
+    const uint32_t cnt = begin ? count[s] : one_count;
+    for (uint32_t i = lane; i < cnt; i += 32u) {
         a0 += p[i * 3 + 0];
         a1 += p[i * 3 + 1];
         a2 += p[i * 3 + 2];
@@ -363,7 +371,13 @@ cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part
                                     const uint32_t *part_count, int n_sets, double *moments,
                                     cudaStream_t st) {
     moments_finalize_kernel<<<(n_sets + 3) / 4, 128, 0, st>>>(partials, part_begin, part_count,
-                                                             n_sets, moments);
+                                                             n_sets, moments, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_finalize_one(const double *partials, uint32_t count, double *moments,
+                                        cudaStream_t st) {
+    moments_finalize_kernel<<<1, 32, 0, st>>>(partials, nullptr, nullptr, 1, moments, count);
     return cudaGetLastError();
 }
 

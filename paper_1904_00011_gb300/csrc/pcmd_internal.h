@@ -124,9 +124,12 @@ struct DrawArgs {
 // PSF / noise / magnitude / Hess stage over raw images.
 struct HessArgs {
     const float *image;         // raw images
-    const SetDesc *desc;        // for n_im, set_id, img_off
+    const SetDesc *desc;        // for n_im, set_id, img_off; nullptr: one image described by
+    uint32_t one_n_im, one_set_id;  //   these two values (image at offset 0)
     int n_sets, n_bands;
     const float *psf;           // device [B][S][S] (or [16][B][S][S] with psf_grid 4), or nullptr
+    int psf_in_param;           // nonzero: no device copy, the [B][S][S] weights are the launch's
+                                //   host weight array (packed, S = psf_size), passed by value
     int psf_size;
     int psf_grid;               // 1, or 4: a 4x4 grid of regions with their own kernels
     uint32_t *hess;             // [n_sets][ny][nx]
@@ -156,6 +159,9 @@ cudaError_t launch_bin_mags(const float *mag, const float *col, const uint8_t *v
 cudaError_t launch_moments_finalize(const double *partials, const uint32_t *part_begin,
                                     const uint32_t *part_count, int n_sets, double *moments,
                                     cudaStream_t st);
+// one set whose partials are partials[0 .. count) (range passed by value)
+cudaError_t launch_moments_finalize_one(const double *partials, uint32_t count, double *moments,
+                                        cudaStream_t st);
 // CTAs per set of the likelihood (several when few sets leave SMs idle); `part` holds
 // [n_sets][ctas] partial sums, `ticket` [n_sets] counters that are zero between launches.
 int loglike_ctas_per_set(int n_sets, int nbins);

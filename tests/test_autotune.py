@@ -75,3 +75,28 @@ def test_tune_applies_the_fastest_shape_and_skips_rejected_ones(monkeypatch, tmp
     sim2 = _FakeSim({k: 1.0 for k in times})
     again = autotune.tune(sim2, [None], [256], candidates=cands, use_cache=True)
     assert again["cached"] and sim2.applied == [(256, 1, 32)]
+
+
+def test_tune_raises_when_no_candidate_runs(monkeypatch, tmp_path):
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "stand-in")
+    sim = _FakeSim({})
+    with pytest.raises(RuntimeError, match="no candidate"):
+        autotune.tune(sim, [None], [256], candidates=[(256, 3, 64), (48, 1, 64)], use_cache=False)
+
+
+def test_cache_key_covers_every_size_and_the_parameters(monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "stand-in")
+    from paper_1904_00011_gb300 import workloads as W
+    sim = _FakeSim({})
+    p = W.full().params[0]
+    sizes = [128, 144, 160, 176, 192, 512]
+    k0 = autotune._key(sim, sizes, False, [p])
+    # a size in the middle of the list changes the key (not only the first four and last two)
+    assert autotune._key(sim, sizes[:4] + [208] + sizes[5:], False, [p]) != k0
+    # another Npix (the sampler mix) changes the key
+    q = dataclasses.replace(p, log_sfh=p.log_sfh + 3.0)
+    assert autotune._key(sim, sizes, False, [q]) != k0
+    assert autotune._key(sim, sizes, False, [p]) == k0

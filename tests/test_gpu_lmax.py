@@ -36,3 +36,25 @@ def test_batched_repeats_equal_single_evaluations(psf):
     assert np.std(ll_b) > 0.0                       # the likelihood is stochastic
     l_max = S.lmax_from_repeats(ll_b)
     assert ll_b.min() <= l_max <= ll_b.max()
+
+
+@pytest.mark.parametrize("psf", [True, False])
+def test_repeats_match_oracle(psf):
+    """Five of the batched repeats (set ids 500-504) against the oracle's forward model and
+    likelihood (Eq. 2-4) on the same set ids, with the oracle's own realisation as the data."""
+    import oracle as O
+    import paper_1904_00011_gb300 as P
+    O.build()
+    n_im, reps = 64, 24
+    w = W.full(n_im=n_im, psf=psf)
+    mock = O.model(w, 0, 123_456, n_threads=16)
+    d_mock = torch.from_numpy(mock["hist"].view(np.int32)).cuda()
+    sim = P.Simulator(w, max_sets=100)
+    p = w.params[0]
+    ll_b = sim.evaluate([p] * reps, [n_im] * reps, d_mock, mock["moments"], n_im * n_im, W.LL_PAPER,
+                        first_set_id=500)
+    for k in range(5):
+        ref = O.model(w, 0, 500 + k, n_threads=16)
+        ll_o = O.loglike(ref["hist"], ref["moments"], n_im * n_im, mock["hist"], mock["moments"],
+                         n_im * n_im, O.LL_PAPER)
+        assert ll_b[k] == pytest.approx(ll_o, rel=1e-4), (k, ll_b[k], ll_o)

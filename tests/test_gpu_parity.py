@@ -38,10 +38,6 @@ def _u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def _flux_close(got, ref, scale):
-    return np.abs(got - ref) <= FLUX_RTOL * np.maximum(np.abs(ref), 1e-3 * scale)
-
-
 # ------------------------------------------------------------------------------ tables
 
 def _parametric_full():
@@ -130,8 +126,8 @@ def test_raw_flux_full_size_sampled(name):
     for k, p in enumerate(picks):
         ref[:, k] = O.simulate(w, 0, 0, pix_begin=p, pix_end=p + 1)[:, p]
     got = img[:, picks]
-    scale = np.abs(ref).mean()
-    assert np.all(_flux_close(got, ref, scale)), np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-9))
+    rel = np.abs(got - ref) / np.where(ref != 0.0, np.abs(ref), 1.0)
+    assert np.all(rel <= FLUX_RTOL), rel.max()
 
 
 # ------------------------------------------------------------------------------ end to end
@@ -146,9 +142,13 @@ def _end_to_end(w, n_threads=16):
     return s, h, m, c, px, ref
 
 
-@pytest.mark.parametrize("name", ["tiny", "full_small", "full", "psf_grid", "psf_grid_ragged", "pool"])
+@pytest.mark.parametrize("name", ["tiny", "full_small", "full", "psf_grid", "psf_grid_ragged", "pool",
+                                  "large_physics"])
 def test_end_to_end_fluxes_bins_loglike(name):
+    # large_physics: the large-Npix model (3 bands, log10 Npix 6, transformed rejection dominant,
+    # Kahan sums, dust, 25x25 PSF, noise) on a 128x128 image
     w = {"tiny": W.tiny, "full_small": lambda: W.full(n_im=128, sky=40.0),
+         "large_physics": lambda: W.large(n_im=128, log_npix=6.0),
          "full": W.full, "psf_grid": lambda: W.full(n_im=128, psf_grid=True),
          "psf_grid_ragged": lambda: W.full(n_im=100, psf_grid=True, sky=10.0),
          "pool": lambda: dataclasses.replace(W.full(n_im=128, sky=20.0),
@@ -160,9 +160,11 @@ def test_end_to_end_fluxes_bins_loglike(name):
     px = px.cpu().numpy().reshape(B + 2, npix)
     # noisy fluxes (post PSF and noise)
     fl = px[:B].astype(np.float64)
-    scale = np.abs(ref["flux"]).mean()
-    ok = _flux_close(fl, ref["flux"], scale)
-    assert ok.mean() > 0.9999, ok.mean()
+    # every pixel within 1e-5 relative of the FP64 oracle (no pixel exempt); a pixel whose
+    # noisy flux is exactly zero in the oracle may only be zero on the GPU too
+    rel = np.abs(fl - ref["flux"]) / np.where(ref["flux"] != 0.0, np.abs(ref["flux"]), 1.0)
+    print("%s: max relative error of the noisy fluxes %.3g over %d values" % (name, rel.max(), rel.size))
+    assert np.all(rel <= FLUX_RTOL), (rel.max(), np.unravel_index(np.argmax(rel), rel.shape))
     # bins: pixels whose (ix, iy) differ
     valid = ref["valid"] > 0
     gv = ~np.isnan(px[B])
@@ -244,6 +246,46 @@ def test_fused_batch_matches_per_set_path_and_oracle():
         ll_o = O.loglike(ref["hist"], ref["moments"], n2, mock["hist"], mock["moments"], 96 * 96,
                          O.LL_POISSON)
         assert ll[k] == pytest.approx(ll_o, rel=LL_RTOL)
+
+
+def test_batch_of_full_size_sets_matches_oracle():
+    """The batched workload at its own sizes: 20 of its sets (images 128..512, log10 Npix 1..6)
+    plus three 512x512 sets at log10 Npix 5.5, 5.8 and 6.0 (transformed rejection dominant),
+    all in one fused persistent launch.  Every set's likelihood against the oracle's; the big
+    sets' counts at sampled pixels bit for bit; every set's Hess diagram (per-set path, same
+    set ids) within the bin-change bar."""
+    w0 = W.batch()
+    params = list(w0.params[:20])
+    sizes = list(w0.n_ims[:20])
+    for lg in (5.5, 5.8, 6.0):
+        params.append(dataclasses.replace(w0.params[0], log_sfh=np.array([lg])))
+        sizes.append(512)
+    w = W.with_params(w0, params, sizes)
+    mp = W.batch_mock_params()
+    mock = O.model(W.with_params(w0, [mp], [256]), 0, 999, n_threads=16)
+    d_mock = torch.from_numpy(mock["hist"].view(np.int32)).cuda()
+    s = _sim(w, max_sets=w.n_sets, max_im=512)
+    first = 7000
+    ll = s.evaluate(w.params, w.n_ims, d_mock, mock["moments"], 256 * 256, W.LL_POISSON,
+                    first_set_id=first)
+    s.simulate(w.params, w.n_ims, first)
+    h, m, c, _ = s.hess(w.n_sets, w.n_ims)
+    gh_all, gc_all = _u32(h), _u32(c)
+    for k in range(w.n_sets):
+        n2 = w.n_ims[k] ** 2
+        ref = O.model(w, k, first + k, n_threads=16)
+        gh = gh_all[k]
+        assert gh.sum() + gc_all[k].sum() == n2
+        assert np.abs(gh.astype(np.int64) - ref["hist"].astype(np.int64)).sum() <= \
+            2 * max(1, int(BIN_CHANGE_MAX * n2)), k
+        ll_o = O.loglike(ref["hist"], ref["moments"], n2, mock["hist"], mock["moments"], 256 * 256,
+                         O.LL_POISSON)
+        assert ll[k] == pytest.approx(ll_o, rel=LL_RTOL), (k, ll[k], ll_o)
+    big = _sim(w, max_im=512)
+    for k in range(20, 23):
+        got = _u32(big.counts(w.params[k], 512, first + k, 131000, 48))
+        _, ref = O.simulate(w, k, first + k, pix_begin=131000, pix_end=131048, counts=True, n_threads=16)
+        assert np.array_equal(got, ref), k
 
 
 def test_launch_shape_does_not_change_counts():

@@ -84,3 +84,20 @@ def test_no_alloc_rejects_oversized_image():
     with pytest.raises(P.PcmdError) as e:
         P.pcmd_hess_noalloc(cfg, buf.data_ptr(), 8193, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), None)
     assert e.value.code == 1
+
+
+def test_no_alloc_rejects_non_finite_settings():
+    import paper_1904_00011_gb300 as P
+    from paper_1904_00011_gb300 import workloads as W
+    w = W.tiny()
+    buf = torch.zeros(16, device="cuda")
+    for field, value in (("sky", float("inf")), ("exptime", float("inf")), ("zeropoint", float("nan")),
+                         ("hess_c_lo", float("nan")), ("hess_width", float("inf"))):
+        cfg = _pixel_config(w, 0, None)
+        if field in ("sky", "exptime", "zeropoint"):
+            getattr(cfg, field)[0] = value
+        else:
+            setattr(cfg, field, value)
+        with pytest.raises(P.PcmdError) as e:
+            P.pcmd_hess_noalloc(cfg, buf.data_ptr(), 8, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), None)
+        assert e.value.code == 1, field
