@@ -18,12 +18,12 @@
  *            as 1, 2, 3"), key = 64-bit seed, counter = (pixel, index, set, tag).
  *   tag      kind << 28 | half << 27 | sub;  kinds HI=1, LO=2, PTRS=3, DUST=4, NOISE=5.
  *   uniform  u(w) = ((w >> 8) | 1) * 2^-24, exact in FP32, in (0, 1).
- *   inversion (lambda < 10): x = b << 24 | l >> 8 with b byte (i & 3) of word (i & 15) >> 2
+ *   inversion (lambda < 64): x = b << 24 | l >> 8 with b byte (i & 3) of word (i & 15) >> 2
  *            of the HI call with index i >> 4, l word (i & 3) of the LO call with index
  *            i >> 2; v = (x + 0.5) 2^-32;
  *            n = min{k : v < F_k}, F_k the FP64 Poisson CDF by p_k = p_{k-1} lambda / k,
- *            capped at 64.
- *   PTRS (lambda >= 10): Hormann (1993) transformed rejection with squeeze, attempts a use
+ *            capped at 128.
+ *   PTRS (lambda >= 64): Hormann (1993) transformed rejection with squeeze, attempts a use
  *            words 2(a&1), 2(a&1)+1 of the PTRS call with sub = a >> 1; acceptance in the
  *            deviance form of the log-pmf (Loader 2000), all in FP32 with the series log below.
  */
@@ -135,7 +135,12 @@ float or_lnf(float x)
 /* Poisson sampler                                                                        */
 /* ------------------------------------------------------------------------------------- */
 
-/* Inversion for lambda < 10: n = min{k : v < F_k}, v = (x + 0.5) 2^-32, FP64 CDF. */
+/* The sampler's boundary: inversion below, transformed rejection at and above; inversion counts
+ * are capped at OR_INV_CAP (P(n > 128) < 2^-40 for every mean below 64). */
+#define OR_INV_LIMIT 64.0f
+#define OR_INV_CAP 128u
+
+/* Inversion for lambda < 64: n = min{k : v < F_k}, v = (x + 0.5) 2^-32, FP64 CDF. */
 uint32_t or_poisson_inversion(float lam_f, uint32_t x)
 {
     double lam = (double)lam_f;
@@ -143,7 +148,7 @@ uint32_t or_poisson_inversion(float lam_f, uint32_t x)
     double F = p;
     double v = ldexp((double)x + 0.5, -32);
     uint32_t k = 0;
-    while (v >= F && k < 64u) {
+    while (v >= F && k < OR_INV_CAP) {
         k = k + 1u;
         p = p * lam;
         p = p / (double)k;
@@ -231,7 +236,7 @@ float or_log_pmf(float kf, float lam)
 
 #define OR_PTRS_MAX_ATTEMPTS 1024u
 
-/* Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Returns the count,
+/* Transformed rejection with squeeze (Hormann 1993) for lambda >= 64.  Returns the count,
  * or UINT32_MAX if the attempt cap is reached. */
 uint32_t or_poisson_ptrs(const float c6[6], uint64_t seed, uint32_t pix, uint32_t i,
                          uint32_t set, uint32_t half, uint32_t *attempts_out)
@@ -271,7 +276,7 @@ uint32_t or_draw(float lam, uint64_t seed, uint32_t pix, uint32_t i, uint32_t se
                  int *err)
 {
     if (lam == 0.0f) return 0u;
-    if (lam < 10.0f) return or_poisson_inversion(lam, or_draw_word(seed, pix, i, set, half));
+    if (lam < OR_INV_LIMIT) return or_poisson_inversion(lam, or_draw_word(seed, pix, i, set, half));
     float c6[6];
     or_ptrs_setup(lam, c6);
     uint32_t n = or_poisson_ptrs(c6, seed, pix, i, set, half, NULL);
@@ -433,9 +438,9 @@ static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_ban
 /* Total-count sampler.  The Section 2.1 footnote states that a sum of Poisson counts is Poisson
  * with the summed mean; the sampler uses the converse (the standard splitting property, not
  * stated in the paper): a Poisson total split over the points by their weights gives
- * independent Poisson counts.  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 10
+ * independent Poisson counts.  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 64
  * (lambda_i 2^40 is exact in FP64), and the pool of one half is every point with L_i > 0, in
- * point order (the others below 10 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
+ * point order (the others below 64 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
  * are exact integers; the total's mean is Lambda = (float)(Lfix 2^-40), the FP64 conversion
  * rounding to nearest.  Star assignment thresholds T_j = min(floor(C_j 2^32 / Lfix), 2^32 - 1)
  * in exact integer arithmetic; a star with word u goes to the first pool entry with u < T_j,
@@ -455,7 +460,7 @@ static void or_pool_build(const float *lam, int n_pts, or_pool *pl)
     uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n_pts > 0 ? n_pts : 1));
     uint64_t c = 0;
     for (int i = 0; i < n_pts; ++i) {
-        if (!(lam[i] > 0.0f && lam[i] < 10.0f)) continue;
+        if (!(lam[i] > 0.0f && lam[i] < OR_INV_LIMIT)) continue;
         uint64_t w = (uint64_t)((double)lam[i] * 1099511627776.0);
         if (w == 0) continue;
         c += w;
@@ -491,12 +496,12 @@ static uint32_t or_pool_pick(const or_pool *pl, uint32_t u)
 }
 
 /* Number of pool stars of (pixel, half): inversion on word 0 of Philox(p, 2^32 - 1, set, LO|h)
- * below 10, transformed rejection with point index 2^32 - 1 at and above. */
+ * below 64, transformed rejection with point index 2^32 - 1 at and above. */
 static uint32_t or_pool_total(const or_pool *pl, uint64_t seed, uint32_t pix, uint32_t set, uint32_t half,
                               int *err)
 {
     if (pl->n == 0) return 0u;
-    if (pl->lam < 10.0f) {
+    if (pl->lam < OR_INV_LIMIT) {
         uint32_t w[4];
         or_call(seed, pix, 0xFFFFFFFFu, set, or_tag(OR_KIND_LO, half, 0), w);
         return or_poisson_inversion(pl->lam, w[0]);
@@ -529,7 +534,7 @@ int or_simulate(int n_pts, int n_bands, const float *lam_h, const double *flux, 
         for (uint32_t h = 0; h < 2; ++h) {
             for (uint32_t i = 0; i < (uint32_t)n_pts; ++i) {
                 float lam = lam_h[(size_t)h * n_pts + i];
-                if (pool && lam < 10.0f) continue;      /* drawn through the pool below */
+                if (pool && lam < OR_INV_LIMIT) continue;      /* drawn through the pool below */
                 int e = 0;
                 uint32_t n = or_draw(lam, seed, p, i, set, h, &e);
                 err |= e;

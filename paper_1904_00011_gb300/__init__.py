@@ -99,6 +99,7 @@ def lib():
         L.pcmd_sync.argtypes = [vp]
         L.pcmd_n_points.argtypes = [vp]
         L.pcmd_set_launch.argtypes = [vp, i, i, i]
+        L.pcmd_set_attempt_cap.argtypes = [vp, i]
         L.pcmd_get_tables.argtypes = [vp, parp, vp, vp, vp]
         L.pcmd_sfh_bins.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.pcmd_sfh_bins.restype = ctypes.c_int
@@ -109,7 +110,8 @@ def lib():
         L.pcmd_gemm_bf16.argtypes = [vp, i, vp, i, vp, i, vp, vp, i, i, i, i, vp, vp]
         L.pcmd_kernel_times.argtypes = [vp, dp, ip]
         for name in ["pcmd_create", "pcmd_simulate", "pcmd_hess", "pcmd_loglike", "pcmd_evaluate",
-                     "pcmd_sync", "pcmd_n_points", "pcmd_set_launch", "pcmd_get_tables",
+                     "pcmd_sync", "pcmd_n_points", "pcmd_set_launch", "pcmd_set_attempt_cap",
+                     "pcmd_get_tables",
                      "pcmd_counts", "pcmd_bin_mags", "pcmd_profile", "pcmd_kernel_times",
                      "pcmd_hess_noalloc", "pcmd_gemm_bf16"]:
             getattr(L, name).restype = ctypes.c_int
@@ -145,7 +147,15 @@ def make_params(p: "workloads.Params") -> pcmd_params:
     return out
 
 
-def params_array(ps: Sequence["workloads.Params"]):
+def params_array(ps):
+    """pcmd_params[n] from a list of workloads.Params, or (no per-set Python work) from a float64
+    matrix [n][PCMD_MAX_SFH + 5] laid out as the struct: log SFH bins, [Fe/H] mean and width,
+    log E(B-V), dust width, distance modulus."""
+    if isinstance(ps, np.ndarray):
+        a = np.ascontiguousarray(ps, np.float64)
+        if a.ndim != 2 or a.shape[1] != PCMD_MAX_SFH + 5:
+            raise ValueError("parameter matrix must be [n][%d]" % (PCMD_MAX_SFH + 5))
+        return (pcmd_params * a.shape[0]).from_buffer(a)
     arr = (pcmd_params * len(ps))()
     for k, p in enumerate(ps):
         arr[k] = make_params(p)
@@ -254,6 +264,10 @@ def pcmd_set_launch(ctx, block: int, split: int, chunk: int) -> None:
     _check(lib().pcmd_set_launch(ctx, block, split, chunk), "pcmd_set_launch", ctx)
 
 
+def pcmd_set_attempt_cap(ctx, cap: int) -> None:
+    _check(lib().pcmd_set_attempt_cap(ctx, cap), "pcmd_set_attempt_cap", ctx)
+
+
 # ------------------------------------------------------------------------------------------
 # Simulator: a context built from a Workload
 # ------------------------------------------------------------------------------------------
@@ -328,6 +342,9 @@ class Simulator:
 
     def set_launch(self, block: int, split: int, chunk: int):
         pcmd_set_launch(self.ctx, block, split, chunk)
+
+    def set_attempt_cap(self, cap: int):
+        pcmd_set_attempt_cap(self.ctx, cap)
 
     def profile(self, enable: bool = True):
         pcmd_profile(self.ctx, enable)

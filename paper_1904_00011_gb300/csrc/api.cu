@@ -14,7 +14,7 @@
 #include "tables_dev.h"
 
 namespace pcmd {
-int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool ptrs, int block, size_t smem);
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool full, int block, size_t smem);
 }
 
 using namespace pcmd;
@@ -79,6 +79,7 @@ struct pcmd_ctx {
     cudaStream_t cap_st = nullptr;
     int device = 0, n_sm = 1;
     int block = 256, split = 4, chunk = 64;
+    uint32_t ptrs_cap = kPtrsMaxAttempts;   // transformed-rejection attempt cap of a draw
 
     SetDesc *desc_d = nullptr;  // the models' descriptors (inside tab_in, uploaded with it)
     DevBuf tables, items, order, partials, part_begin, part_count, image, pix_off, hess,
@@ -95,7 +96,7 @@ struct pcmd_ctx {
     std::vector<uint32_t> order_list;
 
     int n_sets = 0;
-    bool may_ptrs = true;       // a staged model may have points at lambda >= 10
+    bool needs_full = true;     // a staged model may have dense or transformed-rejection points
     std::vector<int> n_im;
     float *img_ptr = nullptr;
     bool have_images = false, have_hess = false;
@@ -112,8 +113,16 @@ struct pcmd_ctx {
     Uploaded up_items, up_order, up_part_begin, up_part_count, up_pix_off;
 
     // graph of the fused evaluation
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<size_t> gkey;   // shape, launch and every device pointer the graph captured
+    // instantiated graphs of the fused evaluation, one per shape (set count, work items, launch,
+    // mock, and every device pointer the graph captured), least recently used evicted first:
+    // a sampler loop over images of a few sizes replays without re-capturing
+    struct GraphEntry {
+        std::vector<size_t> key;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_tick = 0;
 
     // kernel timing (pcmd_profile)
     bool profiling = false;
@@ -298,7 +307,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::vector<double> mdf;
     uint64_t img_off = 0;
     uint32_t m1_i = 0;
-    bool may_ptrs = false;
+    bool needs_full = (ctx->cfg.flags & PCMD_FLAG_POOL) != 0;
     for (int s = 0; s < n_sets; ++s) {
         tin[s].m1_k = m1_k[s];
         tin[s].m1_off = 0;
@@ -313,7 +322,9 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
             const double sfh = std::pow(10.0, p[s].log_sfh[j]);
             for (int k = 0; k < m.n_feh; ++k) w[j * m.n_feh + k] = sfh * mdf[k];
         }
-        {   // an upper bound of the largest lambda: is the transformed-rejection path needed?
+        {   // an upper bound of the largest lambda: can the model have dense inversion groups or
+            // transformed-rejection points (the draw kernel's full instantiation), or only sparse
+            // inversion groups?
             double bound = 0.0;
             for (int j = 0; j < m.n_ages; ++j)
                 for (int k = 0; k < m.n_feh; ++k) {
@@ -325,7 +336,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
                     }
                     bound = std::max(bound, w[j * m.n_feh + k] * im);
                 }
-            if (bound * std::max(hf[0], hf[1]) >= 0.999 * (double)kPtrsThreshold) may_ptrs = true;
+            if (bound * std::max(hf[0], hf[1]) >= 0.999 * (double)kDenseLam) needs_full = true;
         }
         tin[s].base = (uint64_t)s * L.bytes;
         tin[s].flux_factor = std::pow(10.0, -0.4 * p[s].dmod);
@@ -417,7 +428,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         t.done(ctx->st);
     }
     ctx->n_sets = n_sets;
-    ctx->may_ptrs = may_ptrs;
+    ctx->needs_full = needs_full;
     ctx->n_im.assign(n_im, n_im + n_sets);
     return PCMD_OK;
 }
@@ -440,6 +451,7 @@ static DrawArgs base_draw_args(pcmd_ctx *ctx) {
     a.chunk = ctx->chunk;
     a.split = ctx->split;
     a.n_points = (uint32_t)ctx->model.n_points();
+    a.ptrs_cap = ctx->ptrs_cap;
     a.pc = pixel_consts(ctx);
     return a;
 }
@@ -449,13 +461,13 @@ static pcmd_status launch_draw_mode(pcmd_ctx *ctx, DrawArgs &a, int mode) {
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, mode, ctx->cfg.hess_nx,
                                         ctx->cfg.hess_ny);
-    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->may_ptrs, ctx->block, smem);
+    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->needs_full, ctx->block, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = std::min<int>((int)a.n_items, per_sm * ctx->n_sm);
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->st));
     KTimer t(ctx, PCMD_K_DRAW, ctx->st);
-    CK(launch_draw(a, B, kahan, mode, ctx->may_ptrs, grid, ctx->block, smem, ctx->st));
+    CK(launch_draw(a, B, kahan, mode, ctx->needs_full, grid, ctx->block, smem, ctx->st));
     t.done(ctx->st);
     return PCMD_OK;
 }
@@ -569,7 +581,8 @@ pcmd_status pcmd_create(const pcmd_config *cfg, pcmd_ctx **out) {
 void pcmd_destroy(pcmd_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->st);
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (auto &g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < PCMD_KERNEL_KINDS; ++k)
         for (auto &pr : ctx->ev[k]) {
             cudaEventDestroy(pr.first);
@@ -623,6 +636,13 @@ pcmd_status pcmd_set_launch(pcmd_ctx *ctx, int block, int split, int chunk) {
     ctx->block = block;
     ctx->split = split;
     ctx->chunk = chunk;
+    return PCMD_OK;
+}
+
+pcmd_status pcmd_set_attempt_cap(pcmd_ctx *ctx, int cap) {
+    if (!ctx) return PCMD_ERR_ARG;
+    if (cap < 0 || cap > (int)kPtrsMaxAttempts) return arg_error(ctx, "attempt cap must be 0..1024");
+    ctx->ptrs_cap = cap == 0 ? kPtrsMaxAttempts : (uint32_t)cap;
     return PCMD_OK;
 }
 
@@ -843,7 +863,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, kModeFused,
                                         ctx->cfg.hess_nx, ctx->cfg.hess_ny);
-    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->may_ptrs, ctx->block, smem));
+    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->needs_full, ctx->block, smem));
     const int grid = std::max(1, std::min<int>((int)n_items, per_sm * ctx->n_sm));
     uint64_t mk[4];
     std::memcpy(&mk[0], &mom[0], 8);
@@ -852,16 +872,19 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     std::memcpy(&mk[3], &npix, 8);
     const std::vector<size_t> key = {
         (size_t)n_sets, n_items, (size_t)grid, (size_t)mode, (size_t)ctx->block, (size_t)ctx->split,
-        (size_t)ctx->chunk, (size_t)ctx->may_ptrs, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
+        (size_t)ctx->chunk, (size_t)ctx->ptrs_cap, (size_t)ctx->needs_full, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
         (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
         (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
         (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p,
         (size_t)ctx->ll_part.p, (size_t)ctx->ll_ticket.p};
-    if (ctx->gexec && ctx->gkey != key) {
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = nullptr;
-    }
-    if (!ctx->gexec) {
+    cudaGraphExec_t gexec = nullptr;
+    for (auto &g : ctx->graphs)
+        if (g.key == key) {
+            gexec = g.exec;
+            g.used = ++ctx->graph_tick;
+            break;
+        }
+    if (!gexec) {
         DrawArgs a = base_draw_args(ctx);
         a.hess = ctx->hess.as<uint32_t>();
         a.counters = ctx->counters.as<uint32_t>();
@@ -871,7 +894,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         cudaMemsetAsync(ctx->hess.p, 0, sizeof(uint32_t) * nbins * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->counters.p, 0, sizeof(uint32_t) * 2 * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->cap_st);
-        launch_draw(a, B, kahan, kModeFused, ctx->may_ptrs, grid, ctx->block, smem, ctx->cap_st);
+        launch_draw(a, B, kahan, kModeFused, ctx->needs_full, grid, ctx->block, smem, ctx->cap_st);
         launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
                                 ctx->part_count.as<uint32_t>(), n_sets, ctx->moments.as<double>(),
                                 ctx->cap_st);
@@ -880,14 +903,26 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
                        (ctx->cfg.flags & PCMD_FLAG_SIGMA_SQRTSUM) ? 1 : 0, ctx->ll_part.as<double>(),
                        ctx->ll_ticket.as<uint32_t>(), ctx->ll.as<double>(), ctx->cap_st);
         CK(cudaStreamEndCapture(ctx->cap_st, &g));
-        cudaError_t ec = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaError_t ec = cudaGraphInstantiate(&gexec, g, 0);
         cudaGraphDestroy(g);
         CK(ec);
-        ctx->gkey = key;
+        constexpr size_t kMaxGraphs = 32;
+        if (ctx->graphs.size() >= kMaxGraphs) {
+            size_t lru = 0;
+            for (size_t i = 1; i < ctx->graphs.size(); ++i)
+                if (ctx->graphs[i].used < ctx->graphs[lru].used) lru = i;
+            cudaGraphExecDestroy(ctx->graphs[lru].exec);
+            ctx->graphs.erase(ctx->graphs.begin() + (long)lru);
+        }
+        pcmd_ctx::GraphEntry ge;
+        ge.key = key;
+        ge.exec = gexec;
+        ge.used = ++ctx->graph_tick;
+        ctx->graphs.push_back(std::move(ge));
     }
     {
         KTimer t(ctx, PCMD_K_GRAPH, ctx->st);
-        CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+        CK(cudaGraphLaunch(gexec, ctx->st));
         t.done(ctx->st);
     }
     ctx->hess_ptr = ctx->hess.as<uint32_t>();

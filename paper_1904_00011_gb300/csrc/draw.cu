@@ -8,7 +8,7 @@
 // pixel and split (a CTA's warps share a pixel tile and divide the isochrone points), with
 // the point tables streamed through shared memory by bulk copies.
 //
-// Draw word of inversion point i (lambda < 10) of half h at pixel p:
+// Draw word of inversion point i (lambda < 64) of half h at pixel p:
 //   x = b << 24 | l >> 8, b = byte i & 3 of word (i & 15) >> 2 of Philox(p, i >> 4, set, HI|h),
 //   l = word i & 3 of Philox(p, i >> 2, set, LO|h);  n = #{k : x > Z_k}.
 // The fast path only needs b: b < Z_0 >> 24 gives n = 0 without the LO call, and a certain hit
@@ -51,7 +51,7 @@ __device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
     return __fsub_rn(r, st);
 }
 
-// Transformed rejection with squeeze (Hormann 1993) for lambda >= 10.  Attempt `at` uses words
+// Transformed rejection with squeeze (Hormann 1993) for lambda >= 64.  Attempt `at` uses words
 // 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).  The cheap part of an attempt decides
 // the squeeze acceptance and the quick rejections; the rest takes the log-form test.
 struct PtrsTry {
@@ -92,10 +92,12 @@ __device__ __forceinline__ uint4 ptrs_words(const PtrsRec &r, uint32_t pix, uint
 }
 
 // The attempt loop of one draw; out of line, so that the caller's registers stay its own.
+// After `cap` attempts without acceptance the draw gives 0 and latches kErrSampler.
 __device__ __noinline__ uint32_t ptrs_draw(const PtrsRec &r, uint32_t pix, uint32_t set, uint32_t half,
-                                           const uint32_t *rk0, const uint32_t *rk1, uint32_t *err) {
+                                           const uint32_t *rk0, const uint32_t *rk1, uint32_t cap,
+                                           uint32_t *err) {
     uint4 w = make_uint4(0, 0, 0, 0);
-    for (uint32_t at = 0; at < kPtrsMaxAttempts; ++at) {
+    for (uint32_t at = 0; at < cap; ++at) {
         if ((at & 1u) == 0u) w = ptrs_words(r, pix, set, half, at, rk0, rk1);
         const PtrsTry t = ptrs_cheap(r, (at & 1u) ? w.z : w.x, (at & 1u) ? w.w : w.y);
         if (t.status == 0) return (uint32_t)t.kf;
@@ -133,6 +135,20 @@ struct Acc {
         }
     }
     template <int H>
+    __device__ __forceinline__ void add_sum(const float *v) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (KAHAN) {
+                const float y = __fsub_rn(v[b], c[H][b]);
+                const float t = __fadd_rn(s[H][b], y);
+                c[H][b] = __fsub_rn(__fsub_rn(t, s[H][b]), y);
+                s[H][b] = t;
+            } else {
+                s[H][b] = __fadd_rn(s[H][b], v[b]);
+            }
+        }
+    }
+    template <int H>
     __device__ __forceinline__ float value(int b) const {
         return KAHAN ? __fsub_rn(s[H][b], c[H][b]) : s[H][b];
     }
@@ -155,55 +171,65 @@ struct ItemCtx {
 
 constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
 
-// The chunk double buffer, large enough to hold the transformed-rejection test queues
-// (64 tasks of 16 bytes per warp) that use it between items.
-__host__ __device__ constexpr uint32_t chunk_region_bytes(uint32_t chunk, uint32_t rec, uint32_t block) {
-    return 2u * chunk * rec > block * 32u ? 2u * chunk * rec : block * 32u;
-}
+// The chunk double buffer: two chunks of group records.
+__host__ __device__ constexpr uint32_t chunk_region_bytes(uint32_t chunk, uint32_t rec) { return 2u * chunk * rec; }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// n = #{k : x > Z_k} from the slow record of a slot: Z_0, Z_1 in the record, Z_2.. in the tail
-// (saturated beyond its length).  The search starts at the record's start index k_s (near
-// lambda) and walks up or down; the count equals the linear scan's.
+// n = #{k : x > Z_k} from the slow record of a slot: the first n0 thresholds are -1 (every word
+// exceeds them), Z'_k = Z_{n0 + k}: Z'_0, Z'_1 in the record, Z'_2.. in the tail (saturated
+// beyond its length).  n = n0 + #{k : x > Z'_k}.  The search starts at the record's start index
+// k_s (near lambda - n0) and walks up or down; the count equals the linear scan's.
 __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint4 &sr, const uint32_t *tail) {
-    if (x <= sr.x) return 0u;
-    if (x <= sr.y) return 1u;
-    const uint32_t len = sr.w & 0xFFFFu;
+    const uint32_t n0 = (sr.w >> 8) & 0xFFu;
+    if (x <= sr.x) return n0;
+    if (x <= sr.y) return n0 + 1u;
+    const uint32_t len = sr.w & 0xFFu;
     uint32_t ks = sr.w >> 16;                       // 2 <= ks <= len + 1
     if (ks < 2u) ks = 2u;
     auto z = [&](uint32_t k) { return k - 2u < len ? __ldg(tail + sr.z + (k - 2u)) : 0xFFFFFFFFu; };
     uint32_t k = ks;
     if (x > z(k)) {
         do { ++k; } while (k - 2u < len && x > z(k));
-        return k;                                   // first k with x <= Z_k
+        return n0 + k;                              // first k with x <= Z'_k
     }
     while (k > 2u && x <= z(k - 1u)) --k;
-    return k;
+    return n0 + k;
 }
 
-// Resolve the queued maybe-hits of the warp's 32 pixels together: entry = g << 12 | slot << 8 |
-// byte, g the group's index in the staged chunk.  The lanes' queues are enumerated as one list
-// (lane order, then queue order) and every lane resolves every 32nd entry: n = 1 when the byte
-// is above Z_0 >> 24 and below Z_1 >> 24, otherwise the LO call of the slot's quad (for the
-// entry owner's pixel) completes the 32-bit word and the full thresholds decide.  The count
-// replaces the byte in place.  Called by all 32 lanes of the warp.
-template <int B, int MODE, int H>
-__device__ __forceinline__ void resolve_warp(const DrawArgs &a, uint32_t pix, uint32_t set,
-                                          const SlowRec *slow, const uint32_t *tail,
-                                          const uint8_t *cb, uint32_t *queue, int qn) {
+// The warp's queued maybe-hits, resolved by all 32 lanes together.  Queue entry of a lane's
+// group with maybe-hits: g | prefix << 8 | hm << 16, g the group's index in the staged chunk,
+// hm its maybe-hit mask (bit 4q + k = byte q of HI word k = slot 4k + q), prefix the number of
+// maybe-hit bits in the lane's earlier entries (written here).  The bits of all 32 lanes are
+// enumerated as one list (lane order, then entry order, then bit order); every lane takes every
+// 32nd: it finds the owner lane and entry by binary searches, recomputes the owner's HI word,
+// and decides n: 1 when the byte is above Z_0 >> 24 and below Z_1 >> 24, otherwise the LO call
+// of the slot's quad completes the 32-bit word and the full thresholds decide.  The fluxes
+// n f_b of one owner's consecutive list positions are summed by a segmented warp scan (a fixed
+// tree), each owner adds its segments' totals in list order, and the drain's total goes into
+// the pixel's accumulator once.  Called by all 32 lanes of the warp.
+template <int B, bool KAHAN, int MODE, int H>
+__device__ __forceinline__ void drain_warp(const DrawArgs &a, const ItemCtx &ic, const PhiloxPrefix &pf,
+                                           const uint8_t *cb, uint32_t *queue, int qn,
+                                           Acc<B, KAHAN> &acc) {
     constexpr uint32_t rec = group_rec_bytes(B);
-    const uint32_t lane = threadIdx.x & 31u, wbase = threadIdx.x & ~31u;
-    uint32_t inc = (uint32_t)qn;
+    const uint32_t lane = threadIdx.x & 31u, wbase = threadIdx.x & ~31u, bd = blockDim.x;
+    uint32_t nb = 0;
+    for (int e = 0; e < qn; ++e) {
+        uint32_t *q = queue + (uint32_t)e * bd + threadIdx.x;
+        const uint32_t m = *q;
+        *q = (m & 0xFFFF00FFu) | (nb << 8);
+        nb += (uint32_t)__popc(m >> 16);
+    }
+    uint32_t inc = nb;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= (uint32_t)o) inc += t;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-    const uint32_t off = inc - (uint32_t)qn;            // first list index of this lane's entries
+    const uint32_t off = inc - nb;                      // first list position of this lane's bits
+    float part[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) part[b] = 0.0f;
     for (uint32_t v0 = 0; v0 < total; v0 += 32u) {
         const uint32_t v = v0 + lane;
         uint32_t o = 0;                                  // owner: last lane with off <= v
@@ -212,63 +238,100 @@ __device__ __forceinline__ void resolve_warp(const DrawArgs &a, uint32_t pix, ui
             const uint32_t t = __shfl_sync(0xffffffffu, off, o + (uint32_t)st);
             if (t <= v) o += (uint32_t)st;
         }
-        const uint32_t opix = __shfl_sync(0xffffffffu, pix, o);
-        const uint32_t oq = v - __shfl_sync(0xffffffffu, off, o);
-        if (v >= total) continue;
-        uint32_t *slot = queue + oq * blockDim.x + wbase + o;
-        const uint32_t e = *slot;
-        const uint32_t g = e >> 12, j = (e >> 8) & 15u, hi = e & 0xFFu;
-        const uint8_t *r = cb + g * rec;
-        const uint32_t zc0 = r[kRecZ7 + j] | r[kRecZh + j];
-        const uint32_t zc1 = r[kRecZc1 + j];
-        const uint32_t gid = *reinterpret_cast<const uint32_t *>(r);
-        const uint32_t i = gid * (uint32_t)kGroup + j;
-        uint32_t n;
-        if (hi > zc0 && hi < zc1) {
-            n = 1u;
-        } else {
-            const uint4 wlo = philox_rk(opix, i >> 2, set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
-            const uint32_t x = (hi << 24) | (word_of(wlo, j & 3u) >> 8);
-            const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(slow) + i);
-            n = count_from_thresholds(x, sr, tail);
+        const uint32_t ooff = __shfl_sync(0xffffffffu, off, o);
+        const uint32_t oqn = __shfl_sync(0xffffffffu, (uint32_t)qn, o);
+        const uint32_t opix = __shfl_sync(0xffffffffu, ic.pix, o);
+        PhiloxPrefix fo;
+        fo.x0 = __shfl_sync(0xffffffffu, pf.x0, o);
+        fo.n3 = __shfl_sync(0xffffffffu, pf.n3, o);
+        fo.m1 = __shfl_sync(0xffffffffu, pf.m1, o);
+        fo.hp0 = __shfl_sync(0xffffffffu, pf.hp0, o);
+        fo.o3 = __shfl_sync(0xffffffffu, pf.o3, o);
+        const bool valid = v < total;
+        float c[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) c[b] = 0.0f;
+        if (valid) {
+            const uint32_t r = v - ooff;
+            const uint32_t *oq = queue + wbase + o;
+            uint32_t e = 0;                              // the owner's last entry with prefix <= r
+#pragma unroll
+            for (uint32_t st = 8; st > 0; st >>= 1)
+                if (e + st < oqn && ((oq[(e + st) * bd] >> 8) & 0xFFu) <= r) e += st;
+            const uint32_t m = oq[e * bd];
+            uint32_t hm = m >> 16;
+            for (uint32_t rr = r - ((m >> 8) & 0xFFu); rr; --rr) hm &= hm - 1u;
+            const uint32_t bit = (uint32_t)(__ffs(hm) - 1);
+            const uint32_t k = bit & 3u, q = bit >> 2, j = 4u * k + q;
+            const uint8_t *rp = cb + (m & 0xFFu) * rec;
+            const uint32_t gid = *reinterpret_cast<const uint32_t *>(rp);
+            const uint4 w = philox_from_prefix_rk(fo, gid, a.rk0, a.rk1);
+            const uint32_t hi = (word_of(w, k) >> (8u * q)) & 0xFFu;
+            const uint32_t zc0 = rp[kRecZ7 + j] | rp[kRecZh + j];
+            const uint32_t zc1 = rp[kRecZc1 + j];
+            const uint32_t i = gid * (uint32_t)kGroup + j;
+            uint32_t n;
+            if (hi > zc0 && hi < zc1) {
+                n = 1u;
+            } else {
+                const uint4 wlo = philox_rk(opix, i >> 2, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
+                const uint32_t x = (hi << 24) | (word_of(wlo, q) >> 8);
+                const uint4 sr = __ldg(reinterpret_cast<const uint4 *>(ic.slow[H]) + i);
+                n = count_from_thresholds(x, sr, ic.tail);
+            }
+            if (MODE == kModeCounts && n) {
+                if (opix >= a.count_pix0 && opix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(opix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
+            }
+            if (n) {
+                const float *f = reinterpret_cast<const float *>(rp + kRecFlux) + j * B;
+                const float nf = (float)n;
+#pragma unroll
+                for (int b = 0; b < B; ++b) c[b] = __fmul_rn(nf, f[b]);
+            }
         }
-        *slot = (e & ~0xFFu) | n;                        // n <= kInvCap < 256
-        if (MODE == kModeCounts && n) {
-            if (opix >= a.count_pix0 && opix - a.count_pix0 < a.count_npix)
-                a.counts[((size_t)(opix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
+        // segmented inclusive scan over the list positions of one owner (owners ascend with v)
+        const uint32_t key = valid ? o : 32u + lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t tk = __shfl_up_sync(0xffffffffu, key, d);
+            float t[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) t[b] = __shfl_up_sync(0xffffffffu, c[b], d);
+            if (lane >= (uint32_t)d && tk == key) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) c[b] = __fadd_rn(c[b], t[b]);
+            }
+        }
+        // this lane's segment in this pass ends at list position min(off + nb, v0 + 32) - 1
+        const uint32_t s0 = max(off, v0), s1 = min(off + nb, v0 + 32u);
+        const bool mine = s0 < s1;
+        const uint32_t src = mine ? s1 - 1u - v0 : lane;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const float t = __shfl_sync(0xffffffffu, c[b], src);
+            if (mine) part[b] = __fadd_rn(part[b], t);
         }
     }
-    __syncwarp();
-}
-
-// The warp's queued maybe-hits: resolved together, then every lane adds the fluxes of its own
-// entries in queue order (each pixel's sums accumulate in the order its lane queued them).
-template <int B, bool KAHAN, int MODE, int H>
-__device__ __forceinline__ void drain_warp(const DrawArgs &a, const ItemCtx &ic,
-                                           const uint8_t *cb, uint32_t *queue, int qn,
-                                           Acc<B, KAHAN> &acc) {
-    constexpr uint32_t rec = group_rec_bytes(B);
-    resolve_warp<B, MODE, H>(a, ic.pix, ic.set, ic.slow[H], ic.tail, cb, queue, qn);
-    for (int q = 0; q < qn; ++q) {
-        const uint32_t e = queue[q * blockDim.x + threadIdx.x];
-        const uint32_t n = e & 0xFFu;
-        if (n) {
-            const uint32_t g = e >> 12, j = (e >> 8) & 15u;
-            acc.template add<H>((float)n, reinterpret_cast<const float *>(cb + g * rec + kRecFlux) + j * B);
-        }
-    }
+    if (nb) acc.template add_sum<H>(part);
     __syncwarp();
 }
 
 // One staged chunk of groups: the HI call of every (pixel, group) from the pixel's Philox
-// prefix, four byte-wise compares OR-ed into "any maybe-hit", and the rare maybe-hits pushed to
-// the thread's queue, which it drains when full and at the chunk's end.
+// prefix, four byte-wise compares folded into a 16-bit maybe-hit mask, and one queue entry per
+// group with maybe-hits (a predicated store, no per-bit loop); the warp drains the queues when
+// one would overflow and at the chunk's end.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &ic,
                                               const PhiloxPrefix &pf, const uint8_t *cb,
                                               uint32_t cnt, int sidx, uint32_t *queue,
                                               Acc<B, KAHAN> &acc) {
     constexpr uint32_t rec = group_rec_bytes(B);
+    uint32_t *myq = queue + threadIdx.x;
+    const uint32_t bd = blockDim.x;
+    // a lane queues at most one entry per group: with no more groups per lane than queue slots
+    // in this chunk the queue cannot fill before the chunk's end
+    const bool may_fill = (cnt + (uint32_t)a.split - 1u) / (uint32_t)a.split > (uint32_t)kQueueCap;
     int qn = 0;
 #pragma unroll 2
     for (uint32_t g = (uint32_t)sidx; g < cnt; g += (uint32_t)a.split) {
@@ -279,25 +342,22 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
         const uint4 w = philox_from_prefix_rk(pf, gid, a.rk0, a.rk1);
         const uint32_t m0 = ge_bytes(w.x, z7.x, zh.x), m1 = ge_bytes(w.y, z7.y, zh.y);
         const uint32_t m2 = ge_bytes(w.z, z7.z, zh.z), m3 = ge_bytes(w.w, z7.w, zh.w);
-        // maybe-hits of the 16 points in one word: bit 8q + k is byte q of word k (point 4k + q)
+        // maybe-hits of the 16 points: bit 8q + k of t is byte q of word k (point 4k + q), packed
+        // into 16 bits as bit 4q + k
         uint32_t hm = ((m0 & 0x80808080u) >> 7) | ((m1 & 0x80808080u) >> 6) |
                       ((m2 & 0x80808080u) >> 5) | ((m3 & 0x80808080u) >> 4);
-        if (__any_sync(0xffffffffu, qn + __popc(hm) > kQueueCap)) {
-            drain_warp<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+        hm = (hm | (hm >> 4)) & 0x00FF00FFu;
+        hm = (hm | (hm >> 8)) & 0x0000FFFFu;
+        // branch-free push: the entry goes to slot qn (< kQueueCap: a full queue is drained right
+        // after the push that fills it) and counts only when it has maybe-hits
+        myq[(uint32_t)qn * bd] = g | (hm << 16);
+        qn += hm != 0u ? 1 : 0;
+        if (may_fill && __any_sync(0xffffffffu, qn == kQueueCap)) {
+            drain_warp<B, KAHAN, MODE, H>(a, ic, pf, cb, queue, qn, acc);
             qn = 0;
         }
-        if (hm) {
-            do {
-                const uint32_t bit = (uint32_t)(__ffs(hm) - 1);
-                hm &= hm - 1u;
-                const uint32_t k = bit & 7u, q = bit >> 3;
-                const uint32_t hb = (word_of(w, k) >> (8u * q)) & 0xFFu;
-                queue[qn * blockDim.x + threadIdx.x] = (g << 12) | ((4u * k + q) << 8) | hb;
-                ++qn;
-            } while (hm);
-        }
     }
-    if (__any_sync(0xffffffffu, qn > 0)) drain_warp<B, KAHAN, MODE, H>(a, ic, cb, queue, qn, acc);
+    if (__any_sync(0xffffffffu, qn > 0)) drain_warp<B, KAHAN, MODE, H>(a, ic, pf, cb, queue, qn, acc);
 }
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
@@ -368,7 +428,7 @@ __device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &
 // Total-count sampler of half H (the Section 2.1 footnote's additivity of Poisson counts, used
 // in reverse: a Poisson total split over the points by their weights gives independent Poisson
 // counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
-// by inversion (Lambda < 10) or by transformed rejection with point index 2^32 - 1; star s takes
+// by inversion (Lambda < 64) or by transformed rejection with point index 2^32 - 1; star s takes
 // word s & 3 of Philox(p, 2^31 | s >> 2, set, HI|H) and goes to the first pool entry with
 // u < T_j (the last takes the rest): the top 14 bits of u select a guide bucket, a binary
 // search inside it finds the entry (bounded, so no lane walks a long run of tiny weights).
@@ -378,16 +438,19 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
     if (!ic.active || sidx != H % a.split) return;
     const uint8_t *pr = a.tables + d.pool_off[H];
     const PoolHdr hdr = *reinterpret_cast<const PoolHdr *>(pr);
-    if (hdr.mode == 0u || hdr.n == 0u) return;
+    const uint32_t mode = hdr.mode & 0xFFu;
+    if (mode == 0u || hdr.n == 0u) return;
     uint32_t n_star;
-    if (hdr.mode == 1u) {
+    if (mode == 1u) {
+        // n0 leading thresholds of -1 (bits 8-15 of the mode word), then the walk
         const uint32_t x = philox_rk(ic.pix, 0xFFFFFFFFu, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1).x;
         const uint32_t *z = reinterpret_cast<const uint32_t *>(pr + kPoolZOff);
-        n_star = 0u;
-        while (n_star < hdr.n_z && x > __ldg(z + n_star)) ++n_star;
+        uint32_t k = 0u;
+        while (k < hdr.n_z && x > __ldg(z + k)) ++k;
+        n_star = ((hdr.mode >> 8) & 0xFFu) + k;
     } else {
         const PtrsRec rec = load_ptrs(reinterpret_cast<const PtrsRec *>(pr + kPoolPtrsOff), 0u);
-        n_star = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
+        n_star = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.ptrs_cap, a.err);
     }
     const uint32_t *guide = reinterpret_cast<const uint32_t *>(pr + kPoolGuideOff);
     const uint32_t *idx = reinterpret_cast<const uint32_t *>(pr + kPoolIdxOff);
@@ -419,145 +482,42 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
     }
 }
 
-// Transformed-rejection points: every thread runs the attempt loop of each of its records.
-// Transformed-rejection points of half H, one lane per pixel, each draw's attempts in turn
-// (for launches whose models have few or none of these points).
-template <int B, bool KAHAN, int MODE, int H>
-__device__ __forceinline__ void process_ptrs_lane(const DrawArgs &a, const ItemCtx &ic,
-                                                  const SetDesc &d, int sidx, Acc<B, KAHAN> &acc) {
-    const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
-    const uint32_t n_rec = ic.active ? d.n_ptrs[H] : 0u;
-    for (uint32_t q = (uint32_t)sidx; q < n_rec; q += (uint32_t)a.split) {
-        const PtrsRec rec = load_ptrs(pr, q);
-        const uint32_t n = ptrs_draw(rec, ic.pix, ic.set, H, a.rk0, a.rk1, a.err);
-        ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, n, acc);
-    }
-}
-
-// Transformed-rejection points (lambda >= 10) of half H: every lane (pixel) runs the records
-// q = sidx, sidx + split, ... one attempt per iteration of a warp-wide loop, so lanes do not
-// wait for each other's rejections.  An attempt whose squeeze is inconclusive parks its draw:
-// its log-form test goes to the warp's queue and the lane moves on; the warp evaluates the
-// queued tests 32 at a time, then each lane settles its parked draws in the order it parked
-// them (accepted: fluxes added; rejected: resumed at the next attempt before any new record).
-// Every draw makes exactly the decisions of the per-draw attempt loop.  The parked draws use
-// the lane's hit-queue space, the test queue the (idle) chunk buffers.  Called by all 32 lanes.
-constexpr int kPark = kQueueCap / 2;        // parked draws per lane: (record, attempt | slot)
-constexpr uint32_t kLogQ = 64;              // log tests per warp
-constexpr uint32_t kNoSlot = 0xFFFFu;
-
-struct LogTask {
-    float kf, us, V;
-    uint32_t meta;   // record | owner lane << 24 | accepted << 31
-};
-
+// Transformed-rejection points (lambda >= 64) of half H.  The lanes (pixels) of a warp start on
+// the records q = sidx, sidx + split, ... and every iteration of a warp-wide loop makes one
+// attempt for each lane's current draw: an accepted attempt (squeeze, or the log-form test when
+// the squeeze is inconclusive) gives the count and moves the lane to its next record, a
+// rejected one to the draw's next attempt.  Each draw takes exactly the attempt loop's
+// decisions (first accepted attempt, cap as in ptrs_draw); the lanes never wait for each other's
+// rejections except at the end of their record lists.  Called by all 32 lanes of the warp.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
-                                             int sidx, uint32_t *park, LogTask *wq, Acc<B, KAHAN> &acc) {
+                                             int sidx, Acc<B, KAHAN> &acc) {
     const uint32_t n_rec = d.n_ptrs[H];
     if (n_rec == 0u) return;
     const PtrsRec *pr = reinterpret_cast<const PtrsRec *>(a.tables + d.ptrs_off[H]);
-    const uint32_t lane = threadIdx.x & 31u, stride = blockDim.x;
-    uint32_t *pq = park + threadIdx.x;                   // entry e: pq[2e * stride], pq[(2e + 1) * stride]
-    uint32_t qi = ic.active ? (uint32_t)sidx : n_rec;    // next new record of this lane
-    uint32_t cur_q = 0u, cur_at = 0u;
-    bool has_cur = false;
-    int rh = 0, nr = 0, np = 0;                          // resumable [rh, nr), parked [nr, np)
-    uint32_t wn = 0u;                                    // tests queued (warp-uniform)
-
-    auto settle = [&]() {
-        for (uint32_t v = lane; v < wn; v += 32u) {
-            const LogTask t = wq[v];
-            const PtrsRec rec = load_ptrs(pr, t.meta & 0xFFFFFFu);
-            PtrsTry tt;
-            tt.kf = t.kf;
-            tt.us = t.us;
-            tt.V = t.V;
-            tt.status = 2;
-            if (ptrs_log_accept(rec, tt)) wq[v].meta = t.meta | 0x80000000u;
-        }
-        __syncwarp();
-        int keep = 0;
-        for (int e = rh; e < np; ++e) {
-            const uint32_t q = pq[2 * e * stride], m = pq[(2 * e + 1) * stride];
-            uint32_t at = m & 0xFFFFu;
-            const uint32_t slot = m >> 16;
-            if (slot != kNoSlot) {
-                const LogTask t = wq[slot];
-                if (t.meta >> 31) {
-                    ptrs_resolved<B, KAHAN, MODE, H>(a, ic, load_ptrs(pr, q), (uint32_t)t.kf, acc);
-                    continue;
-                }
-                if (++at >= kPtrsMaxAttempts) {
-                    atomicOr(a.err, kErrSampler);
-                    continue;
-                }
-            }
-            pq[2 * keep * stride] = q;
-            pq[(2 * keep + 1) * stride] = at | (kNoSlot << 16);
-            ++keep;
-        }
-        rh = 0;
-        nr = np = keep;
-        wn = 0u;
-        __syncwarp();
-    };
-
-    for (;;) {
-        if (!has_cur) {
-            if (rh < nr) {
-                cur_q = pq[2 * rh * stride];
-                cur_at = pq[(2 * rh + 1) * stride] & 0xFFFFu;
-                ++rh;
-                has_cur = true;
-            } else if (qi < n_rec) {
-                cur_q = qi;
-                cur_at = 0u;
-                qi += (uint32_t)a.split;
-                has_cur = true;
-            }
-        }
-        if (!__any_sync(0xffffffffu, has_cur)) {
-            if (wn == 0u) break;
-            settle();
-            continue;
-        }
-        bool push = false;
-        PtrsTry t;
-        t.kf = t.us = t.V = 0.0f;
-        if (has_cur) {
-            const PtrsRec rec = load_ptrs(pr, cur_q);
-            const uint4 w = ptrs_words(rec, ic.pix, ic.set, H, cur_at, a.rk0, a.rk1);
-            t = ptrs_cheap(rec, (cur_at & 1u) ? w.z : w.x, (cur_at & 1u) ? w.w : w.y);
-            if (t.status == 0) {
+    uint32_t q = ic.active ? (uint32_t)sidx : n_rec;
+    uint32_t at = 0;
+    PtrsRec rec;
+    if (q < n_rec) rec = load_ptrs(pr, q);
+    uint4 w = make_uint4(0, 0, 0, 0);
+    while (__any_sync(0xffffffffu, q < n_rec)) {
+        if (q < n_rec) {
+            if ((at & 1u) == 0u) w = ptrs_words(rec, ic.pix, ic.set, H, at, a.rk0, a.rk1);
+            const PtrsTry t = ptrs_cheap(rec, (at & 1u) ? w.z : w.x, (at & 1u) ? w.w : w.y);
+            bool done = t.status == 0;
+            if (t.status == 2) done = ptrs_log_accept(rec, t);
+            if (done) {
                 ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, (uint32_t)t.kf, acc);
-                has_cur = false;
-            } else if (t.status == 2 && np < kPark) {
-                push = true;
-            } else if (t.status == 2 && ptrs_log_accept(rec, t)) {   // no parking space: test here
-                ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, (uint32_t)t.kf, acc);
-                has_cur = false;
-            } else if (++cur_at >= kPtrsMaxAttempts) {
+            } else if (++at >= a.ptrs_cap) {
                 atomicOr(a.err, kErrSampler);
-                has_cur = false;
+                done = true;
+            }
+            if (done) {
+                q += (uint32_t)a.split;
+                at = 0u;
+                if (q < n_rec) rec = load_ptrs(pr, q);
             }
         }
-        const uint32_t pushers = __ballot_sync(0xffffffffu, push);
-        if (push) {
-            const uint32_t slot = wn + __popc(pushers & ((1u << lane) - 1u));
-            LogTask lt;
-            lt.kf = t.kf;
-            lt.us = t.us;
-            lt.V = t.V;
-            lt.meta = cur_q | (lane << 24);
-            wq[slot] = lt;
-            pq[2 * np * stride] = cur_q;
-            pq[(2 * np + 1) * stride] = cur_at | (slot << 16);
-            ++np;
-            has_cur = false;
-        }
-        wn += (uint32_t)__popc(pushers);
-        if (wn > kLogQ - 32u || __any_sync(0xffffffffu, np >= kPark)) settle();
     }
 }
 
@@ -577,10 +537,9 @@ __device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uin
     for (int b = 0; b < B; ++b) fac[b] = exp10f(d.dust_c[b] * e);
 }
 
-// PTRS: the launch's models may have many transformed-rejection points (lambda >= 10): they
-// are drawn warp-cooperatively; otherwise each lane draws its few in turn.  Either gives the
-// same counts.
-template <int B, bool KAHAN, int MODE, bool PTRS>
+// FULL: dense inversion groups, transformed-rejection points and the total-count sampler are
+// compiled in; without it the kernel handles launches whose models have sparse groups only.
+template <int B, bool KAHAN, int MODE, bool FULL>
 __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t rec = group_rec_bytes(B);
@@ -589,7 +548,7 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
     volatile uint32_t *s_item = reinterpret_cast<volatile uint32_t *>(smem + 16);
     uint32_t *s_ntouch = reinterpret_cast<uint32_t *>(smem + 20);
     uint8_t *bufs = smem + 32;
-    uint32_t *queue = reinterpret_cast<uint32_t *>(bufs + chunk_region_bytes(chunk, rec, blockDim.x));
+    uint32_t *queue = reinterpret_cast<uint32_t *>(bufs + chunk_region_bytes(chunk, rec));
     float *red = reinterpret_cast<float *>(queue + (size_t)kQueueCap * blockDim.x);
     const int tid = threadIdx.x;
     const int ppc = blockDim.x / a.split;
@@ -637,15 +596,18 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
         ic.tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
         Acc<B, KAHAN> acc;
         acc.init();
-        const PhiloxPrefix pf[2] = {
-            philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 0, 0), a.rk0, a.rk1),
-            philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, 1, 0), a.rk0, a.rk1)};
 
         // ---- inversion points, streamed through shared memory chunk by chunk (or, with the
         // total-count sampler, drawn through the pool) ----
         const uint32_t ng0 = d.pool_on ? 0u : d.n_grp[0], ng1 = d.pool_on ? 0u : d.n_grp[1];
         const uint32_t nc0 = (ng0 + chunk - 1) / chunk, nc1 = (ng1 + chunk - 1) / chunk;
         const uint32_t nc = nc0 + nc1;
+        // Chunk c + 1 is copied while chunk c is processed.  Every thread waits for a chunk's
+        // copy at the end of the previous chunk (or before the first); the barrier after the
+        // wait tells the whole CTA whether any wait ran out, in which case the copy stays
+        // pending (the final drain waits for it), no chunk is read from an unfilled buffer and
+        // the CTA stops (the error is latched).
+        bool stop = false;
         if (tid == 0 && nc > 0) {
             const uint32_t cnt = min(chunk, nc0 > 0 ? ng0 : ng1);
             const uint8_t *src = a.tables + (nc0 > 0 ? d.grp_off[0] : d.grp_off[1]);
@@ -653,50 +615,58 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
             bulk_g2s(bufs, src, cnt * rec, &bars[0]);
             pending |= 1u;
         }
-        for (uint32_t c = 0; c < nc; ++c) {
-            const uint32_t b = c & 1u;
+        if (nc > 0) {
+            const bool ok = mbar_wait(&bars[0], parity & 1u, a.err) || mbar_wait(&bars[0], parity & 1u, a.err);
+            stop = __syncthreads_or(!ok) != 0;
+            if (!stop) {
+                parity ^= 1u;
+                pending &= ~1u;
+            }
+        }
+        for (uint32_t c = 0; c < nc && !stop; ++c) {
+            const uint32_t b = c & 1u, bn = b ^ 1u;
             if (tid == 0 && c + 1 < nc) {
                 const uint32_t cn = c + 1;
                 const uint32_t h = cn >= nc0 ? 1u : 0u;
                 const uint32_t first = (h ? cn - nc0 : cn) * chunk;
                 const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
-                const uint32_t bn = cn & 1u;
                 mbar_expect_tx(&bars[bn], cnt * rec);
                 bulk_g2s(bufs + bn * chunk * rec, a.tables + d.grp_off[h] + (uint64_t)first * rec,
                          cnt * rec, &bars[bn]);
                 pending |= 1u << bn;
             }
-            if (!mbar_wait(&bars[b], (parity >> b) & 1u, a.err)) mbar_wait(&bars[b], (parity >> b) & 1u, a.err);
-            parity ^= 1u << b;
-            pending &= ~(1u << b);
             const uint32_t h = c >= nc0 ? 1u : 0u;
             const uint32_t first = (h ? c - nc0 : c) * chunk;
             const uint32_t cnt = min(chunk, (h ? ng1 : ng0) - first);
             const uint8_t *cb = bufs + b * chunk * rec;
-            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, pf[0], cb, cnt, sidx, queue, acc);
-            else process_chunk<B, KAHAN, MODE, 1>(a, ic, pf[1], cb, cnt, sidx, queue, acc);
-            __syncthreads();
+            // the pixel's HI-call prefix of this half (rounds 1-3 without the group index)
+            const PhiloxPrefix pf = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, h, 0), a.rk0, a.rk1);
+            if (h == 0u) process_chunk<B, KAHAN, MODE, 0>(a, ic, pf, cb, cnt, sidx, queue, acc);
+            else process_chunk<B, KAHAN, MODE, 1>(a, ic, pf, cb, cnt, sidx, queue, acc);
+            bool ok = true;
+            if (c + 1 < nc) {
+                const uint32_t par = (parity >> bn) & 1u;
+                ok = mbar_wait(&bars[bn], par, a.err) || mbar_wait(&bars[bn], par, a.err);
+            }
+            stop = __syncthreads_or(!ok) != 0;
+            if (!stop && c + 1 < nc) {
+                parity ^= 1u << bn;
+                pending &= ~(1u << bn);
+            }
         }
+        if (stop) break;
 
-        // ---- dense inversion groups, then transformed-rejection points (lambda >= 10) ----
-        if (d.pool_on) {
-            process_pool<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
-            process_pool<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
-        } else {
-            process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
-            process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
-        }
-        if (PTRS) {
-            LogTask *wq = reinterpret_cast<LogTask *>(bufs) + (size_t)(tid >> 5) * kLogQ;
-            process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, queue, wq, acc);
-            process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, queue, wq, acc);
-            // the test queue overlays the chunk buffers: order these generic accesses before
-            // the next item's bulk copies into them
-            fence_proxy_async_smem();
-            __syncthreads();
-        } else {
-            process_ptrs_lane<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
-            process_ptrs_lane<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+        // ---- dense inversion groups, then transformed-rejection points (lambda >= 64) ----
+        if (FULL) {
+            if (d.pool_on) {
+                process_pool<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+                process_pool<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+            } else {
+                process_dense<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+                process_dense<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
+            }
+            process_ptrs<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
+            process_ptrs<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);
         }
 
         // ---- combine the splits of each pixel in a fixed order ----
@@ -812,7 +782,8 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
         __syncthreads();
         if (!a.queue) break;
     }
-    // a copy can only be outstanding here after a timed-out wait: wait for it once more
+    // a copy can only be outstanding here after a timed-out wait: wait for it once more before
+    // the CTA (and its shared memory) goes away
     if (tid == 0) {
         for (uint32_t b = 0; b < 2; ++b)
             if (pending & (1u << b)) mbar_wait(&bars[b], (parity >> b) & 1u, a.err);
@@ -820,7 +791,7 @@ __global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawA
 }
 
 size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx, int ny) {
-    size_t s = 32 + chunk_region_bytes((uint32_t)chunk, group_rec_bytes(nb), (uint32_t)block) +
+    size_t s = 32 + chunk_region_bytes((uint32_t)chunk, group_rec_bytes(nb)) +
                (size_t)kQueueCap * block * 4 +
                (size_t)block * 2 * nb * 4;
     if (mode == kModeFused) {
@@ -833,11 +804,11 @@ size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx
 
 // Opt in to the dynamic shared memory of each instantiation once per process (before any
 // stream capture: the first call of every configuration goes through draw_max_blocks_per_sm).
-template <int B, bool KAHAN, int MODE, bool PTRS>
+template <int B, bool KAHAN, int MODE, bool FULL>
 static cudaError_t configure_t(size_t smem) {
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(draw_kernel<B, KAHAN, MODE, PTRS>,
+        cudaError_t e = cudaFuncSetAttribute(draw_kernel<B, KAHAN, MODE, FULL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
@@ -845,72 +816,71 @@ static cudaError_t configure_t(size_t smem) {
     return cudaSuccess;
 }
 
-template <int B, bool KAHAN, int MODE, bool PTRS>
+template <int B, bool KAHAN, int MODE, bool FULL>
 static cudaError_t launch_t(const DrawArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-    cudaError_t e = configure_t<B, KAHAN, MODE, PTRS>(smem);
+    cudaError_t e = configure_t<B, KAHAN, MODE, FULL>(smem);
     if (e != cudaSuccess) return e;
-    draw_kernel<B, KAHAN, MODE, PTRS><<<grid, block, smem, st>>>(a);
+    draw_kernel<B, KAHAN, MODE, FULL><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int B, bool KAHAN, int MODE, bool PTRS>
+template <int B, bool KAHAN, int MODE, bool FULL>
 static int occupancy_t(int block, size_t smem) {
-    if (configure_t<B, KAHAN, MODE, PTRS>(smem) != cudaSuccess) return 0;
+    if (configure_t<B, KAHAN, MODE, FULL>(smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, draw_kernel<B, KAHAN, MODE, PTRS>, block, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, draw_kernel<B, KAHAN, MODE, FULL>, block, smem) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
-template <int B, bool KAHAN, bool PTRS>
+template <int B, bool KAHAN, bool FULL>
 static int occupancy_m(int mode, int block, size_t smem) {
     switch (mode) {
-        case kModeImage: return occupancy_t<B, KAHAN, kModeImage, PTRS>(block, smem);
-        case kModeCounts: return occupancy_t<B, KAHAN, kModeCounts, PTRS>(block, smem);
-        default: return occupancy_t<B, KAHAN, kModeFused, PTRS>(block, smem);
+        case kModeImage: return occupancy_t<B, KAHAN, kModeImage, FULL>(block, smem);
+        case kModeCounts: return occupancy_t<B, KAHAN, kModeCounts, FULL>(block, smem);
+        default: return occupancy_t<B, KAHAN, kModeFused, FULL>(block, smem);
     }
 }
 
 template <int B, bool KAHAN>
-static int occupancy_p(int mode, bool ptrs, int block, size_t smem) {
-    return ptrs ? occupancy_m<B, KAHAN, true>(mode, block, smem) : occupancy_m<B, KAHAN, false>(mode, block, smem);
+static int occupancy_f(int mode, bool full, int block, size_t smem) {
+    return full ? occupancy_m<B, KAHAN, true>(mode, block, smem) : occupancy_m<B, KAHAN, false>(mode, block, smem);
 }
 
-int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool ptrs, int block, size_t smem) {
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool full, int block, size_t smem) {
     switch (nb) {
-        case 2: return kahan ? occupancy_p<2, true>(mode, ptrs, block, smem) : occupancy_p<2, false>(mode, ptrs, block, smem);
-        case 3: return kahan ? occupancy_p<3, true>(mode, ptrs, block, smem) : occupancy_p<3, false>(mode, ptrs, block, smem);
-        default: return kahan ? occupancy_p<4, true>(mode, ptrs, block, smem) : occupancy_p<4, false>(mode, ptrs, block, smem);
+        case 2: return kahan ? occupancy_f<2, true>(mode, full, block, smem) : occupancy_f<2, false>(mode, full, block, smem);
+        case 3: return kahan ? occupancy_f<3, true>(mode, full, block, smem) : occupancy_f<3, false>(mode, full, block, smem);
+        default: return kahan ? occupancy_f<4, true>(mode, full, block, smem) : occupancy_f<4, false>(mode, full, block, smem);
     }
 }
 
-template <int B, bool KAHAN, bool PTRS>
-static cudaError_t launch_m(const DrawArgs &a, int mode, int grid, int block, size_t smem,
-                            cudaStream_t st) {
+template <int B, bool KAHAN, bool FULL>
+static cudaError_t launch_m(const DrawArgs &a, int mode, int grid, int block, size_t smem, cudaStream_t st) {
     switch (mode) {
-        case kModeImage: return launch_t<B, KAHAN, kModeImage, PTRS>(a, grid, block, smem, st);
-        case kModeCounts: return launch_t<B, KAHAN, kModeCounts, PTRS>(a, grid, block, smem, st);
-        default: return launch_t<B, KAHAN, kModeFused, PTRS>(a, grid, block, smem, st);
+        case kModeImage: return launch_t<B, KAHAN, kModeImage, FULL>(a, grid, block, smem, st);
+        case kModeCounts: return launch_t<B, KAHAN, kModeCounts, FULL>(a, grid, block, smem, st);
+        default: return launch_t<B, KAHAN, kModeFused, FULL>(a, grid, block, smem, st);
     }
 }
 
 template <int B, bool KAHAN>
-static cudaError_t launch_p(const DrawArgs &a, int mode, bool ptrs, int grid, int block, size_t smem,
+static cudaError_t launch_f(const DrawArgs &a, int mode, bool full, int grid, int block, size_t smem,
                             cudaStream_t st) {
-    return ptrs ? launch_m<B, KAHAN, true>(a, mode, grid, block, smem, st)
+    return full ? launch_m<B, KAHAN, true>(a, mode, grid, block, smem, st)
                 : launch_m<B, KAHAN, false>(a, mode, grid, block, smem, st);
 }
 
-cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool ptrs, int grid, int block,
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool full, int grid, int block,
                         size_t smem, cudaStream_t st) {
     switch (n_bands) {
-        case 2: return kahan ? launch_p<2, true>(a, mode, ptrs, grid, block, smem, st)
-                             : launch_p<2, false>(a, mode, ptrs, grid, block, smem, st);
-        case 3: return kahan ? launch_p<3, true>(a, mode, ptrs, grid, block, smem, st)
-                             : launch_p<3, false>(a, mode, ptrs, grid, block, smem, st);
-        default: return kahan ? launch_p<4, true>(a, mode, ptrs, grid, block, smem, st)
-                              : launch_p<4, false>(a, mode, ptrs, grid, block, smem, st);
+        case 2: return kahan ? launch_f<2, true>(a, mode, full, grid, block, smem, st)
+                             : launch_f<2, false>(a, mode, full, grid, block, smem, st);
+        case 3: return kahan ? launch_f<3, true>(a, mode, full, grid, block, smem, st)
+                             : launch_f<3, false>(a, mode, full, grid, block, smem, st);
+        default: return kahan ? launch_f<4, true>(a, mode, full, grid, block, smem, st)
+                              : launch_f<4, false>(a, mode, full, grid, block, smem, st);
     }
 }
 

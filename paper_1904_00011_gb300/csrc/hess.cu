@@ -63,7 +63,8 @@ __device__ __forceinline__ void conv_col4(const float *tile_b, int hx, int ty0, 
     }
 }
 
-// KS: 0 = no PSF, 25 = 25x25 weights from the kernel parameter, -1 = any odd size from smem.
+// KS: 0 = no PSF, 25 = 25x25 weights from the kernel parameter, -1 = any odd size from smem
+// (a single 25x25 PSF runs hess_bs_kernel below).
 // GRID: the sub-pixel PSF grid (Section 2.2): output pixel (y, x) takes the kernel of region
 // (4y/N, 4x/N), read from global memory (the region is uniform over most warps, so the loads
 // are broadcasts from L1).
@@ -119,45 +120,6 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
             __syncthreads();
         }
         const int tx = tid & 31;
-        // noise, magnitudes, moments, optional pixel output and histogram of one output pixel
-        // (called by every lane of the warp: the histogram add is warp-aggregated)
-        auto finish = [&](int y, int x, float (&F)[B]) {
-            int bin = -1;
-            if (y < N && x < N) {
-                const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
-                const PixelOut o = pixel_stage<B>(F, p, set_id, a.pc);
-                if (o.valid) {
-                    cs += (double)__fsub_rn(o.col, a.pc.c_lo);
-                    ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
-                    nv += 1.0;
-                    bin = o.bin;
-                    if (bin < 0) ++novf;
-                } else {
-                    ++ninv;
-                }
-                if (pout) {
-#pragma unroll
-                    for (int b = 0; b < B; ++b) pout[(size_t)b * npix + p] = F[b];
-                    pout[(size_t)B * npix + p] = o.valid ? o.mag : __int_as_float(0x7fc00000);
-                    pout[(size_t)(B + 1) * npix + p] = o.valid ? o.col : __int_as_float(0x7fc00000);
-                }
-            }
-            hist_add_warp(hist, nullptr, nullptr, bin, 0u);
-        };
-        if (KS > 0 && !GRID) {
-            // each warp: four adjacent rows of the tile (4 warps x 4 rows = kTileH)
-            const int ty0 = (tid >> 5) * 4;
-            float Fk[4][B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) {
-                float o[4];
-                conv_col4<(KS > 0 ? KS : 1)>(tile + b * hx * hy, hx, ty0, tx, pw.w[b], o);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Fk[k][b] = o[k];
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) finish(y0 + ty0 + k, x0 + tx, Fk[k]);
-        } else
         for (int ty = tid >> 5; ty < kTileH; ty += kHessThreads / 32) {
             const int y = y0 + ty, x = x0 + tx;
             const bool in = y < N && x < N;
@@ -235,6 +197,162 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const __grid_constan
     }
 }
 
+// 4-byte global -> shared copy through the async copy unit (no register staging: every copy of
+// a halo tile is in flight at once).
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__host__ __device__ constexpr int bs_halo_w() { return kTileW + 24; }
+__host__ __device__ constexpr int bs_halo_h() { return kTileH + 24; }
+
+// The 25x25 PSF stage with the tile's convolutions split over bands: 4 warps per band (4 rows
+// each), so a CTA runs 4 B warps.  The halo tile is fetched with one async copy per element from
+// wrapped row / column index tables (periodic boundary), the convolved tile meets in shared
+// memory, and every thread then runs the pixel stage of 512 / (128 B) pixels.
+template <int B>
+__global__ void __launch_bounds__(128 * B) hess_bs_kernel(const __grid_constant__ HessArgs a,
+                                                          const __grid_constant__ PsfW pw) {
+    constexpr int KS = 25, R = KS / 2, HX = bs_halo_w(), HY = bs_halo_h(), NT = 128 * B;
+    constexpr int TP = kTileW * kTileH;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int set = blockIdx.y;
+    const SetDesc *dp = a.desc ? a.desc + set : nullptr;
+    const int N = dp ? (int)dp->n_im : (int)a.one_n_im;
+    const uint32_t set_id = dp ? dp->set_id : a.one_set_id;
+    const uint64_t img_off = dp ? dp->img_off : 0ull;
+    const uint32_t npix = (uint32_t)N * (uint32_t)N;
+    const int nbins = a.pc.nx * a.pc.ny;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    float *tile = reinterpret_cast<float *>(hist + nbins);          // [B][HY][HX]
+    float *conv = tile + B * HY * HX;                                // [B][kTileH][kTileW]
+    int *rowtab = reinterpret_cast<int *>(conv + B * TP);            // [HY] wrapped rows * N
+    int *coltab = rowtab + HY;                                       // [HX] wrapped columns
+    double *wred = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(coltab + HX) + 7u) & ~uintptr_t(7));
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < nbins; i += NT) hist[i] = 0u;
+
+    const float *img = a.image + img_off;
+    float *pout = a.pixels ? a.pixels + a.pix_off[set] : nullptr;
+    const int tiles_x = (N + kTileW - 1) / kTileW;
+    const int n_tiles = tiles_x * ((N + kTileH - 1) / kTileH);
+    double cs = 0.0, ms = 0.0, nv = 0.0;
+    uint32_t novf = 0u, ninv = 0u;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int y0 = (t / tiles_x) * kTileH, x0 = (t % tiles_x) * kTileW;
+        for (int i = tid; i < HY + HX; i += NT) {
+            const int v = (i < HY ? y0 + i : x0 + (i - HY)) - R;
+            const int wv = ((v % N) + N) % N;
+            if (i < HY) rowtab[i] = wv * N;
+            else coltab[i - HY] = wv;
+        }
+        __syncthreads();
+        for (int i = tid; i < B * HY * HX; i += NT) {
+            const int b = i / (HY * HX), r = i - b * (HY * HX);
+            const int ty = r / HX, tx = r - ty * HX;
+            cp_async4(tile + i, img + (size_t)b * npix + (size_t)(rowtab[ty] + coltab[tx]));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        {
+            const int b = wid >> 2, ty0 = (wid & 3) * 4;
+            float o[4];
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb)
+                if (bb == b) conv_col4<KS>(tile + bb * HY * HX, HX, ty0, lane, pw.w[bb], o);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) conv[b * TP + (ty0 + k) * kTileW + lane] = o[k];
+        }
+        __syncthreads();
+        for (int q = tid; q < TP; q += NT) {
+            const int y = y0 + q / kTileW, x = x0 + (q % kTileW);
+            int bin = -1;
+            if (y < N && x < N) {
+                const uint32_t p = (uint32_t)y * (uint32_t)N + (uint32_t)x;
+                float F[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) F[b] = conv[b * TP + q];
+                const PixelOut o = pixel_stage<B>(F, p, set_id, a.pc);
+                if (o.valid) {
+                    cs += (double)__fsub_rn(o.col, a.pc.c_lo);
+                    ms += (double)__fsub_rn(o.mag, a.pc.m_lo);
+                    nv += 1.0;
+                    bin = o.bin;
+                    if (bin < 0) ++novf;
+                } else {
+                    ++ninv;
+                }
+                if (pout) {
+#pragma unroll
+                    for (int b = 0; b < B; ++b) pout[(size_t)b * npix + p] = F[b];
+                    pout[(size_t)B * npix + p] = o.valid ? o.mag : __int_as_float(0x7fc00000);
+                    pout[(size_t)(B + 1) * npix + p] = o.valid ? o.col : __int_as_float(0x7fc00000);
+                }
+            }
+            hist_add_warp(hist, nullptr, nullptr, bin, 0u);
+        }
+        __syncthreads();
+    }
+    uint32_t *gh = a.hess + (size_t)set * nbins;
+    for (int i = tid; i < nbins; i += NT) {
+        const uint32_t v = hist[i];
+        if (v) atomicAdd(gh + i, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        ms += __shfl_xor_sync(0xffffffffu, ms, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        novf += __shfl_xor_sync(0xffffffffu, novf, o);
+        ninv += __shfl_xor_sync(0xffffffffu, ninv, o);
+    }
+    if (lane == 0) {
+        wred[wid * 3 + 0] = cs;
+        wred[wid * 3 + 1] = ms;
+        wred[wid * 3 + 2] = nv;
+        if (novf) atomicAdd(a.counters + (size_t)set * 2 + 0, novf);
+        if (ninv) atomicAdd(a.counters + (size_t)set * 2 + 1, ninv);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            t0 += wred[w * 3 + 0];
+            t1 += wred[w * 3 + 1];
+            t2 += wred[w * 3 + 2];
+        }
+        double *out = a.cta_moments + ((size_t)set * a.ctas_per_set + blockIdx.x) * 3;
+        out[0] = t0 + t2 * (double)a.pc.c_lo;
+        out[1] = t1 + t2 * (double)a.pc.m_lo;
+        out[2] = t2;
+    }
+}
+
+static size_t hess_bs_smem_bytes(int nb, int nx, int ny) {
+    size_t s = (size_t)nx * ny * 4 + (size_t)nb * bs_halo_h() * bs_halo_w() * 4 +
+               (size_t)nb * kTileW * kTileH * 4 + (size_t)(bs_halo_h() + bs_halo_w()) * 4;
+    s = (s + 7) & ~size_t(7);
+    s += (size_t)(128 * nb / 32) * 3 * 8;
+    return s;
+}
+
+template <int B>
+static cudaError_t launch_hess_bs(const HessArgs &a, const PsfW &w, cudaStream_t st) {
+    static size_t configured = 0;
+    const size_t smem = hess_bs_smem_bytes(B, a.pc.nx, a.pc.ny);
+    auto k = hess_bs_kernel<B>;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    dim3 grid(a.ctas_per_set, a.n_sets);
+    k<<<grid, 128 * B, smem, st>>>(a, w);
+    return cudaGetLastError();
+}
+
 size_t hess_smem_bytes(int nb, int psf_size, int nx, int ny) {
     const int R = psf_size / 2;
     size_t s = (size_t)nx * ny * 4;
@@ -266,7 +384,7 @@ static cudaError_t launch_hess_b(const HessArgs &a, const PsfW &w, size_t smem, 
         if (a.psf_size == 25) return launch_hess_t<B, 25, true>(a, w, smem, st);
         return launch_hess_t<B, -1, true>(a, w, smem, st);
     }
-    if (a.psf_size == 25) return launch_hess_t<B, 25, false>(a, w, smem, st);
+    if (a.psf_size == 25) return launch_hess_bs<B>(a, w, st);
     return launch_hess_t<B, -1, false>(a, w, smem, st);
 }
 

@@ -7,8 +7,9 @@ namespace pcmd {
 
 constexpr int kMaxBands = 4;
 constexpr int kGroup = 16;                // isochrone points per HI call (one byte each)
-constexpr float kPtrsThreshold = 10.0f;   // inversion below, transformed rejection at/above
-constexpr int kInvCap = 64;               // inversion counts are capped at 64 (lambda < 10)
+constexpr float kPtrsThreshold = 64.0f;   // inversion below, transformed rejection at/above
+constexpr int kInvCap = 128;              // inversion counts are capped at 128 (P(n > 128) < 2^-40
+                                          // for every lambda below 64)
 constexpr float kDenseLam = 0.3f;         // groups with a slot at or above this are "dense"
 constexpr uint32_t kPtrsMaxAttempts = 1024u;
 
@@ -33,14 +34,16 @@ __host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 64
 constexpr uint32_t kRecZ7 = 16, kRecZh = 32, kRecZc1 = 48, kRecFlux = 64;
 
 // Slow-path record per point and half (global memory): full 32-bit thresholds.
+// The first n0 thresholds of a mean above ~22 are -1 (e^-lambda 2^32 < 1/2: every word exceeds
+// them); the record holds the rest, Z'_k = Z_{n0 + k}, and n = n0 + #{k : x > Z'_k}.
 struct SlowRec {
-    uint32_t z0, z1;        // n > k  <=>  x > Z_k
-    uint32_t tail_off;      // index of Z_2 in the tail array
-    uint32_t tail_len;      // low 16 bits: number of Z_k, k >= 2, below 0xFFFFFFFF;
-                            // high 16 bits: start index of the device's threshold walk
+    uint32_t z0, z1;        // Z'_0, Z'_1: n > n0 + k  <=>  x > Z'_k
+    uint32_t tail_off;      // index of Z'_2 in the tail array
+    uint32_t tail_len;      // bits 0-7: number of Z'_k, k >= 2, below 0xFFFFFFFF; bits 8-15: n0;
+                            // bits 16-31: start index of the device's threshold walk
 };
 
-// Transformed-rejection record (lambda >= 10), 48 bytes.
+// Transformed-rejection record (lambda >= 64), 48 bytes.
 struct PtrsRec {
     uint32_t i;             // canonical point index
     float lam, b, a, twoa, vr, log_ia;
@@ -69,8 +72,8 @@ struct __align__(16) SetDesc {
     uint64_t flux_off;      // float [P][B] electrons per star of every point
 };
 
-// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 10): header,
-// then Z[64] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
+// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 64): header,
+// then Z[kInvCap] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
 // table (guide[b] = first entry j with T_j > b 2^(32 - bits), guide[2^bits] = n - 1), the pool's
 // point indices and their star-assignment thresholds T_j.
 constexpr int kPoolGuideBits = 14;
@@ -78,9 +81,10 @@ struct __align__(16) PoolHdr {
     float lam;              // (float) Lambda
     uint32_t n;             // pool size
     uint32_t n_z;           // thresholds of the total (mode 1)
-    uint32_t mode;          // 0 empty, 1 inversion (Lambda < 10), 2 transformed rejection
+    uint32_t mode;          // bits 0-7: 0 empty, 1 inversion (Lambda < 64), 2 transformed
+                            // rejection; bits 8-15 (inversion): leading thresholds of -1, n0
 };
-constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * 64, kPoolGuideOff = kPoolPtrsOff + 48;
+constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * kInvCap, kPoolGuideOff = kPoolPtrsOff + 48;
 constexpr uint32_t kPoolIdxOff = kPoolGuideOff + 4 * ((1u << kPoolGuideBits) + 4);   // guide[2^bits + 1]
 // ... followed by the pool's fixed-point total (uint64, in a 16-byte slot)
 constexpr double kPoolFix = 1099511627776.0;   // 2^40: fixed-point scale of the pool weights
@@ -114,6 +118,7 @@ struct DrawArgs {
     uint32_t *err;              // device error word
     int chunk;                  // groups per staged chunk (<= 256)
     int split;                  // warps-groups sharing one pixel
+    uint32_t ptrs_cap;          // transformed-rejection attempts per draw before the error
     // FUSED mode (no PSF): histogram outputs
     uint32_t *hess;             // [n_sets][ny][nx]
     uint32_t *counters;         // [n_sets][2]
@@ -142,9 +147,9 @@ struct HessArgs {
 };
 
 // launchers (implemented in the .cu files)
-// ptrs: the models may have transformed-rejection points (lambda >= 10): the warp-cooperative
-// rejection loop instead of the per-lane one (same counts either way)
-cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool ptrs, int grid,
+// full: the models may have dense inversion groups, transformed-rejection points or the
+// total-count sampler; otherwise the kernel only streams sparse inversion groups
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool full, int grid,
                         int block, size_t smem, cudaStream_t st);
 size_t draw_smem_bytes(int n_bands, int chunk, int block, int split, int mode, int nx, int ny);
 enum { kModeImage = 0, kModeCounts = 1, kModeFused = 2 };

@@ -18,12 +18,14 @@ namespace pcmd {
 
 namespace {
 
-__device__ __forceinline__ uint32_t threshold_dev(double F) {
+// Z = ceil(F 2^32 - 1/2) - 1, saturated at 2^32 - 1; -1 when F 2^32 <= 1/2 (every word exceeds it).
+__device__ __forceinline__ int64_t threshold_dev(double F) {
     const double y = __dsub_rn(__dmul_rn(F, 4294967296.0), 0.5);
-    if (y >= 4294967295.0) return 0xFFFFFFFFu;
+    if (y >= 4294967295.0) return 0xFFFFFFFFll;
+    if (!(y > 0.0)) return -1;
     const uint64_t t = (uint64_t)y;
     const uint64_t T = t + (y > (double)t ? 1u : 0u);
-    return (uint32_t)(T - 1u);
+    return (int64_t)T - 1;
 }
 
 // IMF weight and electrons per star (distance modulus 0) of point i: the context's arrays,
@@ -62,25 +64,39 @@ __device__ __forceinline__ PointIn point_of(const TabArgs &a, const TabSetIn &in
     return p;
 }
 
-// Thresholds of an inversion point: calls f(k, Z_k) for k = 0 .. while Z_k < 2^32 - 1 (and the
-// first saturated one), at most kInvCap values; returns Z_0.
+// Thresholds of an inversion point.  The first n0 thresholds are -1 (every word exceeds them;
+// only at means above ~22, where e^-lambda 2^32 < 1/2); the count is n0 plus the walk over the
+// others, Z'_k = Z_{n0 + k}.  Calls f(k, Z'_k) for k = 0 .. while Z'_k < 2^32 - 1 (and the first
+// saturated one), kInvCap thresholds in all; returns n0 and Z'_0.
+struct ZHead {
+    uint32_t n0, z0;
+};
 template <class F>
-__device__ __forceinline__ uint32_t thresholds_dev(float lam_f, F &&f) {
+__device__ __forceinline__ ZHead thresholds_dev(float lam_f, F &&f) {
     const double lam = (double)lam_f;
     double p = exp(-lam);
     double Fk = p;
-    uint32_t z0 = threshold_dev(Fk);
-    f(0, z0);
-    if (z0 == 0xFFFFFFFFu) return z0;
-    for (int k = 1; k < kInvCap; ++k) {
-        p = __dmul_rn(p, lam);
-        p = __ddiv_rn(p, (double)k);
-        Fk = __dadd_rn(Fk, p);
-        const uint32_t t = threshold_dev(Fk);
-        f(k, t);
-        if (t == 0xFFFFFFFFu) break;
+    ZHead h{0u, 0xFFFFFFFFu};
+    bool first = true;
+    for (int k = 0; k < kInvCap; ++k) {
+        if (k > 0) {
+            p = __dmul_rn(p, lam);
+            p = __ddiv_rn(p, (double)k);
+            Fk = __dadd_rn(Fk, p);
+        }
+        const int64_t t = threshold_dev(Fk);
+        if (t < 0) {
+            h.n0 = (uint32_t)k + 1u;
+            continue;
+        }
+        if (first) {
+            h.z0 = (uint32_t)t;
+            first = false;
+        }
+        f(k - (int)h.n0, (uint32_t)t);
+        if (t == 0xFFFFFFFFll) break;
     }
-    return z0;
+    return h;
 }
 
 // Transformed-rejection record of one Poisson mean (constants of the setup in FP64, stored FP32).
@@ -105,14 +121,15 @@ __device__ __forceinline__ PtrsRec ptrs_record(float lam_f, uint32_t i, const fl
     return r;
 }
 
-// Per point: class (0 none, 1 inversion, 2 transformed rejection), tail length, lambda.
+// Per point: class (0 none, 1 inversion, 2 transformed rejection), leading count n0, the first
+// two thresholds after it and the tail length.
 struct PointCls {
     int cls;
-    uint32_t z0, z1, tail;
+    uint32_t z0, z1, tail, n0;
 };
 
 __device__ __forceinline__ PointCls classify(const PointIn &p) {
-    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u};
     if (!p.valid || !(p.lam > 0.0f)) return c;
     if (p.lam >= kPtrsThreshold) {
         c.cls = 2;
@@ -120,18 +137,19 @@ __device__ __forceinline__ PointCls classify(const PointIn &p) {
     }
     bool sat = false;
     uint32_t z1 = 0xFFFFFFFFu, tail = 0u;
-    const uint32_t z0 = thresholds_dev(p.lam, [&](int k, uint32_t z) {
+    const ZHead zh = thresholds_dev(p.lam, [&](int k, uint32_t z) {
         if (k == 1) z1 = z;
         if (k >= 2 && !sat) {
             if (z == 0xFFFFFFFFu) sat = true;
             else ++tail;
         }
     });
-    if (z0 == 0xFFFFFFFFu) return c;
+    if (zh.n0 == 0u && zh.z0 == 0xFFFFFFFFu) return c;    // never a star
     c.cls = 1;
-    c.z0 = z0;
+    c.z0 = zh.z0;
     c.z1 = z1;
     c.tail = tail;
+    c.n0 = zh.n0;
     return c;
 }
 
@@ -147,7 +165,7 @@ __device__ __forceinline__ uint32_t group_scan(uint32_t v, int j, uint32_t &tota
     return s - v;
 }
 
-// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 10 (exact:
+// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 64 (exact:
 // lambda 2^40 is exact in FP64), 0 otherwise; a point is in the pool when L > 0.
 __device__ __forceinline__ uint64_t pool_weight(const PointIn &p) {
     if (!p.valid || !(p.lam > 0.0f) || !(p.lam < kPtrsThreshold)) return 0ull;
@@ -197,7 +215,7 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const PointIn p = g < a.G ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
     const PointCls c = classify(p);
     if (g < a.G)   // the write pass reads these instead of running the threshold series again
-        a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t] = make_uint4(c.z0, c.z1, c.tail, (uint32_t)c.cls);
+        a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t] = make_uint4(c.z0, c.z1, c.tail, (uint32_t)c.cls | (c.n0 << 8));
     uint32_t n_tail, n_ptrs;
     group_scan(c.cls == 1 ? c.tail : 0u, j, n_tail);
     group_scan(c.cls == 2 ? 1u : 0u, j, n_ptrs);
@@ -289,7 +307,7 @@ __device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t &total, ui
 }
 
 // Header of a total-count sampler region: pool size n, Lambda = (float)(Lfix 2^-40) (the FP64
-// conversion rounds to nearest), the draw of the total (inversion thresholds below 10, a
+// conversion rounds to nearest), the draw of the total (inversion thresholds below 64, a
 // transformed-rejection record at and above), and the fixed-point total itself.
 __device__ void write_pool_header(uint8_t *pr, uint32_t P, uint32_t n, uint64_t lfix) {
     *reinterpret_cast<uint64_t *>(pr + pool_fix_off(P)) = lfix;
@@ -297,12 +315,12 @@ __device__ void write_pool_header(uint8_t *pr, uint32_t P, uint32_t n, uint64_t 
     if (n > 0) {
         hdr.lam = __double2float_rn(__dmul_rn(__ull2double_rn(lfix), 1.0 / kPoolFix));
         if (hdr.lam < kPtrsThreshold) {
-            hdr.mode = 1u;
             uint32_t *z = reinterpret_cast<uint32_t *>(pr + kPoolZOff);
-            thresholds_dev(hdr.lam, [&](int k, uint32_t zk) {
+            const ZHead zh = thresholds_dev(hdr.lam, [&](int k, uint32_t zk) {
                 z[k] = zk;
                 hdr.n_z = (uint32_t)k + 1u;
             });
+            hdr.mode = 1u | (zh.n0 << 8);       // the total is n0 + #{k : x > z[k]}
         } else {
             hdr.mode = 2u;
             *reinterpret_cast<PtrsRec *>(pr + kPoolPtrsOff) = ptrs_record(hdr.lam, 0xFFFFFFFFu, nullptr, 0);
@@ -379,13 +397,14 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     uint32_t z0 = 0xFFFFFFFFu, z1 = 0xFFFFFFFFu, len = 0u;
     const bool inv = p.valid && p.lam > 0.0f && p.lam < kPtrsThreshold;
     // this lane's tail length first (for the in-group offsets), then the values
-    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u};
     if (inv) {   // as the count pass classified it
         const uint4 pc = a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t];
         c.z0 = pc.x;
         c.z1 = pc.y;
         c.tail = pc.z;
-        c.cls = (int)pc.w;
+        c.cls = (int)(pc.w & 0xFFu);
+        c.n0 = (pc.w >> 8) & 0xFFu;
     }
     uint32_t tot;
     const uint32_t my_tail = group_scan(c.cls == 1 ? c.tail : 0u, j, tot);
@@ -408,10 +427,12 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         });
     }
     if (in_range) {
-        uint32_t ks = (uint32_t)p.lam;
+        // the walk starts near the mean, in the shifted sequence Z'_k = Z_{n0 + k}
+        const uint32_t lk = (uint32_t)p.lam;
+        uint32_t ks = lk > c.n0 ? lk - c.n0 : 0u;
         if (ks > len + 1u) ks = len + 1u;
         if (ks < 2u) ks = 2u;
-        const uint4 sr = c.cls == 1 ? make_uint4(z0, z1, tail_off, len | (ks << 16))
+        const uint4 sr = c.cls == 1 ? make_uint4(z0, z1, tail_off, len | (c.n0 << 8) | (ks << 16))
                                     : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
         reinterpret_cast<uint4 *>(tab + L.slow_off[h])[(size_t)g * kGroup + j] = sr;
     }
@@ -477,7 +498,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     // inspection copies (parity export)
     if (a.insp_lam && p.valid && s == 0) {
         a.insp_lam[(size_t)h * a.P + p.i] = p.lam;
-        a.insp_z0[(size_t)h * a.P + p.i] = inv ? c.z0 : 0xFFFFFFFFu;
+        a.insp_z0[(size_t)h * a.P + p.i] = inv && c.n0 == 0u ? c.z0 : 0xFFFFFFFFu;
         if (h == 0)
             for (int b = 0; b < B; ++b) a.insp_flux[(size_t)p.i * B + b] = fl[b];
     }

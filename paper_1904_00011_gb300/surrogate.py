@@ -212,14 +212,24 @@ class Surrogate:
         u = rng.uniform(size=(n, 12))
         return self.box[:, 0] + u * (self.box[:, 1] - self.box[:, 0])
 
+    def param_matrix(self, theta: np.ndarray) -> np.ndarray:
+        """The parameter rows as the library's pcmd_params layout (float64 [n][MAX_SFH + 5]):
+        7 log SFH bins (offsets from the constant-SFR history), [Fe/H] mean and width, log
+        E(B-V), dust width, distance modulus."""
+        from . import PCMD_MAX_SFH
+        th = np.asarray(theta, np.float64)
+        m = np.zeros((th.shape[0], PCMD_MAX_SFH + 5))
+        m[:, :7] = np.asarray(self.base.params[0].log_sfh, np.float64)[None, :] + th[:, :7]
+        m[:, PCMD_MAX_SFH:] = th[:, 7:12]
+        return m
+
     def simulate(self, theta: np.ndarray, set_id0: Optional[int] = None):
         """Exact Hess diagrams [n][ny][nx] (int32 CUDA tensor) of the parameter rows."""
         n = len(theta)
-        w = workloads.surrogate_from_theta(theta, n_im=self.n_im, base=self.base)
         if set_id0 is None:
             set_id0 = self.set_counter
             self.set_counter += n
-        self.sim.simulate(w.params, [self.n_im] * n, set_id0)
+        self.sim.simulate(self.param_matrix(theta), [self.n_im] * n, set_id0)
         h, m, c, _ = self.sim.hess(n, [self.n_im] * n)
         return h, m
 
@@ -321,6 +331,30 @@ class Surrogate:
                         "ll_rel_err_median": float(np.median(np.abs(d) / np.abs(ll_e))),
                         "ll_spearman": float(_spearman(ll_s, ll_e))})
         return out
+
+
+    def scatter_calibration(self, d_mock, mock_moments, mock_n_pix: float, n_theta: int = 32,
+                            n_rep: int = 16, seed: int = 77) -> dict:
+        """The surrogate's likelihood error next to the exact simulator's own scatter (Appendix A:
+        the likelihood of one parameter point is itself stochastic).  For n_theta held-out points,
+        the exact likelihood at n_rep RNG set ids gives a mean and a standard deviation; the
+        surrogate's likelihood plus the held-out offset is compared with that mean.  Returns the
+        median over points of |surrogate + offset - exact mean| / exact scatter, and the parts."""
+        rng = np.random.default_rng(seed)
+        theta = self.sample_theta(n_theta, rng).astype(np.float32)
+        reps = np.repeat(theta, n_rep, axis=0)
+        ll = self.exact_loglike(reps, d_mock, mock_moments, mock_n_pix, set_id0=13 << 26)
+        ll = ll.reshape(n_theta, n_rep)
+        mean, sd = ll.mean(axis=1), ll.std(axis=1, ddof=1)
+        sur = self.loglike(theta, d_mock, mock_n_pix) + self.calib["offset"]
+        err = np.abs(sur - mean)
+        ratio = err / np.maximum(sd, 1e-12)
+        return {"n_theta": n_theta, "n_rep": n_rep,
+                "ll_err_over_exact_scatter": float(np.median(ratio)),
+                "ll_err_over_exact_scatter_p90": float(np.percentile(ratio, 90)),
+                "surrogate_abs_err_median": float(np.median(err)),
+                "exact_scatter_median": float(np.median(sd)),
+                "exact_ll_median": float(np.median(mean))}
 
 
 def _spearman(a, b):

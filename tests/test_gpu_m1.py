@@ -40,7 +40,8 @@ def test_m1_tables_match_oracle(mu):
     assert np.all(np.abs(flux.view(np.int32) - f32.view(np.int32)) <= 1)
     rng = np.random.default_rng(1)
     for h in range(2):
-        idx = np.nonzero((lam[h] > 0) & (lam[h] < 10))[0]
+        # below a mean of ~22 some word gives zero stars: Z_0 >= 0 is exported
+        idx = np.nonzero((lam[h] > 0) & (lam[h] < 22))[0]
         for i in rng.choice(idx, size=min(40, idx.size), replace=False):
             assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i])) == 0
             if z0[h, i] < 0xFFFFFFFF:

@@ -64,12 +64,18 @@ def test_tables_match_oracle(name):
     assert np.all(np.abs(flux.view(np.int32) - f32.view(np.int32)) <= 1)
     rng = np.random.default_rng(0)
     for h in range(2):
-        idx = np.nonzero((lam[h] > 0) & (lam[h] < 10))[0]
+        # below a mean of ~22 some word gives zero stars: Z_0 >= 0 is exported
+        idx = np.nonzero((lam[h] > 0) & (lam[h] < 22))[0]
         for i in rng.choice(idx, size=min(60, idx.size), replace=False):
             # z0 is the largest word with zero stars under the oracle's inversion
             assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i])) == 0
             if z0[h, i] < 0xFFFFFFFF:
                 assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i]) + 1) >= 1
+        # from ~22.9 to 64 even the smallest word gives a star (e^-lambda 2^32 < 1/2): no Z_0
+        big = np.nonzero((lam[h] > 22.9) & (lam[h] < 64))[0]
+        for i in big[:20]:
+            assert z0[h, i] == 0xFFFFFFFF
+            assert O.poisson_inversion(float(lam[h, i]), 0) >= 1
 
 
 # ------------------------------------------------------------------------------ counts
@@ -314,6 +320,37 @@ def test_nearly_empty_pixels_are_invalid():
     w = W.tiny(npix=1e-3)
     s, h, m, c, px, ref = _end_to_end(w)
     assert _u32(c)[0][1] == ref["counters"][1] and ref["counters"][1] > 4000
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_sampler_limit_is_latched_and_reported(fused):
+    """A transformed-rejection draw that reaches the attempt cap latches PCMD_ERR_SAMPLER_LIMIT in
+    the device error word; the next synchronising call returns it, and once the cap is restored
+    the same context evaluates normally and equals a fresh context.  fused: the graph-replayed
+    batched path (no PSF), else the image + PSF path."""
+    import paper_1904_00011_gb300 as P
+    w = W.large(n_im=64, log_npix=6.0)
+    if fused:
+        w = dataclasses.replace(w, psf=None)
+    s = _sim(w)
+    n = w.n_im
+    s.simulate(w.params, [n], 31)
+    h, m, _, _ = s.hess(1, [n])
+    torch.cuda.synchronize()
+    mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
+    ll0 = s.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=40)[0]
+    s.set_attempt_cap(1)           # about one draw in seven needs a second attempt
+    with pytest.raises(P.PcmdError) as e:
+        s.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=40)
+    assert e.value.code == 4       # PCMD_ERR_SAMPLER_LIMIT
+    s.set_attempt_cap(0)
+    ll1 = s.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=40)[0]
+    assert ll1 == ll0
+    fresh = _sim(w)
+    assert fresh.evaluate(w.params, [n], mock, mom, n * n, W.LL_PAPER, first_set_id=40)[0] == ll0
+    with pytest.raises(P.PcmdError) as e:
+        s.set_attempt_cap(1025)
+    assert e.value.code == 1
 
 
 def test_argument_and_state_errors():
