@@ -82,6 +82,7 @@ struct pcmd_ctx {
     uint32_t ptrs_cap = kPtrsMaxAttempts;   // transformed-rejection attempt cap of a draw
 
     SetDesc *desc_d = nullptr;  // the models' descriptors (inside tab_in, uploaded with it)
+    DevBuf btab;                // byte tables of the dense groups (allocated when needed)
     DevBuf tables, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
@@ -352,6 +353,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         }
         d.tail_off = tin[s].base + L.tail_off;
         d.flux_off = tin[s].base + L.flux_off;
+        for (int h = 0; h < 2; ++h)
+            d.btab_off[h] = ((uint64_t)s * 2u + (uint64_t)h) * ((P + kGroup - 1u) / kGroup) * kBtabGroupBytes;
         d.pool_on = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 1u : 0u;
         for (int h = 0; h < 2; ++h) d.pool_off[h] = tin[s].base + L.pool_off[h];
         // dust screen of this model (Section 2.2): E = 10^log_ebv exp(sigma z)
@@ -381,6 +384,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
     CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
+    if (needs_full) CK(ctx->btab.ensure((size_t)n_sets * 2 * G * kBtabGroupBytes));
     CK(ctx->tab_in.ensure(up_bytes));
     ctx->desc_d = reinterpret_cast<SetDesc *>(ctx->tab_in.as<uint8_t>() + desc_off);
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
@@ -400,6 +404,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     TabArgs ta;
     std::memset(&ta, 0, sizeof ta);
     ta.tables = ctx->tables.as<uint8_t>();
+    ta.btab = needs_full ? ctx->btab.as<uint8_t>() : nullptr;
     ta.desc = ctx->desc_d;
     ta.sets = ctx->tab_in.as<TabSetIn>();
     ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
@@ -437,6 +442,7 @@ static DrawArgs base_draw_args(pcmd_ctx *ctx) {
     DrawArgs a;
     std::memset(&a, 0, sizeof a);
     a.tables = ctx->tables.as<uint8_t>();
+    a.btab = ctx->btab.as<uint8_t>();
     a.desc = ctx->desc_d;
     a.items = ctx->items.as<uint2>();
     a.order = ctx->order.as<uint32_t>();
@@ -588,7 +594,7 @@ void pcmd_destroy(pcmd_ctx *ctx) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
-    DevBuf *bufs[] = {&ctx->ll_part, &ctx->ll_ticket, &ctx->tables, &ctx->items, &ctx->order, &ctx->partials,
+    DevBuf *bufs[] = {&ctx->ll_part, &ctx->ll_ticket, &ctx->tables, &ctx->btab, &ctx->items, &ctx->order, &ctx->partials,
                       &ctx->part_begin, &ctx->part_count, &ctx->image, &ctx->pix_off, &ctx->hess,
                       &ctx->moments, &ctx->counters, &ctx->ll, &ctx->psf_d, &ctx->queue, &ctx->err,
                       &ctx->imf_d, &ctx->bflux_d, &ctx->tab_in, &ctx->tab_scratch, &ctx->insp};
@@ -872,7 +878,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     std::memcpy(&mk[3], &npix, 8);
     const std::vector<size_t> key = {
         (size_t)n_sets, n_items, (size_t)grid, (size_t)mode, (size_t)ctx->block, (size_t)ctx->split,
-        (size_t)ctx->chunk, (size_t)ctx->ptrs_cap, (size_t)ctx->needs_full, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p,
+        (size_t)ctx->chunk, (size_t)ctx->ptrs_cap, (size_t)ctx->needs_full, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p, (size_t)ctx->btab.p,
         (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
         (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
         (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p,

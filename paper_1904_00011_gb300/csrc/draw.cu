@@ -195,6 +195,18 @@ __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint
     return n0 + k;
 }
 
+// n = #{k : x > Z_k} given a lower bound c <= n (the count at a smaller word): walks upwards from
+// k = c through the slot's shifted thresholds.
+__device__ __forceinline__ uint32_t count_up_from(uint32_t x, const uint4 &sr, const uint32_t *tail, uint32_t c) {
+    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
+    uint32_t k = c - n0;                            // c >= n0: every word exceeds the first n0
+    auto z = [&](uint32_t kk) -> uint32_t {
+        return kk == 0u ? sr.x : kk == 1u ? sr.y : (kk - 2u < len ? __ldg(tail + sr.z + (kk - 2u)) : 0xFFFFFFFFu);
+    };
+    while (x > z(k)) ++k;                           // z saturates at len + 2
+    return n0 + k;
+}
+
 // The warp's queued maybe-hits, resolved by all 32 lanes together.  Queue entry of a lane's
 // group with maybe-hits: g | prefix << 8 | hm << 16, g the group's index in the staged chunk,
 // hm its maybe-hit mask (bit 4q + k = byte q of HI word k = slot 4k + q), prefix the number of
@@ -361,8 +373,10 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
 }
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
-// the HI call and the four LO calls of the group are drawn up front and every slot walks its
-// thresholds directly.
+// the HI call and the four LO calls of the group are drawn up front.  Each slot's count starts
+// from its byte table: the count at the lower edge of the HI byte, final when it is the same for
+// the whole byte; otherwise the walk continues upwards through the slot's thresholds from there
+// (a word of the byte cannot have fewer stars than the byte's lower edge).
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -370,6 +384,7 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
     const uint32_t nd = ic.active ? d.n_dense[H] : 0u;
     if (nd == 0u) return;
     const uint8_t *base = a.tables + d.dense_off[H];
+    const uint8_t *btab = a.btab + d.btab_off[H];
     const PhiloxPrefix ph = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
     const PhiloxPrefix pl = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
     for (uint32_t q = (uint32_t)sidx; q < nd; q += (uint32_t)a.split) {
@@ -378,15 +393,26 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
         const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * (uint32_t)kGroup;
         const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+        const uint8_t *bt = btab + (size_t)q * kBtabGroupBytes;
 #pragma unroll 1
         for (uint32_t qd = 0; qd < 4u; ++qd) {
-            const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
-#pragma unroll 2
+            // the quad's four table entries first: their loads overlap the LO call
+            uint32_t e[4];
+#pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
                 const uint32_t j = 4u * qd + t;
-                const uint32_t x = (hi_byte(whi, j) << 24) | (word_of(wlo, t) >> 8);
-                const uint4 sr = __ldg(slow + j);
-                const uint32_t n = count_from_thresholds(x, sr, ic.tail);
+                e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
+            }
+            const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
+#pragma unroll
+            for (uint32_t t = 0; t < 4u; ++t) {
+                const uint32_t j = 4u * qd + t;
+                uint32_t n = e[t] & 0x7Fu;
+                if (!(e[t] & 0x80u)) {
+                    const uint32_t x = (hi_byte(whi, j) << 24) | (word_of(wlo, t) >> 8);
+                    const uint4 sr = __ldg(slow + j);
+                    n = count_up_from(x, sr, ic.tail, n);
+                }
                 if (n) {
                     float f[B];
 #pragma unroll

@@ -552,12 +552,55 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
     return L;
 }
 
+namespace {
+
+// n0 + (first k with x <= Z'_k): the count of word x from a slow record, by binary search over
+// the shifted thresholds (Z'_k saturated from len + 2 on).
+__device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, const uint32_t *tail) {
+    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
+    auto z = [&](uint32_t k) -> uint32_t {
+        return k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
+    };
+    uint32_t lo = 0u, hi = len + 2u;                 // z(hi) = 2^32 - 1 >= x
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (x <= z(mid)) hi = mid;
+        else lo = mid + 1u;
+    }
+    return n0 + lo;
+}
+
+// Byte tables of the dense groups: one CTA per (dense-list position, half, model), one thread per
+// (slot, byte) entry: count(b << 24) and whether count((b << 24) | 0xFFFFFF) is the same.
+__global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
+    const uint32_t q = blockIdx.x;
+    const int h = blockIdx.y, s = blockIdx.z;
+    const SetDesc &d = a.desc[s];
+    if (q >= d.n_dense[h]) return;
+    const uint32_t rec = group_rec_bytes(a.n_bands);
+    const uint32_t gid = *reinterpret_cast<const uint32_t *>(a.tables + d.dense_off[h] + (uint64_t)q * rec);
+    const uint4 *slow = reinterpret_cast<const uint4 *>(a.tables + d.slow_off[h]) + (uint64_t)gid * kGroup;
+    const uint32_t *tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
+    uint8_t *out = a.btab + d.btab_off[h] + (uint64_t)q * kBtabGroupBytes;
+    for (uint32_t e = threadIdx.x; e < kBtabGroupBytes; e += blockDim.x) {
+        const uint32_t j = e >> 8, b = e & 255u;
+        const uint4 sr = slow[j];
+        const uint32_t c0 = count_bsearch(b << 24, sr, tail);
+        const uint32_t c1 = count_bsearch((b << 24) | 0xFFFFFFu, sr, tail);
+        // counts below a mean of 64 stay below 128 (the CDF passes 1 - 2^-33 first)
+        out[e] = (uint8_t)((c0 & 0x7Fu) | (c0 == c1 ? 0x80u : 0u));
+    }
+}
+
+}  // namespace
+
 cudaError_t launch_build_tables(const TabArgs &a, int n_sets, cudaStream_t st) {
     if (a.G == 0 || n_sets < 1 || n_sets > 65535) return cudaErrorInvalidValue;
     const dim3 grid((a.G * kGroup + 255u) / 256u, 2, n_sets);
     tab_count_kernel<<<grid, 256, 0, st>>>(a);
     tab_scan_kernel<<<dim3(2, n_sets), 1024, 0, st>>>(a);
     tab_write_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.btab) tab_btab_kernel<<<dim3(a.G, 2, n_sets), 256, 0, st>>>(a);
     if (a.pool) {
         const uint32_t ng = (max(a.P, (1u << kPoolGuideBits) + 1) + 255) / 256;
         tab_pool_guide_kernel<<<dim3(ng, 2, n_sets), 256, 0, st>>>(a);
