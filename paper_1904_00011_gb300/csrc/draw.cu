@@ -394,6 +394,11 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * (uint32_t)kGroup;
         const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
         const uint8_t *bt = btab + (size_t)q * kBtabGroupBytes;
+        // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and
+        // the group total goes into the pixel's (compensated) accumulator once
+        float gs[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) gs[b] = 0.0f;
 #pragma unroll 1
         for (uint32_t qd = 0; qd < 4u; ++qd) {
             // the quad's four table entries first: their loads overlap the LO call
@@ -413,19 +418,17 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
                     const uint4 sr = __ldg(slow + j);
                     n = count_up_from(x, sr, ic.tail, n);
                 }
-                if (n) {
-                    float f[B];
+                const float nf = (float)n;
 #pragma unroll
-                    for (int b = 0; b < B; ++b) f[b] = __ldg(fl + j * B + b);
-                    acc.template add<H>((float)n, f);
-                    if (MODE == kModeCounts) {
-                        if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                            a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
-                                     gid * (uint32_t)kGroup + j] = n;
-                    }
+                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, __ldg(fl + j * B + b), gs[b]);
+                if (MODE == kModeCounts && n) {
+                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
+                                 gid * (uint32_t)kGroup + j] = n;
                 }
             }
         }
+        acc.template add_sum<H>(gs);
     }
 }
 
@@ -526,6 +529,12 @@ __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &i
     PtrsRec rec;
     if (q < n_rec) rec = load_ptrs(pr, q);
     uint4 w = make_uint4(0, 0, 0, 0);
+    // accepted draws' n f_b are summed with plain FMAs, 32 draws at a time, and each partial goes
+    // into the pixel's (compensated) accumulator
+    float ps[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) ps[b] = 0.0f;
+    uint32_t np = 0u;
     while (__any_sync(0xffffffffu, q < n_rec)) {
         if (q < n_rec) {
             if ((at & 1u) == 0u) w = ptrs_words(rec, ic.pix, ic.set, H, at, a.rk0, a.rk1);
@@ -533,7 +542,20 @@ __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &i
             bool done = t.status == 0;
             if (t.status == 2) done = ptrs_log_accept(rec, t);
             if (done) {
-                ptrs_resolved<B, KAHAN, MODE, H>(a, ic, rec, (uint32_t)t.kf, acc);
+                const uint32_t n = (uint32_t)t.kf;
+                const float nf = (float)n;
+#pragma unroll
+                for (int b = 0; b < B; ++b) ps[b] = fmaf(nf, rec.flux[b], ps[b]);
+                if (++np == 32u) {
+                    acc.template add_sum<H>(ps);
+#pragma unroll
+                    for (int b = 0; b < B; ++b) ps[b] = 0.0f;
+                    np = 0u;
+                }
+                if (MODE == kModeCounts && n) {
+                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
+                }
             } else if (++at >= a.ptrs_cap) {
                 atomicOr(a.err, kErrSampler);
                 done = true;
@@ -545,6 +567,7 @@ __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &i
             }
         }
     }
+    if (np) acc.template add_sum<H>(ps);
 }
 
 // Dust screen factors of one pixel: E(B-V) = 10^log_ebv exp(sigma z), z ~ N(0, 1) by
@@ -566,7 +589,7 @@ __device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uin
 // FULL: dense inversion groups, transformed-rejection points and the total-count sampler are
 // compiled in; without it the kernel handles launches whose models have sparse groups only.
 template <int B, bool KAHAN, int MODE, bool FULL>
-__global__ void __launch_bounds__(256) draw_kernel(const __grid_constant__ DrawArgs a) {
+__global__ void __launch_bounds__(256, FULL ? 2 : 1) draw_kernel(const __grid_constant__ DrawArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t rec = group_rec_bytes(B);
     const uint32_t chunk = (uint32_t)a.chunk;
