@@ -545,7 +545,12 @@ def run_npix_range(P, W, torch) -> dict:
     return out
 
 
-def run_surrogate(torch, n_sims: int = 1 << 20, infer_batch: int = 4096, reps: int = 10):
+# Inference batch of the surrogate lines: 96 rows per SM, i.e. three 128-row tiles per SM on the
+# 1024-wide layers and whole waves of tiles on every layer (152 SMs).
+INFER_BATCH = 152 * 96
+
+
+def run_surrogate(torch, n_sims: int = 1 << 20, infer_batch: int = INFER_BATCH, reps: int = 10):
     """Surrogate: train on fresh simulations, report held-out accuracy against the exact
     simulator, inference throughput (tensor-core GEMMs) and the nested-sampling pre-screen gain."""
     from paper_1904_00011_gb300.surrogate import Surrogate
@@ -627,12 +632,17 @@ def run_lmax(P, W, torch, reps: int = 100):
     mock, mom = h[0].clone(), m[0].cpu().numpy().copy()
     p = w.params[0]
     sim.evaluate([p] * reps, [n] * reps, mock, mom, n * n, W.LL_PAPER, first_set_id=10)
+    torch.cuda.synchronize()
+    sim.profile(True)
     t0 = time.perf_counter()
     ll = sim.evaluate([p] * reps, [n] * reps, mock, mom, n * n, W.LL_PAPER, first_set_id=1000)
     dt = time.perf_counter() - t0
+    kt = sim.kernel_times()
+    sim.profile(False)
     return {"workload": "full model 256x256, best fit recomputed %d times in one batched call "
                         "(Appendix A ceiling)" % reps,
             "ms": 1e3 * dt, "evals_per_s": reps / dt, "model_pixels_per_s": reps * n * n / dt,
+            "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]},
             "l_max": S.lmax_from_repeats(ll), "ll_std": float(np.std(ll)),
             "ll_min": float(np.min(ll)), "ll_max": float(np.max(ll))}
 
@@ -694,7 +704,7 @@ def run_pool(P, W, torch, reps: int = 20):
             "launch": {k: tuned[k] for k in ("block", "split", "chunk")}}
 
 
-def run_mlp(torch, batch: int = 4096, reps: int = 20):
+def run_mlp(torch, batch: int = INFER_BATCH, reps: int = 20):
     """Surrogate network alone (random init, no training): the 5-layer inference forward and the
     fused forward + likelihood on a batch of parameter points; GEMM roofline."""
     from paper_1904_00011_gb300.surrogate import Mlp

@@ -496,12 +496,14 @@ static uint32_t or_pool_pick(const or_pool *pl, uint32_t u)
 }
 
 /* Number of pool stars of (pixel, half): inversion on word 0 of Philox(p, 2^32 - 1, set, LO|h)
- * below 64, transformed rejection with point index 2^32 - 1 at and above. */
+ * below 10, transformed rejection with point index 2^32 - 1 at and above (the total has its own
+ * boundary: one draw per pixel and half). */
+#define OR_POOL_TOTAL_LIMIT 10.0f
 static uint32_t or_pool_total(const or_pool *pl, uint64_t seed, uint32_t pix, uint32_t set, uint32_t half,
                               int *err)
 {
     if (pl->n == 0) return 0u;
-    if (pl->lam < OR_INV_LIMIT) {
+    if (pl->lam < OR_POOL_TOTAL_LIMIT) {
         uint32_t w[4];
         or_call(seed, pix, 0xFFFFFFFFu, set, or_tag(OR_KIND_LO, half, 0), w);
         return or_poisson_inversion(pl->lam, w[0]);

@@ -18,9 +18,9 @@ CACHE = os.environ.get("PCMD_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json"))
 
 DEFAULT_CANDIDATES: List[Tuple[int, int, int]] = [
-    (256, 4, 64), (256, 4, 128), (256, 2, 64), (256, 2, 128), (256, 8, 64), (256, 1, 64),
-    (128, 2, 64), (128, 4, 64), (128, 1, 128), (256, 4, 32), (256, 8, 128), (128, 2, 128),
-    (256, 2, 32), (256, 1, 32),
+    (256, 4, 64), (256, 4, 128), (256, 4, 256), (256, 2, 64), (256, 2, 128), (256, 8, 64),
+    (256, 8, 256), (256, 1, 64), (128, 2, 64), (128, 4, 64), (128, 1, 128), (256, 4, 32),
+    (256, 8, 128), (128, 2, 128), (256, 2, 32), (256, 1, 32),
 ]
 
 

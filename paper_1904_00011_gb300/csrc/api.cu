@@ -78,7 +78,7 @@ struct pcmd_ctx {
     cudaStream_t st = nullptr;
     cudaStream_t cap_st = nullptr;
     int device = 0, n_sm = 1;
-    int block = 256, split = 4, chunk = 64;
+    int block = 256, split = 4, chunk = 256;   // launch shape (pcmd_set_launch; autotuned)
     uint32_t ptrs_cap = kPtrsMaxAttempts;   // transformed-rejection attempt cap of a draw
 
     SetDesc *desc_d = nullptr;  // the models' descriptors (inside tab_in, uploaded with it)

@@ -167,6 +167,7 @@ struct ItemCtx {
     bool active;
     const SlowRec *slow[2];
     const uint32_t *tail;
+    const float *flux;      // [P][B] electrons per star of every point
 };
 
 constexpr int kQueueCap = 16;   // hit-queue entries per thread (shared memory)
@@ -222,7 +223,7 @@ template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void drain_warp(const DrawArgs &a, const ItemCtx &ic, const PhiloxPrefix &pf,
                                            const uint8_t *cb, uint32_t *queue, int qn,
                                            Acc<B, KAHAN> &acc) {
-    constexpr uint32_t rec = group_rec_bytes(B);
+    constexpr uint32_t rec = kSparseRecBytes;
     const uint32_t lane = threadIdx.x & 31u, wbase = threadIdx.x & ~31u, bd = blockDim.x;
     uint32_t nb = 0;
     for (int e = 0; e < qn; ++e) {
@@ -296,10 +297,10 @@ __device__ __forceinline__ void drain_warp(const DrawArgs &a, const ItemCtx &ic,
                     a.counts[((size_t)(opix - a.count_pix0) * 2u + H) * a.n_points + i] = n;
             }
             if (n) {
-                const float *f = reinterpret_cast<const float *>(rp + kRecFlux) + j * B;
+                const float *f = ic.flux + (size_t)i * B;
                 const float nf = (float)n;
 #pragma unroll
-                for (int b = 0; b < B; ++b) c[b] = __fmul_rn(nf, f[b]);
+                for (int b = 0; b < B; ++b) c[b] = __fmul_rn(nf, __ldg(f + b));
             }
         }
         // segmented inclusive scan over the list positions of one owner (owners ascend with v)
@@ -338,7 +339,7 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
                                               const PhiloxPrefix &pf, const uint8_t *cb,
                                               uint32_t cnt, int sidx, uint32_t *queue,
                                               Acc<B, KAHAN> &acc) {
-    constexpr uint32_t rec = group_rec_bytes(B);
+    constexpr uint32_t rec = kSparseRecBytes;
     uint32_t *myq = queue + threadIdx.x;
     const uint32_t bd = blockDim.x;
     // a lane queues at most one entry per group: with no more groups per lane than queue slots
@@ -457,7 +458,7 @@ __device__ __forceinline__ void ptrs_resolved(const DrawArgs &a, const ItemCtx &
 // Total-count sampler of half H (the Section 2.1 footnote's additivity of Poisson counts, used
 // in reverse: a Poisson total split over the points by their weights gives independent Poisson
 // counts): N ~ Poisson(Lambda) from word 0 of Philox(p, 2^32 - 1, set, LO|H)
-// by inversion (Lambda < 64) or by transformed rejection with point index 2^32 - 1; star s takes
+// by inversion (Lambda < 10) or by transformed rejection with point index 2^32 - 1; star s takes
 // word s & 3 of Philox(p, 2^31 | s >> 2, set, HI|H) and goes to the first pool entry with
 // u < T_j (the last takes the rest): the top 14 bits of u select a guide bucket, a binary
 // search inside it finds the entry (bounded, so no lane walks a long run of tiny weights).
@@ -589,9 +590,9 @@ __device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uin
 // FULL: dense inversion groups, transformed-rejection points and the total-count sampler are
 // compiled in; without it the kernel handles launches whose models have sparse groups only.
 template <int B, bool KAHAN, int MODE, bool FULL>
-__global__ void __launch_bounds__(256, FULL ? 2 : 1) draw_kernel(const __grid_constant__ DrawArgs a) {
+__global__ void __launch_bounds__(256, FULL ? 2 : 3) draw_kernel(const __grid_constant__ DrawArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    constexpr uint32_t rec = group_rec_bytes(B);
+    constexpr uint32_t rec = kSparseRecBytes;   // staged sparse group records
     const uint32_t chunk = (uint32_t)a.chunk;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     volatile uint32_t *s_item = reinterpret_cast<volatile uint32_t *>(smem + 16);
@@ -643,6 +644,7 @@ __global__ void __launch_bounds__(256, FULL ? 2 : 1) draw_kernel(const __grid_co
         ic.slow[0] = reinterpret_cast<const SlowRec *>(a.tables + d.slow_off[0]);
         ic.slow[1] = reinterpret_cast<const SlowRec *>(a.tables + d.slow_off[1]);
         ic.tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
+        ic.flux = reinterpret_cast<const float *>(a.tables + d.flux_off);
         Acc<B, KAHAN> acc;
         acc.init();
 
@@ -840,7 +842,7 @@ __global__ void __launch_bounds__(256, FULL ? 2 : 1) draw_kernel(const __grid_co
 }
 
 size_t draw_smem_bytes(int nb, int chunk, int block, int split, int mode, int nx, int ny) {
-    size_t s = 32 + chunk_region_bytes((uint32_t)chunk, group_rec_bytes(nb)) +
+    size_t s = 32 + chunk_region_bytes((uint32_t)chunk, kSparseRecBytes) +
                (size_t)kQueueCap * block * 4 +
                (size_t)block * 2 * nb * 4;
     if (mode == kModeFused) {

@@ -10,6 +10,10 @@ constexpr int kGroup = 16;                // isochrone points per HI call (one b
 constexpr float kPtrsThreshold = 64.0f;   // inversion below, transformed rejection at/above
 constexpr int kInvCap = 128;              // inversion counts are capped at 128 (P(n > 128) < 2^-40
                                           // for every lambda below 64)
+// The total-count sampler draws its per-pixel total by inversion only below 10: a single draw
+// per pixel and half would otherwise need one serial FP64 threshold series of up to ~120 terms
+// per model and a walk of up to ~60 thresholds per pixel.
+constexpr float kPoolTotalLimit = 10.0f;
 constexpr float kDenseLam = 0.3f;         // groups with a slot at or above this are "dense"
 constexpr uint32_t kPtrsMaxAttempts = 1024u;
 
@@ -32,6 +36,9 @@ enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
 // byte compares against z7 / zh.
 __host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 64u * (uint32_t)nb; }
 constexpr uint32_t kRecZ7 = 16, kRecZh = 32, kRecZc1 = 48, kRecFlux = 64;
+// The sparse list (streamed through shared memory) keeps only the first 64 bytes of a record:
+// its drain reads a hit's fluxes from the per-point flux table instead.
+constexpr uint32_t kSparseRecBytes = 64;
 
 // Slow-path record per point and half (global memory): full 32-bit thresholds.
 // The first n0 thresholds of a mean above ~22 are -1 (e^-lambda 2^32 < 1/2: every word exceeds
@@ -87,7 +94,7 @@ struct __align__(16) PoolHdr {
     float lam;              // (float) Lambda
     uint32_t n;             // pool size
     uint32_t n_z;           // thresholds of the total (mode 1)
-    uint32_t mode;          // bits 0-7: 0 empty, 1 inversion (Lambda < 64), 2 transformed
+    uint32_t mode;          // bits 0-7: 0 empty, 1 inversion (Lambda < 10), 2 transformed
                             // rejection; bits 8-15 (inversion): leading thresholds of -1, n0
 };
 constexpr uint32_t kPoolZOff = 16, kPoolPtrsOff = kPoolZOff + 4 * kInvCap, kPoolGuideOff = kPoolPtrsOff + 48;

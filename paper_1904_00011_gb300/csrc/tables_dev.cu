@@ -307,14 +307,14 @@ __device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t &total, ui
 }
 
 // Header of a total-count sampler region: pool size n, Lambda = (float)(Lfix 2^-40) (the FP64
-// conversion rounds to nearest), the draw of the total (inversion thresholds below 64, a
+// conversion rounds to nearest), the draw of the total (inversion thresholds below 10, a
 // transformed-rejection record at and above), and the fixed-point total itself.
 __device__ void write_pool_header(uint8_t *pr, uint32_t P, uint32_t n, uint64_t lfix) {
     *reinterpret_cast<uint64_t *>(pr + pool_fix_off(P)) = lfix;
     PoolHdr hdr{0.0f, n, 0u, 0u};
     if (n > 0) {
         hdr.lam = __double2float_rn(__dmul_rn(__ull2double_rn(lfix), 1.0 / kPoolFix));
-        if (hdr.lam < kPtrsThreshold) {
+        if (hdr.lam < kPoolTotalLimit) {
             uint32_t *z = reinterpret_cast<uint32_t *>(pr + kPoolZOff);
             const ZHead zh = thresholds_dev(hdr.lam, [&](int k, uint32_t zk) {
                 z[k] = zk;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
 
     // group record (every lane writes its slot; lane 0 the header)
     if (in_range && sc.x != 0u) {
-        const uint32_t rec = group_rec_bytes(B);
+        const uint32_t rec = sc.x == 2u ? group_rec_bytes(B) : kSparseRecBytes;
         uint8_t *r = tab + (sc.x == 2u ? L.dense_off[h] : L.grp_off[h]) + (size_t)sc.y * rec;
         const uint32_t zc0 = c.cls == 1 ? (z0 >> 24) : 0xFFu;
         const uint32_t zc1 = c.cls == 1 ? (z1 >> 24) : 0xFFu;
@@ -466,8 +466,10 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         r[kRecZ7 + j] = (uint8_t)(zc0 & 0x7Fu);
         r[kRecZh + j] = (uint8_t)(zc0 & 0x80u);
         r[kRecZc1 + j] = (uint8_t)zc1;
-        float *f = reinterpret_cast<float *>(r + kRecFlux) + j * B;
-        for (int b = 0; b < B; ++b) f[b] = fl[b];
+        if (sc.x == 2u) {   // dense records carry their fluxes (sparse ones use the flux table)
+            float *f = reinterpret_cast<float *>(r + kRecFlux) + j * B;
+            for (int b = 0; b < B; ++b) f[b] = fl[b];
+        }
     }
 
     // total-count sampler: this point's pool entry (point index, star-assignment threshold)
@@ -540,7 +542,7 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
         return o;
     };
     for (int h = 0; h < 2; ++h) {
-        L.grp_off[h] = place(G * rec);
+        L.grp_off[h] = place(G * kSparseRecBytes);
         L.dense_off[h] = place(G * rec);
         L.slow_off[h] = place((uint64_t)G * kGroup * sizeof(SlowRec));
         L.ptrs_off[h] = place((uint64_t)P * sizeof(PtrsRec));
