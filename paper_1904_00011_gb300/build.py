@@ -15,10 +15,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["api.cu", "draw.cu", "hess.cu", "loglike.cu", "noalloc.cu", "mlp.cu", "mlp_gemm.cu",
+CU_SOURCES = ["api.cu", "draw.cu", "draw_full.cu", "hess.cu", "loglike.cu", "noalloc.cu", "mlp.cu", "mlp_gemm.cu",
               "tables_dev.cu"]  # missing ones skipped
 CPP_SOURCES = ["tables.cpp"]
-HEADERS = ["common.cuh", "pcmd_internal.h", "tables.h", "tables_dev.h", "mlp_internal.h"]
+HEADERS = ["common.cuh", "draw_kernel.cuh", "pcmd_internal.h", "tables.h", "tables_dev.h", "mlp_internal.h"]
 
 
 def _newest_input() -> float:

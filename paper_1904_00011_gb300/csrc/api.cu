@@ -14,7 +14,6 @@
 #include "tables_dev.h"
 
 namespace pcmd {
-int draw_max_blocks_per_sm(int nb, bool kahan, int mode, bool full, int block, size_t smem);
 }
 
 using namespace pcmd;
@@ -97,7 +96,7 @@ struct pcmd_ctx {
     std::vector<uint32_t> order_list;
 
     int n_sets = 0;
-    bool needs_full = true;     // a staged model may have dense or transformed-rejection points
+    int draw_paths = kPathDense;    // draw paths the staged models can need (kPath* bits)
     std::vector<int> n_im;
     float *img_ptr = nullptr;
     bool have_images = false, have_hess = false;
@@ -308,7 +307,8 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::vector<double> mdf;
     uint64_t img_off = 0;
     uint32_t m1_i = 0;
-    bool needs_full = (ctx->cfg.flags & PCMD_FLAG_POOL) != 0;
+    const bool pool = (ctx->cfg.flags & PCMD_FLAG_POOL) != 0;
+    bool any_dense = false, any_ptrs = false;
     for (int s = 0; s < n_sets; ++s) {
         tin[s].m1_k = m1_k[s];
         tin[s].m1_off = 0;
@@ -337,7 +337,9 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
                     }
                     bound = std::max(bound, w[j * m.n_feh + k] * im);
                 }
-            if (bound * std::max(hf[0], hf[1]) >= 0.999 * (double)kDenseLam) needs_full = true;
+            const double top = bound * std::max(hf[0], hf[1]);
+            if (top >= 0.999 * (double)kDenseLam) any_dense = true;
+            if (top >= 0.999 * (double)kPtrsThreshold) any_ptrs = true;
         }
         tin[s].base = (uint64_t)s * L.bytes;
         tin[s].flux_factor = std::pow(10.0, -0.4 * p[s].dmod);
@@ -384,7 +386,11 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     CK(ctx->h_items.ensure(sizeof(uint2) * n_items));
     CK(ctx->h_order.ensure(sizeof(uint32_t) * n_items));
     CK(ctx->tables.ensure(L.bytes * (size_t)n_sets));
-    if (needs_full) CK(ctx->btab.ensure((size_t)n_sets * 2 * G * kBtabGroupBytes));
+    // the total-count sampler replaces the inversion groups (no dense groups to draw); points at or
+    // above the rejection boundary keep their own draws either way
+    const int draw_paths = pool ? (kPathPool | (any_ptrs ? kPathDense : 0)) : (any_dense ? kPathDense : kPathSparse);
+    const bool need_btab = !pool && any_dense;
+    if (need_btab) CK(ctx->btab.ensure((size_t)n_sets * 2 * G * kBtabGroupBytes));
     CK(ctx->tab_in.ensure(up_bytes));
     ctx->desc_d = reinterpret_cast<SetDesc *>(ctx->tab_in.as<uint8_t>() + desc_off);
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
@@ -404,7 +410,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     TabArgs ta;
     std::memset(&ta, 0, sizeof ta);
     ta.tables = ctx->tables.as<uint8_t>();
-    ta.btab = needs_full ? ctx->btab.as<uint8_t>() : nullptr;
+    ta.btab = need_btab ? ctx->btab.as<uint8_t>() : nullptr;
     ta.desc = ctx->desc_d;
     ta.sets = ctx->tab_in.as<TabSetIn>();
     ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
@@ -433,7 +439,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         t.done(ctx->st);
     }
     ctx->n_sets = n_sets;
-    ctx->needs_full = needs_full;
+    ctx->draw_paths = draw_paths;
     ctx->n_im.assign(n_im, n_im + n_sets);
     return PCMD_OK;
 }
@@ -467,13 +473,13 @@ static pcmd_status launch_draw_mode(pcmd_ctx *ctx, DrawArgs &a, int mode) {
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, mode, ctx->cfg.hess_nx,
                                         ctx->cfg.hess_ny);
-    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->needs_full, ctx->block, smem);
+    int per_sm = draw_max_blocks_per_sm(B, kahan, mode, ctx->draw_paths, ctx->block, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = std::min<int>((int)a.n_items, per_sm * ctx->n_sm);
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->st));
     KTimer t(ctx, PCMD_K_DRAW, ctx->st);
-    CK(launch_draw(a, B, kahan, mode, ctx->needs_full, grid, ctx->block, smem, ctx->st));
+    CK(launch_draw(a, B, kahan, mode, ctx->draw_paths, grid, ctx->block, smem, ctx->st));
     t.done(ctx->st);
     return PCMD_OK;
 }
@@ -869,7 +875,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     const bool kahan = (ctx->cfg.flags & PCMD_FLAG_KAHAN) != 0;
     const size_t smem = draw_smem_bytes(B, ctx->chunk, ctx->block, ctx->split, kModeFused,
                                         ctx->cfg.hess_nx, ctx->cfg.hess_ny);
-    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->needs_full, ctx->block, smem));
+    int per_sm = std::max(1, draw_max_blocks_per_sm(B, kahan, kModeFused, ctx->draw_paths, ctx->block, smem));
     const int grid = std::max(1, std::min<int>((int)n_items, per_sm * ctx->n_sm));
     uint64_t mk[4];
     std::memcpy(&mk[0], &mom[0], 8);
@@ -878,7 +884,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
     std::memcpy(&mk[3], &npix, 8);
     const std::vector<size_t> key = {
         (size_t)n_sets, n_items, (size_t)grid, (size_t)mode, (size_t)ctx->block, (size_t)ctx->split,
-        (size_t)ctx->chunk, (size_t)ctx->ptrs_cap, (size_t)ctx->needs_full, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p, (size_t)ctx->btab.p,
+        (size_t)ctx->chunk, (size_t)ctx->ptrs_cap, (size_t)ctx->draw_paths, mk[0], mk[1], mk[2], mk[3], (size_t)d_mock, (size_t)ctx->tables.p, (size_t)ctx->btab.p,
         (size_t)ctx->desc_d, (size_t)ctx->items.p, (size_t)ctx->order.p, (size_t)ctx->queue.p,
         (size_t)ctx->err.p, (size_t)ctx->hess.p, (size_t)ctx->counters.p, (size_t)ctx->partials.p,
         (size_t)ctx->part_begin.p, (size_t)ctx->part_count.p, (size_t)ctx->moments.p, (size_t)ctx->ll.p,
@@ -900,7 +906,7 @@ static pcmd_status evaluate_fused(pcmd_ctx *ctx, int n_sets, const uint32_t *d_m
         cudaMemsetAsync(ctx->hess.p, 0, sizeof(uint32_t) * nbins * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->counters.p, 0, sizeof(uint32_t) * 2 * n_sets, ctx->cap_st);
         cudaMemsetAsync(ctx->queue.p, 0, sizeof(uint32_t), ctx->cap_st);
-        launch_draw(a, B, kahan, kModeFused, ctx->needs_full, grid, ctx->block, smem, ctx->cap_st);
+        launch_draw(a, B, kahan, kModeFused, ctx->draw_paths, grid, ctx->block, smem, ctx->cap_st);
         launch_moments_finalize(ctx->partials.as<double>(), ctx->part_begin.as<uint32_t>(),
                                 ctx->part_count.as<uint32_t>(), n_sets, ctx->moments.as<double>(),
                                 ctx->cap_st);

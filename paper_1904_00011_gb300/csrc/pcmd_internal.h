@@ -160,11 +160,15 @@ struct HessArgs {
     PixelConsts pc;
 };
 
+// Draw paths compiled into a draw kernel instantiation besides the sparse inversion groups:
+// dense groups + transformed rejection, and the total-count sampler (which replaces the inversion
+// groups).  The host launches the smallest set the staged models can need.
+enum { kPathSparse = 0, kPathDense = 1, kPathPool = 2 };
+
 // launchers (implemented in the .cu files)
-// full: the models may have dense inversion groups, transformed-rejection points or the
-// total-count sampler; otherwise the kernel only streams sparse inversion groups
-cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, bool full, int grid,
+cudaError_t launch_draw(const DrawArgs &a, int n_bands, bool kahan, int mode, int paths, int grid,
                         int block, size_t smem, cudaStream_t st);
+int draw_max_blocks_per_sm(int nb, bool kahan, int mode, int paths, int block, size_t smem);
 size_t draw_smem_bytes(int n_bands, int chunk, int block, int split, int mode, int nx, int ny);
 enum { kModeImage = 0, kModeCounts = 1, kModeFused = 2 };
 
