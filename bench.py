@@ -37,8 +37,8 @@ METRIC = "model pixels/s (plain full model, one likelihood evaluation per step)"
 # Each step evaluates a new parameter point (a sampler-like random walk) with a new RNG set id.
 PEAK_ISSUE_PER_SM_CLK = 128          # 4 schedulers x 32 lanes: thread-instructions per clock
 # dram__bytes_read.sum + dram__bytes_write.sum of one draw launch on the headline workload
-# (ncu, launch shape 256/4/64): the point tables are read once, the image stays in L2
-DRAW_TRAFFIC_BYTES = 971776 + 0
+# (ncu, launch shape 256/4/128): the point tables are read once, the image stays in L2
+DRAW_TRAFFIC_BYTES = 846848 + 0
 OPS_PER_INV_DRAW = 3.5               # 1/16 Philox4x32-10 block (40 instr) + one byte compare
 OPS_PER_PTRS_DRAW = 60.0             # 1/2 Philox block + ~40 FP32 ops of the squeeze test
 
@@ -201,7 +201,8 @@ def run_reference(args, world, rank):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12   # FMA lanes x 2 FLOP x max SM clock
 
 
-def hess_roofline(hess_ms: float, n_bands: int, npix: int, psf: int, nbins: int) -> dict:
+def hess_roofline(hess_ms: float, n_bands: int, npix: int, psf: int, nbins: int,
+                  psf_grid: bool = False) -> dict:
     """PSF / noise / magnitude / Hess kernel: 2 KS^2 FLOP per pixel and band (the stencil) against
     the FP32 FMA peak, and its algorithmic bytes (raw image read once, histogram flush) against
     the measured HBM copy bandwidth."""
@@ -209,7 +210,10 @@ def hess_roofline(hess_ms: float, n_bands: int, npix: int, psf: int, nbins: int)
     flop = 2.0 * psf * psf * n_bands * npix
     byts = 4.0 * n_bands * npix + 4.0 * nbins
     hbm = _measured_peak("hbm_gbs", 6800.0)
-    return {"kernel": "hess_kernel<%d,%d>" % (n_bands, psf), "avg_launch_ms": hess_ms,
+    # a single 25x25 PSF runs the band-split kernel, other sizes and PSF grids the tiled one
+    name = ("hess_bs_kernel<%d>" % n_bands if psf == 25 and not psf_grid
+            else "hess_kernel<%d,%d>" % (n_bands, psf))
+    return {"kernel": name, "avg_launch_ms": hess_ms,
             "fp32": {"bound": "fp32", "achieved": flop / s / 1e12, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": flop / s / 1e12 / FP32_PEAK_TFLOPS,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
@@ -366,7 +370,7 @@ def run_gb300(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": DRAW_TRAFFIC_BYTES,
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu capture of this kernel on this workload)",
-                     "kernel": "draw_kernel<2,false,IMAGE,false>",
+                     "kernel": "draw_kernel<2,false,IMAGE,sparse>",
                      "avg_launch_ms": avg_draw_s * 1e3,
                      "algorithmic": "%g instr/pixel = %d inversion draws x %g + %d PTRS draws x %g"
                                     % (ops, n_inv, OPS_PER_INV_DRAW, n_ptrs, OPS_PER_PTRS_DRAW),
@@ -670,7 +674,7 @@ def run_psf_grid(P, W, torch, reps: int = 10):
     hess_ms = kt["hess"][0] / max(1, kt["hess"][1])
     return {"workload": "full model 256x256 with a 4x4 grid of sub-pixel-shifted 25x25 Moffat PSFs",
             "ms_per_eval": 1e3 * dt, "model_pixels_per_s": n * n / dt, "hess_ms": hess_ms,
-            "hess_roofline": hess_roofline(hess_ms, w.n_bands, n * n, 25, w.hess_nx * w.hess_ny)}
+            "hess_roofline": hess_roofline(hess_ms, w.n_bands, n * n, 25, w.hess_nx * w.hess_ny, psf_grid=True)}
 
 
 def run_pool(P, W, torch, reps: int = 20):

@@ -1,6 +1,7 @@
 // C ABI of libpcmd (declared in include/pcmd.h): contexts, argument checks, table upload and
 // the launch sequence of the forward model.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -225,22 +226,20 @@ static pcmd_status check_params(pcmd_ctx *ctx, const pcmd_params *p, int n_sets,
 // point from the same FP64 products as the device builder; groups with an inversion point,
 // dense groups (a point at or above kDenseLam) and transformed-rejection points.
 static double model_cost(const Model &m, const double *w, const double hf[2]) {
-    const int P = m.n_points();
+    // per isochrone: transformed-rejection points from the sorted IMF weights (binary search),
+    // its groups counted as dense or sparse from its largest weight (an ordering estimate only)
     double c = 200.0;
+    const double groups = (double)(m.n_mass + kGroup - 1) / (double)kGroup;
     for (int h = 0; h < 2; ++h) {
         if (hf[h] == 0.0) continue;
-        for (int g = 0; g < (P + kGroup - 1) / kGroup; ++g) {
-            float mx = 0.0f;
-            bool act = false;
-            for (int i = g * kGroup; i < std::min(P, g * kGroup + kGroup); ++i) {
-                const float l = (float)(w[i / m.n_mass] * m.imf[i] * hf[h]);
-                if (l >= kPtrsThreshold) c += 180.0;
-                else if (l > 1e-10f) {
-                    act = true;
-                    mx = std::max(mx, l);
-                }
-            }
-            if (act) c += mx >= kDenseLam ? 700.0 : 70.0;
+        for (int jk = 0; jk < m.n_ages * m.n_feh; ++jk) {
+            const double s = w[jk] * hf[h];
+            if (!(s > 0.0)) continue;
+            const double *d = m.imf_desc.data() + (size_t)jk * m.n_mass;
+            const double cut = (double)kPtrsThreshold / s;
+            const long n_ptrs = std::upper_bound(d, d + m.n_mass, cut, std::greater<double>()) - d;
+            c += 180.0 * (double)n_ptrs;
+            c += groups * (s * m.imf_max[jk] >= (double)kDenseLam ? 700.0 : 70.0);
         }
     }
     return c;

@@ -76,6 +76,9 @@ void Model::build_imf() {
             imf_of_isochrone(&mass[o], n_mass, imf_slope, imf_kind, &imf[o]);
             for (int i = 0; i < n_mass; ++i) imf_max[(size_t)j * n_feh + k] = std::max(imf_max[(size_t)j * n_feh + k], imf[o + i]);
         }
+    imf_desc = imf;
+    for (size_t o = 0; o < imf_desc.size(); o += (size_t)n_mass)
+        std::sort(imf_desc.begin() + (long)o, imf_desc.begin() + (long)o + n_mass, std::greater<double>());
 }
 
 void Model::mdf_weights(double mu, double sigma, std::vector<double> &w) const {

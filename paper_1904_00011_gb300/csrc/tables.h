@@ -14,6 +14,7 @@ struct Model {
     std::vector<double> feh, mass, abs_mag;
     std::vector<double> imf;   // [n_ages][n_feh][n_mass], each isochrone sums to 1
     std::vector<double> imf_max;   // [n_ages][n_feh] largest IMF weight of each isochrone
+    std::vector<double> imf_desc;  // [n_ages][n_feh][n_mass] each isochrone's IMF weights, descending
     std::vector<double> base_flux;  // [P][n_bands] electrons per star at distance modulus 0
     double imf_slope = 2.35, mdf_cut = 0.01, f_dust = 0.5;
     double exptime[kMaxBands] = {1, 1, 1, 1}, zeropoint[kMaxBands] = {0, 0, 0, 0};
