@@ -594,7 +594,7 @@ __device__ __forceinline__ void dust_factors(const SetDesc &d, uint32_t pix, uin
 // groups and transformed-rejection points), kPathPool (the total-count sampler in place of the
 // inversion groups), or both.  The host picks the smallest set its models can need.
 template <int B, bool KAHAN, int MODE, int PATHS>
-__global__ void __launch_bounds__(256, (PATHS & kPathDense) ? 2 : 3) draw_kernel(const __grid_constant__ DrawArgs a) {
+__global__ void __launch_bounds__(256, (PATHS & kPathDense) ? 2 : ((PATHS & kPathPool) ? 4 : 3)) draw_kernel(const __grid_constant__ DrawArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t rec = kSparseRecBytes;   // staged sparse group records
     const uint32_t chunk = (uint32_t)a.chunk;
