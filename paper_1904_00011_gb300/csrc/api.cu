@@ -308,6 +308,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     uint32_t m1_i = 0;
     const bool pool = (ctx->cfg.flags & PCMD_FLAG_POOL) != 0;
     bool any_dense = false, any_ptrs = false;
+    uint64_t btab_bytes = 0;      // word tables of every set's dense groups
     for (int s = 0; s < n_sets; ++s) {
         tin[s].m1_k = m1_k[s];
         tin[s].m1_off = 0;
@@ -322,6 +323,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
             const double sfh = std::pow(10.0, p[s].log_sfh[j]);
             for (int k = 0; k < m.n_feh; ++k) w[j * m.n_feh + k] = sfh * mdf[k];
         }
+        uint32_t btab_cap = 0;
         {   // an upper bound of the largest lambda: can the model have dense inversion groups or
             // transformed-rejection points (the draw kernel's full instantiation), or only sparse
             // inversion groups?
@@ -339,6 +341,27 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
             const double top = bound * std::max(hf[0], hf[1]);
             if (top >= 0.999 * (double)kDenseLam) any_dense = true;
             if (top >= 0.999 * (double)kPtrsThreshold) any_ptrs = true;
+            // room for the dense groups' word tables: a dense group holds a point whose lambda
+            // bound reaches kDenseLam, so the count of such points (the sorted IMF weights of
+            // each isochrone, binary search) bounds the dense list of either half
+            uint64_t pts = 0;
+            if (top >= 0.999 * (double)kDenseLam) {
+                const double hmax = std::max(hf[0], hf[1]);
+                for (int j = 0; j < m.n_ages; ++j)
+                    for (int k = 0; k < m.n_feh; ++k) {
+                        const double sw = w[j * m.n_feh + k] * hmax;
+                        if (!(sw > 0.0)) continue;
+                        const double cut = 0.999 * (double)kDenseLam / sw;
+                        if (k == m1_k[s]) {
+                            const double *mi = m1_imf + (size_t)tin[s].m1_off + (size_t)j * m.n_mass;
+                            for (int i = 0; i < m.n_mass; ++i) pts += mi[i] >= cut ? 1u : 0u;
+                        } else {
+                            const double *dsc = m.imf_desc.data() + ((size_t)j * m.n_feh + k) * m.n_mass;
+                            pts += (uint64_t)(std::upper_bound(dsc, dsc + m.n_mass, cut, std::greater<double>()) - dsc);
+                        }
+                    }
+            }
+            btab_cap = (uint32_t)std::min<uint64_t>(pts, (P + kGroup - 1u) / kGroup);
         }
         tin[s].base = (uint64_t)s * L.bytes;
         tin[s].flux_factor = std::pow(10.0, -0.4 * p[s].dmod);
@@ -354,8 +377,9 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
         }
         d.tail_off = tin[s].base + L.tail_off;
         d.flux_off = tin[s].base + L.flux_off;
-        for (int h = 0; h < 2; ++h)
-            d.btab_off[h] = ((uint64_t)s * 2u + (uint64_t)h) * ((P + kGroup - 1u) / kGroup) * kBtabGroupBytes;
+        d.btab_cap = btab_cap;
+        for (int h = 0; h < 2; ++h) d.btab_off[h] = btab_bytes + (uint64_t)h * btab_cap * kBtabGroupBytes;
+        btab_bytes += 2ull * btab_cap * kBtabGroupBytes;
         d.pool_on = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 1u : 0u;
         for (int h = 0; h < 2; ++h) d.pool_off[h] = tin[s].base + L.pool_off[h];
         // dust screen of this model (Section 2.2): E = 10^log_ebv exp(sigma z)
@@ -389,7 +413,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     // above the rejection boundary keep their own draws either way
     const int draw_paths = pool ? (kPathPool | (any_ptrs ? kPathDense : 0)) : (any_dense ? kPathDense : kPathSparse);
     const bool need_btab = !pool && any_dense;
-    if (need_btab) CK(ctx->btab.ensure((size_t)n_sets * 2 * G * kBtabGroupBytes));
+    if (need_btab) CK(ctx->btab.ensure((size_t)btab_bytes));
     CK(ctx->tab_in.ensure(up_bytes));
     ctx->desc_d = reinterpret_cast<SetDesc *>(ctx->tab_in.as<uint8_t>() + desc_off);
     const size_t n_scr = (ctx->cfg.flags & PCMD_FLAG_POOL) ? 2 : 1;
@@ -410,6 +434,7 @@ static pcmd_status stage_sets(pcmd_ctx *ctx, const pcmd_params *p, int n_sets, c
     std::memset(&ta, 0, sizeof ta);
     ta.tables = ctx->tables.as<uint8_t>();
     ta.btab = need_btab ? ctx->btab.as<uint8_t>() : nullptr;
+    ta.err = ctx->err.as<uint32_t>();
     ta.desc = ctx->desc_d;
     ta.sets = ctx->tab_in.as<TabSetIn>();
     ta.weights = reinterpret_cast<const double *>(ctx->tab_in.as<uint8_t>() + in_bytes);
@@ -773,6 +798,10 @@ pcmd_status pcmd_sync(pcmd_ctx *ctx) {
             ctx->err_text = "a bounded wait inside a kernel ran out";
             return PCMD_ERR_TIMEOUT;
         }
+        if (e & kErrBounds) {
+            ctx->err_text = "a dense-group list exceeded the room reserved for its word tables";
+            return PCMD_ERR_CUDA;
+        }
         ctx->err_text = "transformed rejection reached its attempt cap";
         return PCMD_ERR_SAMPLER_LIMIT;
     }
@@ -805,6 +834,10 @@ static pcmd_status fetch_ll(pcmd_ctx *ctx, int n_sets, double *h_ll) {
     if (e & kErrTimeout) {
         ctx->err_text = "a bounded wait inside a kernel ran out";
         return PCMD_ERR_TIMEOUT;
+    }
+    if (e & kErrBounds) {
+        ctx->err_text = "a dense-group list exceeded the room reserved for its word tables";
+        return PCMD_ERR_CUDA;
     }
     ctx->err_text = "transformed rejection reached its attempt cap";
     return PCMD_ERR_SAMPLER_LIMIT;

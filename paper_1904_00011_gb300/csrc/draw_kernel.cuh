@@ -377,10 +377,11 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
 }
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
-// the HI call and the four LO calls of the group are drawn up front.  Each slot's count starts
-// from its byte table: the count at the lower edge of the HI byte, final when it is the same for
-// the whole byte; otherwise the walk continues upwards through the slot's thresholds from there
-// (a word of the byte cannot have fewer stars than the byte's lower edge).
+// the HI call and the four LO calls of the group are drawn up front.  Each slot's count comes
+// from its word table: the count at the lower edge of the HI byte, plus one when the word's low
+// 24 bits exceed those of the byte's first threshold; only a byte holding two or more thresholds
+// (the tails of the distribution) continues upwards through the slot's thresholds when the word
+// is above the first.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -388,7 +389,7 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
     const uint32_t nd = ic.active ? d.n_dense[H] : 0u;
     if (nd == 0u) return;
     const uint8_t *base = a.tables + d.dense_off[H];
-    const uint8_t *btab = a.btab + d.btab_off[H];
+    const uint32_t *btab = reinterpret_cast<const uint32_t *>(a.btab + d.btab_off[H]);
     const PhiloxPrefix ph = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
     const PhiloxPrefix pl = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
     for (uint32_t q = (uint32_t)sidx; q < nd; q += (uint32_t)a.split) {
@@ -397,13 +398,13 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
         const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * (uint32_t)kGroup;
         const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
-        const uint8_t *bt = btab + (size_t)q * kBtabGroupBytes;
+        const uint32_t *bt = btab + (size_t)q * kBtabGroupEntries;
         // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and
         // the group total goes into the pixel's (compensated) accumulator once
         float gs[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) gs[b] = 0.0f;
-#pragma unroll 1
+#pragma unroll 2
         for (uint32_t qd = 0; qd < 4u; ++qd) {
             // the quad's four table entries first: their loads overlap the LO call
             uint32_t e[4];
@@ -416,9 +417,11 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
 #pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
                 const uint32_t j = 4u * qd + t;
-                uint32_t n = e[t] & 0x7Fu;
-                if (!(e[t] & 0x80u)) {
-                    const uint32_t x = (hi_byte(whi, j) << 24) | (word_of(wlo, t) >> 8);
+                const uint32_t low = word_of(wlo, t) >> 8;
+                const bool above = low > (e[t] >> 8);
+                uint32_t n = (e[t] & 0x7Fu) + (above ? 1u : 0u);
+                if ((e[t] & 0x80u) && above) {
+                    const uint32_t x = (hi_byte(whi, j) << 24) | low;
                     const uint4 sr = __ldg(slow + j);
                     n = count_up_from(x, sr, ic.tail, n);
                 }
@@ -517,11 +520,16 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
 
 // Transformed-rejection points (lambda >= 64) of half H.  The lanes (pixels) of a warp start on
 // the records q = sidx, sidx + split, ... and every iteration of a warp-wide loop makes one
-// attempt for each lane's current draw: an accepted attempt (squeeze, or the log-form test when
-// the squeeze is inconclusive) gives the count and moves the lane to its next record, a
-// rejected one to the draw's next attempt.  Each draw takes exactly the attempt loop's
-// decisions (first accepted attempt, cap as in ptrs_draw); the lanes never wait for each other's
-// rejections except at the end of their record lists.  Called by all 32 lanes of the warp.
+// cheap attempt for each lane's current draw: a squeeze acceptance gives the count and moves
+// the lane to its next record, a quick rejection moves it to the draw's next attempt, and an
+// attempt the squeeze leaves open waits for the log-form test.  The waiting lanes take their
+// log-form tests together, once kPtrsLogBatch of them wait or every live lane does, so the
+// warp runs the expensive test a few times per draw round instead of in nearly every
+// iteration.  Each draw still takes exactly the attempt loop's decisions in order (first
+// accepted attempt, cap as in ptrs_draw): a waiting lane makes no further attempt of its draw
+// until its test is decided.  Called by all 32 lanes of the warp.
+constexpr int kPtrsLogBatch = 16;
+
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                              int sidx, Acc<B, KAHAN> &acc) {
@@ -533,42 +541,54 @@ __device__ __forceinline__ void process_ptrs(const DrawArgs &a, const ItemCtx &i
     PtrsRec rec;
     if (q < n_rec) rec = load_ptrs(pr, q);
     uint4 w = make_uint4(0, 0, 0, 0);
+    PtrsTry t;
+    t.kf = t.us = t.V = 0.0f;
+    t.status = 1;
+    bool wait = false;          // the current attempt waits for its log-form test
     // accepted draws' n f_b are summed with plain FMAs, 32 draws at a time, and each partial goes
     // into the pixel's (compensated) accumulator
     float ps[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) ps[b] = 0.0f;
     uint32_t np = 0u;
-    while (__any_sync(0xffffffffu, q < n_rec)) {
-        if (q < n_rec) {
+    // the draw of record q ends: accepted with count n, or (ok false) the attempt cap was reached
+    auto finish = [&](uint32_t n, bool ok) {
+        if (ok) {
+            const float nf = (float)n;
+#pragma unroll
+            for (int b = 0; b < B; ++b) ps[b] = fmaf(nf, rec.flux[b], ps[b]);
+            if (++np == 32u) {
+                acc.template add_sum<H>(ps);
+#pragma unroll
+                for (int b = 0; b < B; ++b) ps[b] = 0.0f;
+                np = 0u;
+            }
+            if (MODE == kModeCounts && n) {
+                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
+            }
+        } else {
+            atomicOr(a.err, kErrSampler);
+        }
+        q += (uint32_t)a.split;
+        at = 0u;
+        if (q < n_rec) rec = load_ptrs(pr, q);
+    };
+    for (;;) {
+        const uint32_t live = __ballot_sync(0xffffffffu, q < n_rec);
+        if (live == 0u) break;
+        const uint32_t waiting = __ballot_sync(0xffffffffu, wait);
+        if (waiting != 0u && (__popc(waiting) >= kPtrsLogBatch || waiting == live) && wait) {
+            wait = false;
+            if (ptrs_log_accept(rec, t)) finish((uint32_t)t.kf, true);
+            else if (++at >= a.ptrs_cap) finish(0u, false);
+        }
+        if (q < n_rec && !wait) {
             if ((at & 1u) == 0u) w = ptrs_words(rec, ic.pix, ic.set, H, at, a.rk0, a.rk1);
-            const PtrsTry t = ptrs_cheap(rec, (at & 1u) ? w.z : w.x, (at & 1u) ? w.w : w.y);
-            bool done = t.status == 0;
-            if (t.status == 2) done = ptrs_log_accept(rec, t);
-            if (done) {
-                const uint32_t n = (uint32_t)t.kf;
-                const float nf = (float)n;
-#pragma unroll
-                for (int b = 0; b < B; ++b) ps[b] = fmaf(nf, rec.flux[b], ps[b]);
-                if (++np == 32u) {
-                    acc.template add_sum<H>(ps);
-#pragma unroll
-                    for (int b = 0; b < B; ++b) ps[b] = 0.0f;
-                    np = 0u;
-                }
-                if (MODE == kModeCounts && n) {
-                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + rec.i] = n;
-                }
-            } else if (++at >= a.ptrs_cap) {
-                atomicOr(a.err, kErrSampler);
-                done = true;
-            }
-            if (done) {
-                q += (uint32_t)a.split;
-                at = 0u;
-                if (q < n_rec) rec = load_ptrs(pr, q);
-            }
+            t = ptrs_cheap(rec, (at & 1u) ? w.z : w.x, (at & 1u) ? w.w : w.y);
+            if (t.status == 0) finish((uint32_t)t.kf, true);
+            else if (t.status == 2) wait = true;
+            else if (++at >= a.ptrs_cap) finish(0u, false);
         }
     }
     if (np) acc.template add_sum<H>(ps);

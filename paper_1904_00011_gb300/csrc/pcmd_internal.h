@@ -77,13 +77,19 @@ struct __align__(16) SetDesc {
     uint32_t pool_on;       // total-count sampler for the points below lambda 10
     uint64_t pool_off[2];   // PoolHdr + thresholds / guide / entries per half (host-built)
     uint64_t flux_off;      // float [P][B] electrons per star of every point
-    uint64_t btab_off[2];   // byte tables of the dense groups (offsets in the byte-table buffer)
+    uint64_t btab_off[2];   // word tables of the dense groups (byte offsets in the word-table buffer)
+    uint32_t btab_cap;      // dense groups per half the word tables have room for
+    uint32_t pad_btab[3];
 };
 
-// Byte table of a dense group: for each of its 16 slots and each HI byte b, the count at the
-// byte's lower edge, count(b << 24), in bits 0-6, and bit 7 set when the count is the same for
-// every word of the byte (then the byte alone gives the draw).  kBtabGroupBytes per group.
-constexpr uint32_t kBtabGroupBytes = kGroup * 256u;
+// Word table of a dense group: for each of its 16 slots and each HI byte b one 32-bit entry,
+// bits 0-6 the count at the byte's lower edge c = count(b << 24), bit 7 set when two or more
+// thresholds fall inside the byte, bits 8-31 the low 24 bits of the first threshold at or above
+// b << 24 (0xFFFFFF when the count is the same over the whole byte).  A word x of the byte has
+// count c + (low24(x) > bits 8-31), exact unless bit 7 is set and x is above that threshold
+// (then the thresholds decide from c + 1 on).  kBtabGroupBytes per group.
+constexpr uint32_t kBtabGroupEntries = kGroup * 256u;
+constexpr uint32_t kBtabGroupBytes = kBtabGroupEntries * 4u;
 
 // Total-count sampler of one dust half (the pool = every point with 0 < lambda < 64): header,
 // then Z[kInvCap] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
@@ -118,7 +124,7 @@ struct PixelConsts {
 
 struct DrawArgs {
     const uint8_t *tables;      // table buffer
-    const uint8_t *btab;        // byte tables of the dense groups (full instantiation only)
+    const uint8_t *btab;        // word tables of the dense groups (full instantiation only)
     const SetDesc *desc;        // [n_sets]
     const uint2 *items;         // (set index, tile) per work item, grouped by set
     const uint32_t *order;      // queue position -> item (longest first); nullptr = identity

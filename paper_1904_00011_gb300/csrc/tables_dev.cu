@@ -354,7 +354,15 @@ __global__ void __launch_bounds__(1024) tab_scan_kernel(const TabArgs a) {
     if (threadIdx.x == 0) {
         SetDesc *d = a.desc + s;
         d->n_grp[h] = carry.x;
-        d->n_dense[h] = carry.y;
+        // the word tables have room for btab_cap dense groups per half (an upper bound from the
+        // host's FP64 lambda bound): more is an internal error, latched, and the list is cut so
+        // that nothing reads or writes past the tables
+        uint32_t nd = carry.y;
+        if (a.btab && nd > d->btab_cap) {
+            atomicOr(a.err, kErrBounds);
+            nd = d->btab_cap;
+        }
+        d->n_dense[h] = nd;
         d->n_ptrs[h] = carry.w;
     }
     if (!a.pool) return;
@@ -572,8 +580,10 @@ __device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, c
     return n0 + lo;
 }
 
-// Byte tables of the dense groups: one CTA per (dense-list position, half, model), one thread per
-// (slot, byte) entry: count(b << 24) and whether count((b << 24) | 0xFFFFFF) is the same.
+// Word tables of the dense groups: one CTA per (dense-list position, half, model), one thread per
+// (slot, byte) entry: c = count(b << 24), whether count((b << 24) | 0xFFFFFF) exceeds c + 1, and
+// the low 24 bits of the first threshold at or above b << 24 (Z_c: index c - n0 of the record's
+// shifted thresholds), or 0xFFFFFF when the count does not change over the byte.
 __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint32_t q = blockIdx.x;
     const int h = blockIdx.y, s = blockIdx.z;
@@ -583,14 +593,21 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint32_t gid = *reinterpret_cast<const uint32_t *>(a.tables + d.dense_off[h] + (uint64_t)q * rec);
     const uint4 *slow = reinterpret_cast<const uint4 *>(a.tables + d.slow_off[h]) + (uint64_t)gid * kGroup;
     const uint32_t *tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
-    uint8_t *out = a.btab + d.btab_off[h] + (uint64_t)q * kBtabGroupBytes;
-    for (uint32_t e = threadIdx.x; e < kBtabGroupBytes; e += blockDim.x) {
+    uint32_t *out = reinterpret_cast<uint32_t *>(a.btab + d.btab_off[h]) + (uint64_t)q * kBtabGroupEntries;
+    for (uint32_t e = threadIdx.x; e < kBtabGroupEntries; e += blockDim.x) {
         const uint32_t j = e >> 8, b = e & 255u;
         const uint4 sr = slow[j];
+        const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
         const uint32_t c0 = count_bsearch(b << 24, sr, tail);
         const uint32_t c1 = count_bsearch((b << 24) | 0xFFFFFFu, sr, tail);
+        uint32_t zl = 0xFFFFFFu;
+        if (c1 != c0) {
+            const uint32_t k = c0 - n0;                 // c0 >= n0: every word exceeds the first n0
+            const uint32_t z = k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
+            zl = z & 0xFFFFFFu;                         // Z_c lies inside the byte: its top byte is b
+        }
         // counts below a mean of 64 stay below 128 (the CDF passes 1 - 2^-33 first)
-        out[e] = (uint8_t)((c0 & 0x7Fu) | (c0 == c1 ? 0x80u : 0u));
+        out[e] = (c0 & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
     }
 }
 

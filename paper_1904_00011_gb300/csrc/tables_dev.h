@@ -32,7 +32,8 @@ struct TabSetIn {
 
 struct TabArgs {
     uint8_t *tables;
-    uint8_t *btab;              // byte tables of the dense groups, or nullptr (no dense groups)
+    uint8_t *btab;              // word tables of the dense groups, or nullptr (no dense groups)
+    uint32_t *err;              // latched error word of the context (kErrBounds)
     SetDesc *desc;              // list lengths are written here (device)
     const TabSetIn *sets;       // [n_sets]
     const double *weights;      // [n_sets][n_ages * n_feh]
