@@ -228,7 +228,7 @@ def issue_roofline(instr: float, seconds: float, what: str) -> dict:
             "algorithmic": what, "peak_basis": "152 SMs x 128 issue slots/clk x 2070 MHz"}
 
 
-INV_LIMIT = 64.0                     # inversion below this mean, transformed rejection at/above
+INV_LIMIT = 192.0                    # inversion below this mean, transformed rejection at/above
 
 
 def algorithmic_ops(sim, params):

@@ -8,7 +8,7 @@
 // pixel and split (a CTA's warps share a pixel tile and divide the isochrone points), with
 // the point tables streamed through shared memory by bulk copies.
 //
-// Draw word of inversion point i (lambda < 64) of half h at pixel p:
+// Draw word of inversion point i (lambda < 192) of half h at pixel p:
 //   x = b << 24 | l >> 8, b = byte i & 3 of word (i & 15) >> 2 of Philox(p, i >> 4, set, HI|h),
 //   l = word i & 3 of Philox(p, i >> 2, set, LO|h);  n = #{k : x > Z_k}.
 // The fast path only needs b: b < Z_0 >> 24 gives n = 0 without the LO call, and a certain hit
@@ -54,7 +54,7 @@ __device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
     return __fsub_rn(r, st);
 }
 
-// Transformed rejection with squeeze (Hormann 1993) for lambda >= 64.  Attempt `at` uses words
+// Transformed rejection with squeeze (Hormann 1993) for lambda >= 192.  Attempt `at` uses words
 // 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).  The cheap part of an attempt decides
 // the squeeze acceptance and the quick rejections; the rest takes the log-form test.
 struct PtrsTry {
@@ -208,6 +208,18 @@ __device__ __forceinline__ uint32_t count_up_from(uint32_t x, const uint4 &sr, c
         return kk == 0u ? sr.x : kk == 1u ? sr.y : (kk - 2u < len ? __ldg(tail + sr.z + (kk - 2u)) : 0xFFFFFFFFu);
     };
     while (x > z(k)) ++k;                           // z saturates at len + 2
+    return n0 + k;
+}
+
+// n = #{k : x > Z_k} given an upper bound c >= n (x <= Z_c): walks downwards from k = c.  The
+// first n0 thresholds are -1, so the walk stops at n0 at the latest.
+__device__ __forceinline__ uint32_t count_down_from(uint32_t x, const uint4 &sr, const uint32_t *tail, uint32_t c) {
+    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
+    uint32_t k = c - n0;
+    auto z = [&](uint32_t kk) -> uint32_t {
+        return kk == 0u ? sr.x : kk == 1u ? sr.y : (kk - 2u < len ? __ldg(tail + sr.z + (kk - 2u)) : 0xFFFFFFFFu);
+    };
+    while (k > 0u && x <= z(k - 1u)) --k;
     return n0 + k;
 }
 
@@ -378,10 +390,11 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
 // the HI call and the four LO calls of the group are drawn up front.  Each slot's count comes
-// from its word table: the count at the lower edge of the HI byte, plus one when the word's low
-// 24 bits exceed those of the byte's first threshold; only a byte holding two or more thresholds
-// (the tails of the distribution) continues upwards through the slot's thresholds when the word
-// is above the first.
+// from its word table and the slot's leading count n0: n0 plus the table's count at the lower
+// edge of the HI byte, plus one when the word's low 24 bits exceed those of the byte's first
+// threshold.  A byte holding two or more thresholds (the
+// tails of the distribution) starts at its most frequent count m instead and walks through the
+// slot's thresholds from there, upwards when the word is above Z_m, downwards otherwise.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -406,12 +419,14 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         for (int b = 0; b < B; ++b) gs[b] = 0.0f;
 #pragma unroll 2
         for (uint32_t qd = 0; qd < 4u; ++qd) {
-            // the quad's four table entries first: their loads overlap the LO call
+            // the quad's four table entries and slow records first: their loads overlap the LO call
             uint32_t e[4];
+            uint4 sq[4];
 #pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
                 const uint32_t j = 4u * qd + t;
                 e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
+                sq[t] = __ldg(slow + j);
             }
             const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
 #pragma unroll
@@ -419,11 +434,10 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
                 const uint32_t j = 4u * qd + t;
                 const uint32_t low = word_of(wlo, t) >> 8;
                 const bool above = low > (e[t] >> 8);
-                uint32_t n = (e[t] & 0x7Fu) + (above ? 1u : 0u);
-                if ((e[t] & 0x80u) && above) {
+                uint32_t n = ((sq[t].w >> 8) & 0xFFu) + (e[t] & 0x7Fu) + (above ? 1u : 0u);
+                if (e[t] & 0x80u) {
                     const uint32_t x = (hi_byte(whi, j) << 24) | low;
-                    const uint4 sr = __ldg(slow + j);
-                    n = count_up_from(x, sr, ic.tail, n);
+                    n = above ? count_up_from(x, sq[t], ic.tail, n) : count_down_from(x, sq[t], ic.tail, n);
                 }
                 const float nf = (float)n;
 #pragma unroll
@@ -518,7 +532,7 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
     }
 }
 
-// Transformed-rejection points (lambda >= 64) of half H.  The lanes (pixels) of a warp start on
+// Transformed-rejection points (lambda >= 192) of half H.  The lanes (pixels) of a warp start on
 // the records q = sidx, sidx + split, ... and every iteration of a warp-wide loop makes one
 // cheap attempt for each lane's current draw: a squeeze acceptance gives the count and moves
 // the lane to its next record, a quick rejection moves it to the draw's next attempt, and an
@@ -731,7 +745,7 @@ __global__ void __launch_bounds__(256, (PATHS & kPathDense) ? 2 : ((PATHS & kPat
         }
         if (stop) break;
 
-        // ---- dense inversion groups, then transformed-rejection points (lambda >= 64) ----
+        // ---- dense inversion groups, then transformed-rejection points (lambda >= 192) ----
         if (PATHS & kPathPool) {
             process_pool<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
             process_pool<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);

@@ -7,9 +7,12 @@ namespace pcmd {
 
 constexpr int kMaxBands = 4;
 constexpr int kGroup = 16;                // isochrone points per HI call (one byte each)
-constexpr float kPtrsThreshold = 64.0f;   // inversion below, transformed rejection at/above
-constexpr int kInvCap = 128;              // inversion counts are capped at 128 (P(n > 128) < 2^-40
-                                          // for every lambda below 64)
+constexpr float kPtrsThreshold = 192.0f;  // inversion below, transformed rejection at/above
+constexpr int kInvCap = 384;              // inversion counts are capped at 384 (P(n > 384) < 2^-110
+                                          // for every lambda below 192)
+// Tail thresholds per inversion point: Z'_2 .. up to the first saturated one (at most 174 below a
+// mean of 192: the CDF passes 1 - 2^-33 within ~176 counts of the first non-negative threshold).
+constexpr int kTailCap = 192;
 // The total-count sampler draws its per-pixel total by inversion only below 10: a single draw
 // per pixel and half would otherwise need one serial FP64 threshold series of up to ~120 terms
 // per model and a walk of up to ~60 thresholds per pixel.
@@ -50,7 +53,7 @@ struct SlowRec {
                             // bits 16-31: start index of the device's threshold walk
 };
 
-// Transformed-rejection record (lambda >= 64), 48 bytes.
+// Transformed-rejection record (lambda >= 192), 48 bytes.
 struct PtrsRec {
     uint32_t i;             // canonical point index
     float lam, b, a, twoa, vr, log_ia;
@@ -83,15 +86,16 @@ struct __align__(16) SetDesc {
 };
 
 // Word table of a dense group: for each of its 16 slots and each HI byte b one 32-bit entry,
-// bits 0-6 the count at the byte's lower edge c = count(b << 24), bit 7 set when two or more
-// thresholds fall inside the byte, bits 8-31 the low 24 bits of the first threshold at or above
-// b << 24 (0xFFFFFF when the count is the same over the whole byte).  A word x of the byte has
-// count c + (low24(x) > bits 8-31), exact unless bit 7 is set and x is above that threshold
-// (then the thresholds decide from c + 1 on).  kBtabGroupBytes per group.
+// bits 0-6 a count c relative to the slot's n0 (the count at the byte's lower edge, count(b << 24)
+// - n0 <= 119 below a mean of 192), bit 7 set when two or more thresholds fall inside the byte,
+// bits 8-31 the low 24 bits of Z_(n0 + c) (0xFFFFFF when the count is the same over the whole
+// byte).  A word x of the byte has count n0 + c + (low24(x) > bits 8-31), exact unless bit 7 is
+// set; then c is the byte's most frequent count and the thresholds decide from there.
+// kBtabGroupBytes per group.
 constexpr uint32_t kBtabGroupEntries = kGroup * 256u;
 constexpr uint32_t kBtabGroupBytes = kBtabGroupEntries * 4u;
 
-// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 64): header,
+// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 192): header,
 // then Z[kInvCap] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
 // table (guide[b] = first entry j with T_j > b 2^(32 - bits), guide[2^bits] = n - 1), the pool's
 // point indices and their star-assignment thresholds T_j.

@@ -145,6 +145,7 @@ __device__ __forceinline__ PointCls classify(const PointIn &p) {
         }
     });
     if (zh.n0 == 0u && zh.z0 == 0xFFFFFFFFu) return c;    // never a star
+    if (tail > (uint32_t)kTailCap) tail = kTailCap;      // unreachable below a mean of 192
     c.cls = 1;
     c.z0 = zh.z0;
     c.z1 = z1;
@@ -165,7 +166,7 @@ __device__ __forceinline__ uint32_t group_scan(uint32_t v, int j, uint32_t &tota
     return s - v;
 }
 
-// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 64 (exact:
+// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 192 (exact:
 // lambda 2^40 is exact in FP64), 0 otherwise; a point is in the pool when L > 0.
 __device__ __forceinline__ uint64_t pool_weight(const PointIn &p) {
     if (!p.valid || !(p.lam > 0.0f) || !(p.lam < kPtrsThreshold)) return 0ull;
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     uint32_t tot;
     const uint32_t my_tail = group_scan(c.cls == 1 ? c.tail : 0u, j, tot);
     const uint32_t my_ptrs = group_scan(p.valid && p.lam >= kPtrsThreshold ? 1u : 0u, j, tot);
-    const uint32_t tail_off = (uint32_t)h * a.P * (uint32_t)(kInvCap - 2) + sc.z + my_tail;
+    const uint32_t tail_off = (uint32_t)h * a.P * (uint32_t)kTailCap + sc.z + my_tail;
     uint32_t *tail = reinterpret_cast<uint32_t *>(tab + L.tail_off) + tail_off;
     if (c.cls == 1) {
         z0 = c.z0;
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         thresholds_dev(p.lam, [&](int k, uint32_t z) {
             if (k >= 2 && !sat) {
                 if (z == 0xFFFFFFFFu) sat = true;
-                else tail[n++] = z;
+                else if (n < len) tail[n++] = z;
             }
         });
     }
@@ -555,7 +556,7 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
         L.slow_off[h] = place((uint64_t)G * kGroup * sizeof(SlowRec));
         L.ptrs_off[h] = place((uint64_t)P * sizeof(PtrsRec));
     }
-    L.tail_off = place(2ull * P * (kInvCap - 2) * 4u + 4u);
+    L.tail_off = place(2ull * P * kTailCap * 4u + 4u);
     L.flux_off = place((uint64_t)P * n_bands * 4u);
     for (int h = 0; h < 2; ++h) L.pool_off[h] = place(pool_region_bytes(P));
     L.bytes = off;
@@ -581,9 +582,10 @@ __device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, c
 }
 
 // Word tables of the dense groups: one CTA per (dense-list position, half, model), one thread per
-// (slot, byte) entry: c = count(b << 24), whether count((b << 24) | 0xFFFFFF) exceeds c + 1, and
-// the low 24 bits of the first threshold at or above b << 24 (Z_c: index c - n0 of the record's
-// shifted thresholds), or 0xFFFFFF when the count does not change over the byte.
+// (slot, byte) entry.  c0 = count(b << 24), c1 = count((b << 24) | 0xFFFFFF).  One threshold or
+// none inside the byte: c0 and the low 24 bits of Z_c0 (0xFFFFFF when c1 = c0).  Two or more
+// (flag bit 7): the count m in [c0, c1] that holds the most words of the byte and the low 24
+// bits of Z_m (0xFFFFFF when m = c1), so that most words of the byte end where the search starts.
 __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint32_t q = blockIdx.x;
     const int h = blockIdx.y, s = blockIdx.z;
@@ -600,14 +602,32 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
         const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
         const uint32_t c0 = count_bsearch(b << 24, sr, tail);
         const uint32_t c1 = count_bsearch((b << 24) | 0xFFFFFFu, sr, tail);
-        uint32_t zl = 0xFFFFFFu;
-        if (c1 != c0) {
-            const uint32_t k = c0 - n0;                 // c0 >= n0: every word exceeds the first n0
-            const uint32_t z = k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
-            zl = z & 0xFFFFFFu;                         // Z_c lies inside the byte: its top byte is b
+        // Z_c (c >= n0: every word exceeds the first n0 thresholds)
+        auto zc = [&](uint32_t c) -> uint32_t {
+            const uint32_t k = c - n0;
+            return k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
+        };
+        uint32_t c = c0, zl = 0xFFFFFFu;
+        const uint32_t cmax = n0 + 0x7Fu;               // the entry holds c - n0 in 7 bits
+        if (c1 == c0 + 1u) {
+            zl = zc(c0) & 0xFFFFFFu;                    // Z_c0 lies inside the byte: its top byte is b
+        } else if (c1 > c0 + 1u) {
+            // words of count m in the byte: [max(Z_{m-1} + 1, b << 24), min(Z_m, b << 24 | 2^24 - 1)]
+            // (empty when two thresholds are equal)
+            uint32_t best = 0u, lo = b << 24;
+            for (uint32_t m = c0; m <= c1 && m <= cmax; ++m) {
+                const uint32_t hi = m == c1 ? ((b << 24) | 0xFFFFFFu) : zc(m);
+                const uint32_t width = hi >= lo ? hi - lo + 1u : 0u;
+                if (m == c0 || width > best) {
+                    best = width;
+                    c = m;
+                }
+                lo = hi + 1u;
+            }
+            zl = c == c1 ? 0xFFFFFFu : (zc(c) & 0xFFFFFFu);
         }
-        // counts below a mean of 64 stay below 128 (the CDF passes 1 - 2^-33 first)
-        out[e] = (c0 & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
+        // below a mean of 192 the count at any byte's lower edge is at most n0 + 119
+        out[e] = ((c - n0) & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
     }
 }
 

@@ -71,8 +71,8 @@ def test_tables_match_oracle(name):
             assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i])) == 0
             if z0[h, i] < 0xFFFFFFFF:
                 assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i]) + 1) >= 1
-        # from ~22.9 to 64 even the smallest word gives a star (e^-lambda 2^32 < 1/2): no Z_0
-        big = np.nonzero((lam[h] > 22.9) & (lam[h] < 64))[0]
+        # from ~22.9 to 192 even the smallest word gives a star (e^-lambda 2^32 < 1/2): no Z_0
+        big = np.nonzero((lam[h] > 22.9) & (lam[h] < 192))[0]
         for i in big[:20]:
             assert z0[h, i] == 0xFFFFFFFF
             assert O.poisson_inversion(float(lam[h, i]), 0) >= 1
@@ -151,10 +151,10 @@ def _end_to_end(w, n_threads=16):
 @pytest.mark.parametrize("name", ["tiny", "full_small", "full", "psf_grid", "psf_grid_ragged", "pool",
                                   "large_physics"])
 def test_end_to_end_fluxes_bins_loglike(name):
-    # large_physics: the large-Npix model (3 bands, log10 Npix 6, transformed rejection dominant,
-    # Kahan sums, dust, 25x25 PSF, noise) on a 128x128 image
+    # large_physics: the large-Npix model (3 bands, log10 Npix 6.5: sparse, dense and
+    # transformed-rejection draws, Kahan sums, dust, 25x25 PSF, noise) on a 128x128 image
     w = {"tiny": W.tiny, "full_small": lambda: W.full(n_im=128, sky=40.0),
-         "large_physics": lambda: W.large(n_im=128, log_npix=6.0),
+         "large_physics": lambda: W.large(n_im=128, log_npix=6.5),
          "full": W.full, "psf_grid": lambda: W.full(n_im=128, psf_grid=True),
          "psf_grid_ragged": lambda: W.full(n_im=100, psf_grid=True, sky=10.0),
          "pool": lambda: dataclasses.replace(W.full(n_im=128, sky=20.0),
@@ -329,7 +329,7 @@ def test_sampler_limit_is_latched_and_reported(fused):
     the same context evaluates normally and equals a fresh context.  fused: the graph-replayed
     batched path (no PSF), else the image + PSF path."""
     import paper_1904_00011_gb300 as P
-    w = W.large(n_im=64, log_npix=6.0)
+    w = W.large(n_im=64, log_npix=6.5)
     if fused:
         w = dataclasses.replace(w, psf=None)
     s = _sim(w)
