@@ -428,6 +428,18 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
                 e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
                 sq[t] = __ldg(slow + j);
             }
+            // the quad's 4 x B fluxes: B 16-byte loads (the record's flux block is 16-byte aligned);
+            // with four bands each slot's own 16-byte load below (fewer live registers)
+            constexpr int kFq = B < 4 ? 4 * B : 1;
+            float fq[kFq];
+#pragma unroll
+            for (int v = 0; v < (B < 4 ? B : 0); ++v) {
+                const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + qd * (uint32_t)B + (uint32_t)v);
+                fq[4 * v] = f4.x;
+                fq[4 * v + 1] = f4.y;
+                fq[4 * v + 2] = f4.z;
+                fq[4 * v + 3] = f4.w;
+            }
             const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
 #pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
@@ -440,8 +452,15 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
                     n = above ? count_up_from(x, sq[t], ic.tail, n) : count_down_from(x, sq[t], ic.tail, n);
                 }
                 const float nf = (float)n;
+                if (B < 4) {
 #pragma unroll
-                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, __ldg(fl + j * B + b), gs[b]);
+                    for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fq[(t * B + b) % kFq], gs[b]);
+                } else {
+                    const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + j);
+                    const float fs[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                    for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fs[b % 4], gs[b]);
+                }
                 if (MODE == kModeCounts && n) {
                     if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
                         a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +

@@ -128,7 +128,9 @@ struct PointCls {
     uint32_t z0, z1, tail, n0;
 };
 
-__device__ __forceinline__ PointCls classify(const PointIn &p) {
+// The one pass over the threshold series: the tail thresholds Z'_2 .. (up to the first saturated
+// one, at most kTailCap) go to `tail`, the point's fixed slot of kTailCap words.
+__device__ __forceinline__ PointCls classify(const PointIn &p, uint32_t *tail_out) {
     PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u};
     if (!p.valid || !(p.lam > 0.0f)) return c;
     if (p.lam >= kPtrsThreshold) {
@@ -141,11 +143,10 @@ __device__ __forceinline__ PointCls classify(const PointIn &p) {
         if (k == 1) z1 = z;
         if (k >= 2 && !sat) {
             if (z == 0xFFFFFFFFu) sat = true;
-            else ++tail;
+            else if (tail < (uint32_t)kTailCap) tail_out[tail++] = z;   // the cap is unreachable below 192
         }
     });
     if (zh.n0 == 0u && zh.z0 == 0xFFFFFFFFu) return c;    // never a star
-    if (tail > (uint32_t)kTailCap) tail = kTailCap;      // unreachable below a mean of 192
     c.cls = 1;
     c.z0 = zh.z0;
     c.z1 = z1;
@@ -214,7 +215,10 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const int j = (int)(t % (uint32_t)kGroup);
     const TabSetIn in = a.sets[s];
     const PointIn p = g < a.G ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
-    const PointCls c = classify(p);
+    // tail thresholds of point slot t of half h: a fixed slot of kTailCap words
+    uint32_t *tail = reinterpret_cast<uint32_t *>(a.tables + in.base + a.layout.tail_off) +
+                     ((size_t)h * a.G * kGroup + t) * kTailCap;
+    const PointCls c = classify(p, tail);
     if (g < a.G)   // the write pass reads these instead of running the threshold series again
         a.pt_scratch[((size_t)s * 2 + h) * a.G * kGroup + t] = make_uint4(c.z0, c.z1, c.tail, (uint32_t)c.cls | (c.n0 << 8));
     uint32_t n_tail, n_ptrs;
@@ -416,24 +420,13 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         c.n0 = (pc.w >> 8) & 0xFFu;
     }
     uint32_t tot;
-    const uint32_t my_tail = group_scan(c.cls == 1 ? c.tail : 0u, j, tot);
     const uint32_t my_ptrs = group_scan(p.valid && p.lam >= kPtrsThreshold ? 1u : 0u, j, tot);
-    const uint32_t tail_off = (uint32_t)h * a.P * (uint32_t)kTailCap + sc.z + my_tail;
-    uint32_t *tail = reinterpret_cast<uint32_t *>(tab + L.tail_off) + tail_off;
+    // the count pass wrote the tail thresholds into the point's fixed slot
+    const uint32_t tail_off = (uint32_t)(((size_t)h * a.G * kGroup + t) * kTailCap);
     if (c.cls == 1) {
         z0 = c.z0;
         z1 = c.z1;
         len = c.tail;
-    }
-    if (c.cls == 1 && c.tail > 0u) {
-        bool sat = false;
-        uint32_t n = 0;
-        thresholds_dev(p.lam, [&](int k, uint32_t z) {
-            if (k >= 2 && !sat) {
-                if (z == 0xFFFFFFFFu) sat = true;
-                else if (n < len) tail[n++] = z;
-            }
-        });
     }
     if (in_range) {
         // the walk starts near the mean, in the shifted sequence Z'_k = Z_{n0 + k}
@@ -556,7 +549,7 @@ TabLayout tab_layout(uint32_t P, int n_bands) {
         L.slow_off[h] = place((uint64_t)G * kGroup * sizeof(SlowRec));
         L.ptrs_off[h] = place((uint64_t)P * sizeof(PtrsRec));
     }
-    L.tail_off = place(2ull * P * kTailCap * 4u + 4u);
+    L.tail_off = place(2ull * ((P + kGroup - 1u) / kGroup) * kGroup * kTailCap * 4u + 4u);
     L.flux_off = place((uint64_t)P * n_bands * 4u);
     for (int h = 0; h < 2; ++h) L.pool_off[h] = place(pool_region_bytes(P));
     L.bytes = off;
@@ -581,11 +574,13 @@ __device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, c
     return n0 + lo;
 }
 
-// Word tables of the dense groups: one CTA per (dense-list position, half, model), one thread per
-// (slot, byte) entry.  c0 = count(b << 24), c1 = count((b << 24) | 0xFFFFFF).  One threshold or
-// none inside the byte: c0 and the low 24 bits of Z_c0 (0xFFFFFF when c1 = c0).  Two or more
-// (flag bit 7): the count m in [c0, c1] that holds the most words of the byte and the low 24
-// bits of Z_m (0xFFFFFF when m = c1), so that most words of the byte end where the search starts.
+// Word tables of the dense groups: one CTA per (dense-list position, half, model); 16 threads per
+// slot, each for 16 consecutive HI bytes, walking the slot's thresholds alongside the byte edges
+// (one binary search for the first byte, then a merge).  For byte b: c0 = count(b << 24), c1 =
+// count((b << 24) | 0xFFFFFF).  One threshold or none inside the byte: c0 and the low 24 bits of
+// Z_c0 (0xFFFFFF when c1 = c0).  Two or more (flag bit 7): the count m in [c0, c1] that holds the
+// most words of the byte and the low 24 bits of Z_m (0xFFFFFF when m = c1), so that most words of
+// the byte end where the search starts.  Counts are stored relative to the slot's n0.
 __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint32_t q = blockIdx.x;
     const int h = blockIdx.y, s = blockIdx.z;
@@ -596,38 +591,45 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint4 *slow = reinterpret_cast<const uint4 *>(a.tables + d.slow_off[h]) + (uint64_t)gid * kGroup;
     const uint32_t *tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
     uint32_t *out = reinterpret_cast<uint32_t *>(a.btab + d.btab_off[h]) + (uint64_t)q * kBtabGroupEntries;
-    for (uint32_t e = threadIdx.x; e < kBtabGroupEntries; e += blockDim.x) {
-        const uint32_t j = e >> 8, b = e & 255u;
+    for (uint32_t t = threadIdx.x; t < kGroup * 16u; t += blockDim.x) {
+        const uint32_t j = t >> 4, b0 = (t & 15u) * 16u;
         const uint4 sr = slow[j];
         const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
-        const uint32_t c0 = count_bsearch(b << 24, sr, tail);
-        const uint32_t c1 = count_bsearch((b << 24) | 0xFFFFFFu, sr, tail);
-        // Z_c (c >= n0: every word exceeds the first n0 thresholds)
+        // Z_c (c >= n0: every word exceeds the first n0 thresholds); 2^32 - 1 from len + 2 on
         auto zc = [&](uint32_t c) -> uint32_t {
             const uint32_t k = c - n0;
             return k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
         };
-        uint32_t c = c0, zl = 0xFFFFFFu;
         const uint32_t cmax = n0 + 0x7Fu;               // the entry holds c - n0 in 7 bits
-        if (c1 == c0 + 1u) {
-            zl = zc(c0) & 0xFFFFFFu;                    // Z_c0 lies inside the byte: its top byte is b
-        } else if (c1 > c0 + 1u) {
-            // words of count m in the byte: [max(Z_{m-1} + 1, b << 24), min(Z_m, b << 24 | 2^24 - 1)]
-            // (empty when two thresholds are equal)
-            uint32_t best = 0u, lo = b << 24;
-            for (uint32_t m = c0; m <= c1 && m <= cmax; ++m) {
-                const uint32_t hi = m == c1 ? ((b << 24) | 0xFFFFFFu) : zc(m);
-                const uint32_t width = hi >= lo ? hi - lo + 1u : 0u;
-                if (m == c0 || width > best) {
-                    best = width;
-                    c = m;
+        uint32_t cur = count_bsearch(b0 << 24, sr, tail);
+        for (uint32_t b = b0; b < b0 + 16u; ++b) {
+            const uint32_t lo = b << 24, hi = lo | 0xFFFFFFu;
+            while (zc(cur) < lo) ++cur;                 // count(lo) = #{k : Z_k < lo}
+            const uint32_t c0 = cur;
+            uint32_t c1 = c0;
+            while (zc(c1) < hi) ++c1;                   // count(hi)
+            uint32_t c = c0, zl = 0xFFFFFFu;
+            if (c1 == c0 + 1u) {
+                zl = zc(c0) & 0xFFFFFFu;                // Z_c0 lies inside the byte: its top byte is b
+            } else if (c1 > c0 + 1u) {
+                // words of count m in the byte: [max(Z_{m-1} + 1, lo), min(Z_m, hi)] (empty when two
+                // thresholds are equal)
+                uint32_t best = 0u, wlo = lo;
+                for (uint32_t m = c0; m <= c1 && m <= cmax; ++m) {
+                    const uint32_t whi = m == c1 ? hi : zc(m);
+                    const uint32_t width = whi >= wlo ? whi - wlo + 1u : 0u;
+                    if (m == c0 || width > best) {
+                        best = width;
+                        c = m;
+                    }
+                    wlo = whi + 1u;
                 }
-                lo = hi + 1u;
+                zl = c == c1 ? 0xFFFFFFu : (zc(c) & 0xFFFFFFu);
             }
-            zl = c == c1 ? 0xFFFFFFu : (zc(c) & 0xFFFFFFu);
+            // below a mean of 192 the count at any byte's lower edge is at most n0 + 119
+            out[j * 256u + b] = ((c - n0) & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
+            cur = c1;                                   // count((b + 1) << 24) >= count(hi)
         }
-        // below a mean of 192 the count at any byte's lower edge is at most n0 + 119
-        out[e] = ((c - n0) & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
     }
 }
 

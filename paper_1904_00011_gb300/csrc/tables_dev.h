@@ -14,7 +14,7 @@ struct TabLayout {
     uint64_t dense_off[2];  // group records of the dense inversion groups, G per half
     uint64_t slow_off[2];   // SlowRec[16 G] per half
     uint64_t ptrs_off[2];   // PtrsRec[P] per half
-    uint64_t tail_off;      // uint32 [2][P][kInvCap - 2] tail thresholds
+    uint64_t tail_off;      // uint32 [2][16 G][kTailCap] tail thresholds (a fixed slot per point)
     uint64_t flux_off;      // float [P][B] electrons per star
     uint64_t pool_off[2];   // total-count sampler regions (written only when the sampler is used)
     uint64_t bytes;         // table size (256-byte multiple)
