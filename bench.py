@@ -229,6 +229,7 @@ def issue_roofline(instr: float, seconds: float, what: str) -> dict:
 
 
 INV_LIMIT = 192.0                    # inversion below this mean, transformed rejection at/above
+DENSE_LAM = 0.08                     # slots from this mean on are drawn in dense groups
 
 
 def algorithmic_ops(sim, params):
@@ -498,7 +499,7 @@ def run_line(P, W, torch, w, label: str, reps: int = 3, candidates=None, tune_re
     sim.profile(False)
     lam, _, _ = sim.tables(w.params[0])
     inv = int(((lam > 0) & (lam < INV_LIMIT)).sum())
-    dense = int(((lam >= 0.3) & (lam < INV_LIMIT)).sum())
+    dense = int(((lam >= DENSE_LAM) & (lam < INV_LIMIT)).sum())
     ptrs = int((lam >= INV_LIMIT).sum())
     fused = w.psf is None
     draw_ms = (kt["graph"] if fused else kt["draw"])[0] / max(1, (kt["graph"] if fused else kt["draw"])[1])

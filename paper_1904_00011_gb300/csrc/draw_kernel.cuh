@@ -199,28 +199,16 @@ __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint
     return n0 + k;
 }
 
-// n = #{k : x > Z_k} given a lower bound c <= n (the count at a smaller word): walks upwards from
-// k = c through the slot's shifted thresholds.
-__device__ __forceinline__ uint32_t count_up_from(uint32_t x, const uint4 &sr, const uint32_t *tail, uint32_t c) {
-    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
-    uint32_t k = c - n0;                            // c >= n0: every word exceeds the first n0
-    auto z = [&](uint32_t kk) -> uint32_t {
-        return kk == 0u ? sr.x : kk == 1u ? sr.y : (kk - 2u < len ? __ldg(tail + sr.z + (kk - 2u)) : 0xFFFFFFFFu);
-    };
-    while (x > z(k)) ++k;                           // z saturates at len + 2
-    return n0 + k;
+// Walks over a dense slot's thresholds zs (zs[k] = Z_{n0 + k}, saturated to the slot's end), in
+// counts relative to n0: upwards, the first k >= k0 with x <= zs[k] (given x > zs[k0 - 1]);
+// downwards, the last k <= k0 with x > zs[k - 1], or 0 (given x <= zs[k0]).
+__device__ __forceinline__ uint32_t slot_up(uint32_t x, const uint32_t *zs, uint32_t k) {
+    while (k < (uint32_t)kTailCap - 1u && x > __ldg(zs + k)) ++k;
+    return k;
 }
-
-// n = #{k : x > Z_k} given an upper bound c >= n (x <= Z_c): walks downwards from k = c.  The
-// first n0 thresholds are -1, so the walk stops at n0 at the latest.
-__device__ __forceinline__ uint32_t count_down_from(uint32_t x, const uint4 &sr, const uint32_t *tail, uint32_t c) {
-    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
-    uint32_t k = c - n0;
-    auto z = [&](uint32_t kk) -> uint32_t {
-        return kk == 0u ? sr.x : kk == 1u ? sr.y : (kk - 2u < len ? __ldg(tail + sr.z + (kk - 2u)) : 0xFFFFFFFFu);
-    };
-    while (k > 0u && x <= z(k - 1u)) --k;
-    return n0 + k;
+__device__ __forceinline__ uint32_t slot_down(uint32_t x, const uint32_t *zs, uint32_t k) {
+    while (k > 0u && x <= __ldg(zs + k - 1u)) --k;
+    return k;
 }
 
 // The warp's queued maybe-hits, resolved by all 32 lanes together.  Queue entry of a lane's
@@ -390,11 +378,11 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
 
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
 // the HI call and the four LO calls of the group are drawn up front.  Each slot's count comes
-// from its word table and the slot's leading count n0: n0 plus the table's count at the lower
-// edge of the HI byte, plus one when the word's low 24 bits exceed those of the byte's first
-// threshold.  A byte holding two or more thresholds (the
-// tails of the distribution) starts at its most frequent count m instead and walks through the
-// slot's thresholds from there, upwards when the word is above Z_m, downwards otherwise.
+// from its word table and the slot's leading count n0 (kept in the group record): n0 plus the
+// table's count at the lower edge of the HI byte, plus one when the word's low 24 bits exceed
+// those of the byte's first threshold.  A byte holding two or more thresholds (the tails of the
+// distribution) starts at its most frequent count m instead and walks through the point's
+// threshold slot from there, upwards when the word is above Z_m, downwards otherwise.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -403,15 +391,18 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
     if (nd == 0u) return;
     const uint8_t *base = a.tables + d.dense_off[H];
     const uint32_t *btab = reinterpret_cast<const uint32_t *>(a.btab + d.btab_off[H]);
+    // threshold slots of this half: kTailCap words per point slot, 16 G point slots per half
+    const uint32_t *zh = ic.tail + (size_t)H * ((a.n_points + kGroup - 1u) / kGroup) * kGroup * kTailCap;
     const PhiloxPrefix ph = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindHi, H, 0), a.rk0, a.rk1);
     const PhiloxPrefix pl = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
     for (uint32_t q = (uint32_t)sidx; q < nd; q += (uint32_t)a.split) {
         const uint8_t *r = base + (size_t)q * rec;
         const uint32_t gid = __ldg(reinterpret_cast<const uint32_t *>(r));
         const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
-        const uint4 *slow = reinterpret_cast<const uint4 *>(ic.slow[H]) + gid * (uint32_t)kGroup;
-        const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
         const uint32_t *bt = btab + (size_t)q * kBtabGroupEntries;
+        const uint32_t *zg = zh + (size_t)gid * kGroup * kTailCap;
+        const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+        const uint4 n0w = __ldg(reinterpret_cast<const uint4 *>(r + kRecN0));
         // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and
         // the group total goes into the pixel's (compensated) accumulator once
         float gs[B];
@@ -419,17 +410,15 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         for (int b = 0; b < B; ++b) gs[b] = 0.0f;
 #pragma unroll 2
         for (uint32_t qd = 0; qd < 4u; ++qd) {
-            // the quad's four table entries and slow records first: their loads overlap the LO call
+            // the quad's four table entries and its 4 x B fluxes first: their loads overlap the LO
+            // call (B 16-byte flux loads: the record's flux block is 16-byte aligned; with four bands
+            // each slot's own 16-byte load below, fewer live registers)
             uint32_t e[4];
-            uint4 sq[4];
 #pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
                 const uint32_t j = 4u * qd + t;
                 e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
-                sq[t] = __ldg(slow + j);
             }
-            // the quad's 4 x B fluxes: B 16-byte loads (the record's flux block is 16-byte aligned);
-            // with four bands each slot's own 16-byte load below (fewer live registers)
             constexpr int kFq = B < 4 ? 4 * B : 1;
             float fq[kFq];
 #pragma unroll
@@ -441,16 +430,19 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
                 fq[4 * v + 3] = f4.w;
             }
             const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
+            const uint32_t n0q = word_of(n0w, qd);
 #pragma unroll
             for (uint32_t t = 0; t < 4u; ++t) {
                 const uint32_t j = 4u * qd + t;
                 const uint32_t low = word_of(wlo, t) >> 8;
                 const bool above = low > (e[t] >> 8);
-                uint32_t n = ((sq[t].w >> 8) & 0xFFu) + (e[t] & 0x7Fu) + (above ? 1u : 0u);
+                uint32_t k = (e[t] & 0x7Fu) + (above ? 1u : 0u);   // relative to n0
                 if (e[t] & 0x80u) {
                     const uint32_t x = (hi_byte(whi, j) << 24) | low;
-                    n = above ? count_up_from(x, sq[t], ic.tail, n) : count_down_from(x, sq[t], ic.tail, n);
+                    const uint32_t *zs = zg + j * (uint32_t)kTailCap;
+                    k = above ? slot_up(x, zs, k) : slot_down(x, zs, k);
                 }
+                const uint32_t n = ((n0q >> (8u * t)) & 0xFFu) + k;
                 const float nf = (float)n;
                 if (B < 4) {
 #pragma unroll

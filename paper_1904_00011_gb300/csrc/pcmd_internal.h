@@ -17,7 +17,7 @@ constexpr int kTailCap = 192;
 // per pixel and half would otherwise need one serial FP64 threshold series of up to ~120 terms
 // per model and a walk of up to ~60 thresholds per pixel.
 constexpr float kPoolTotalLimit = 10.0f;
-constexpr float kDenseLam = 0.3f;         // groups with a slot at or above this are "dense"
+constexpr float kDenseLam = 0.08f;        // groups with a slot at or above this are "dense"
 constexpr uint32_t kPtrsMaxAttempts = 1024u;
 
 // RNG stream kinds (tag = kind << 28 | half << 27 | sub)
@@ -39,6 +39,8 @@ enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
 // byte compares against z7 / zh.
 __host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 64u * (uint32_t)nb; }
 constexpr uint32_t kRecZ7 = 16, kRecZh = 32, kRecZc1 = 48, kRecFlux = 64;
+// A dense group record holds each slot's leading count n0 (u8[16]) in place of the coarse bytes z7.
+constexpr uint32_t kRecN0 = kRecZ7;
 // The sparse list (streamed through shared memory) keeps only the first 64 bytes of a record:
 // its drain reads a hit's fluxes from the per-point flux table instead.
 constexpr uint32_t kSparseRecBytes = 64;

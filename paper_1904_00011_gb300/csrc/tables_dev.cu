@@ -125,27 +125,29 @@ __device__ __forceinline__ PtrsRec ptrs_record(float lam_f, uint32_t i, const fl
 // two thresholds after it and the tail length.
 struct PointCls {
     int cls;
-    uint32_t z0, z1, tail, n0;
+    uint32_t z0, z1, tail, n0, nw;
 };
 
-// The one pass over the threshold series: the tail thresholds Z'_2 .. (up to the first saturated
-// one, at most kTailCap) go to `tail`, the point's fixed slot of kTailCap words.
-__device__ __forceinline__ PointCls classify(const PointIn &p, uint32_t *tail_out) {
-    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u};
+// The one pass over the threshold series: Z'_0, Z'_1, ... (up to the first saturated one, at most
+// kTailCap) go to `slot`, the point's fixed slot of kTailCap words; nw counts the words written.
+__device__ __forceinline__ PointCls classify(const PointIn &p, uint32_t *slot) {
+    PointCls c{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
     if (!p.valid || !(p.lam > 0.0f)) return c;
     if (p.lam >= kPtrsThreshold) {
         c.cls = 2;
         return c;
     }
     bool sat = false;
-    uint32_t z1 = 0xFFFFFFFFu, tail = 0u;
+    uint32_t z1 = 0xFFFFFFFFu, tail = 0u, nw = 0u;
     const ZHead zh = thresholds_dev(p.lam, [&](int k, uint32_t z) {
         if (k == 1) z1 = z;
+        if (nw < (uint32_t)kTailCap) slot[nw++] = z;    // k = nw: Z'_k at word k (the cap is unreachable below 192)
         if (k >= 2 && !sat) {
             if (z == 0xFFFFFFFFu) sat = true;
-            else if (tail < (uint32_t)kTailCap) tail_out[tail++] = z;   // the cap is unreachable below 192
+            else ++tail;
         }
     });
+    c.nw = nw;
     if (zh.n0 == 0u && zh.z0 == 0xFFFFFFFFu) return c;    // never a star
     c.cls = 1;
     c.z0 = zh.z0;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     const int j = (int)(t % (uint32_t)kGroup);
     const TabSetIn in = a.sets[s];
     const PointIn p = g < a.G ? point_of(a, in, g, j, h) : PointIn{0.0f, 0u, false};
-    // tail thresholds of point slot t of half h: a fixed slot of kTailCap words
+    // thresholds of point slot t of half h: a fixed slot of kTailCap words
     uint32_t *tail = reinterpret_cast<uint32_t *>(a.tables + in.base + a.layout.tail_off) +
                      ((size_t)h * a.G * kGroup + t) * kTailCap;
     const PointCls c = classify(p, tail);
@@ -227,6 +229,10 @@ __global__ void __launch_bounds__(256) tab_count_kernel(const TabArgs a) {
     // dense: an inversion slot at or above kDenseLam
     const uint32_t act = __ballot_sync(0xffffffffu, c.cls == 1) >> (threadIdx.x & 16u) & 0xFFFFu;
     const uint32_t dense = __ballot_sync(0xffffffffu, c.cls == 1 && p.lam >= kDenseLam) >> (threadIdx.x & 16u) & 0xFFFFu;
+    // the slots of a dense group's inversion points are saturated (2^32 - 1) to their end, so that
+    // a walk through them needs no length
+    if (dense && c.cls == 1)
+        for (uint32_t k = c.nw; k < (uint32_t)kTailCap; ++k) tail[k] = 0xFFFFFFFFu;
     if (j == 0 && g < a.G) {
         const uint32_t cls = act == 0u ? 0u : (dense ? 2u : 1u);
         a.scratch[((size_t)s * 2 + h) * a.G + g] = make_uint4(cls, n_tail, n_ptrs, 0u);
@@ -421,8 +427,9 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
     }
     uint32_t tot;
     const uint32_t my_ptrs = group_scan(p.valid && p.lam >= kPtrsThreshold ? 1u : 0u, j, tot);
-    // the count pass wrote the tail thresholds into the point's fixed slot
-    const uint32_t tail_off = (uint32_t)(((size_t)h * a.G * kGroup + t) * kTailCap);
+    // the count pass wrote Z'_0, Z'_1, ... into the point's fixed slot; the slow record's tail offset
+    // points at Z'_2
+    const uint32_t tail_off = (uint32_t)(((size_t)h * a.G * kGroup + t) * kTailCap) + 2u;
     if (c.cls == 1) {
         z0 = c.z0;
         z1 = c.z1;
@@ -465,7 +472,8 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         const uint32_t zc0 = c.cls == 1 ? (z0 >> 24) : 0xFFu;
         const uint32_t zc1 = c.cls == 1 ? (z1 >> 24) : 0xFFu;
         if (j == 0) *reinterpret_cast<uint4 *>(r) = make_uint4(g, 0u, 0u, 0u);
-        r[kRecZ7 + j] = (uint8_t)(zc0 & 0x7Fu);
+        // a dense record keeps each slot's leading count n0 where a sparse one has its coarse bytes
+        r[kRecZ7 + j] = sc.x == 2u ? (uint8_t)(c.cls == 1 ? c.n0 : 0u) : (uint8_t)(zc0 & 0x7Fu);
         r[kRecZh + j] = (uint8_t)(zc0 & 0x80u);
         r[kRecZc1 + j] = (uint8_t)zc1;
         if (sc.x == 2u) {   // dense records carry their fluxes (sparse ones use the flux table)
