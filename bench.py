@@ -525,8 +525,9 @@ def run_line(P, W, torch, w, label: str, reps: int = 3, candidates=None, tune_re
 
 
 def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 1024):
-    """Large-Npix regime: 1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, transformed
-    rejection dominant, Kahan sums; full evaluation (PSF path) per step."""
+    """Large-Npix regime: 1024x1024, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, dense inversion
+    groups dominant (transformed rejection from log10 Npix ~6), Kahan sums; full evaluation (PSF
+    path) per step."""
     w = W.large(log_npix=log_npix, n_im=n_im)
     return run_line(P, W, torch, w, "%dx%d, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
                     "dust, 25x25 PSF, noise, Kahan sums" % (n_im, n_im, log_npix), reps=reps,
@@ -680,7 +681,7 @@ def run_psf_grid(P, W, torch, reps: int = 10):
 
 def run_pool(P, W, torch, reps: int = 20):
     """The full model (256x256, log10 Npix 2) with the total-count sampler for the points below
-    lambda 10: per pixel and half one Poisson total and ~Npix / 2 star assignments instead of
+    the sampler boundary (lambda 192): per pixel and half one Poisson total and ~Npix / 2 star assignments instead of
     14 700 per-point draws; same law of the image, another RNG stream."""
     import dataclasses
     w0 = W.full()

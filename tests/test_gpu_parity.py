@@ -256,7 +256,7 @@ def test_fused_batch_matches_per_set_path_and_oracle():
 
 def test_batch_of_full_size_sets_matches_oracle():
     """The batched workload at its own sizes: 20 of its sets (images 128..512, log10 Npix 1..6)
-    plus three 512x512 sets at log10 Npix 5.5, 5.8 and 6.0 (transformed rejection dominant),
+    plus three 512x512 sets at log10 Npix 5.5, 5.8 and 6.0 (transformed rejection and dense groups),
     all in one fused persistent launch.  Every set's likelihood against the oracle's; the big
     sets' counts at sampled pixels bit for bit; every set's Hess diagram (per-set path, same
     set ids) within the bin-change bar."""
