@@ -228,7 +228,7 @@ def issue_roofline(instr: float, seconds: float, what: str) -> dict:
             "algorithmic": what, "peak_basis": "152 SMs x 128 issue slots/clk x 2070 MHz"}
 
 
-INV_LIMIT = 192.0                    # inversion below this mean, transformed rejection at/above
+INV_LIMIT = 640.0                    # inversion below this mean, transformed rejection at/above
 DENSE_LAM = 0.08                     # slots from this mean on are drawn in dense groups
 
 
@@ -681,7 +681,7 @@ def run_psf_grid(P, W, torch, reps: int = 10):
 
 def run_pool(P, W, torch, reps: int = 20):
     """The full model (256x256, log10 Npix 2) with the total-count sampler for the points below
-    the sampler boundary (lambda 192): per pixel and half one Poisson total and ~Npix / 2 star assignments instead of
+    the sampler boundary (lambda 640): per pixel and half one Poisson total and ~Npix / 2 star assignments instead of
     14 700 per-point draws; same law of the image, another RNG stream."""
     import dataclasses
     w0 = W.full()

@@ -53,7 +53,7 @@ enum {
     PCMD_FLAG_NOISE = 2,          /* sky + photon noise (Section 2.1) */
     PCMD_FLAG_KAHAN = 4,          /* compensated FP32 flux sums (large Npix) */
     PCMD_FLAG_SIGMA_SQRTSUM = 8,  /* Eq. 3 read as max(sqrt(d + m), 2) instead of as printed */
-    PCMD_FLAG_POOL = 16           /* total-count sampler for the points with lambda < 192 (the
+    PCMD_FLAG_POOL = 16           /* total-count sampler for the points with lambda < 640 (the
                                    * Poisson additivity of the Section 2.1 footnote, used in
                                    * reverse): per pixel and dust half N ~ Poisson(sum of
                                    * their lambdas) stars, each assigned to a point with
@@ -189,7 +189,7 @@ pcmd_status pcmd_sync(pcmd_ctx *ctx);
 pcmd_status pcmd_set_launch(pcmd_ctx *ctx, int block, int split, int chunk);
 
 /* Debug: lower the transformed-rejection sampler's attempt cap per draw (Section 2.1 Poisson
- * draws at lambda >= 192; the sampler's specification caps a draw at 1024 attempts).  cap
+ * draws at lambda >= 640; the sampler's specification caps a draw at 1024 attempts).  cap
  * 1..1024, 0 restores 1024; anything else returns PCMD_ERR_ARG.  A draw that reaches the cap
  * gives 0 stars and latches PCMD_ERR_SAMPLER_LIMIT, returned by the next synchronising call;
  * this lets a caller exercise that error path (a cap of 1 fails about one draw in seven).
@@ -227,7 +227,7 @@ int pcmd_n_points(const pcmd_ctx *ctx);
 /* Host copies of one model's tables, as the device table builder computes them for the draw
  * kernel: h_lam [2][P] FP32 Poisson means of the two dust halves (half 1 = behind the screen),
  * h_flux [P][n_bands] FP32 electrons per star, h_z0 [2][P] the 32-bit draw-word threshold above
- * which a draw is non-zero (0xFFFFFFFF unless 0 < lambda < 192).  Any pointer may be NULL.
+ * which a draw is non-zero (0xFFFFFFFF unless 0 < lambda < 640).  Any pointer may be NULL.
  * Builds the model's tables on the context's stream (replacing staged tables of an earlier
  * call) and synchronises. */
 pcmd_status pcmd_get_tables(pcmd_ctx *ctx, const pcmd_params *h_params, float *h_lam,

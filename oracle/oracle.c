@@ -18,12 +18,12 @@
  *            as 1, 2, 3"), key = 64-bit seed, counter = (pixel, index, set, tag).
  *   tag      kind << 28 | half << 27 | sub;  kinds HI=1, LO=2, PTRS=3, DUST=4, NOISE=5.
  *   uniform  u(w) = ((w >> 8) | 1) * 2^-24, exact in FP32, in (0, 1).
- *   inversion (lambda < 192): x = b << 24 | l >> 8 with b byte (i & 3) of word (i & 15) >> 2
+ *   inversion (lambda < 640): x = b << 24 | l >> 8 with b byte (i & 3) of word (i & 15) >> 2
  *            of the HI call with index i >> 4, l word (i & 3) of the LO call with index
  *            i >> 2; v = (x + 0.5) 2^-32;
  *            n = min{k : v < F_k}, F_k the FP64 Poisson CDF by p_k = p_{k-1} lambda / k,
- *            capped at 384.
- *   PTRS (lambda >= 192): Hormann (1993) transformed rejection with squeeze, attempts a use
+ *            capped at 1024.
+ *   PTRS (lambda >= 640): Hormann (1993) transformed rejection with squeeze, attempts a use
  *            words 2(a&1), 2(a&1)+1 of the PTRS call with sub = a >> 1; acceptance in the
  *            deviance form of the log-pmf (Loader 2000), all in FP32 with the series log below.
  */
@@ -136,12 +136,12 @@ float or_lnf(float x)
 /* ------------------------------------------------------------------------------------- */
 
 /* The sampler's boundary: inversion below, transformed rejection at and above; inversion counts
- * are capped at OR_INV_CAP (P(n > 384) < 2^-110 for every mean below 192: the CDF passes
+ * are capped at OR_INV_CAP (P(n > 1024) < 2^-140 for every mean below 640: the CDF passes
  * 1 - 2^-33 first, so the cap never truncates the law). */
-#define OR_INV_LIMIT 192.0f
-#define OR_INV_CAP 384u
+#define OR_INV_LIMIT 640.0f
+#define OR_INV_CAP 1024u
 
-/* Inversion for lambda < 192: n = min{k : v < F_k}, v = (x + 0.5) 2^-32, FP64 CDF. */
+/* Inversion for lambda < 640: n = min{k : v < F_k}, v = (x + 0.5) 2^-32, FP64 CDF. */
 uint32_t or_poisson_inversion(float lam_f, uint32_t x)
 {
     double lam = (double)lam_f;
@@ -237,7 +237,7 @@ float or_log_pmf(float kf, float lam)
 
 #define OR_PTRS_MAX_ATTEMPTS 1024u
 
-/* Transformed rejection with squeeze (Hormann 1993) for lambda >= 192.  Returns the count,
+/* Transformed rejection with squeeze (Hormann 1993) for lambda >= 640.  Returns the count,
  * or UINT32_MAX if the attempt cap is reached. */
 uint32_t or_poisson_ptrs(const float c6[6], uint64_t seed, uint32_t pix, uint32_t i,
                          uint32_t set, uint32_t half, uint32_t *attempts_out)
@@ -439,9 +439,9 @@ static void or_dust_factors(uint64_t seed, uint32_t pix, uint32_t set, int n_ban
 /* Total-count sampler.  The Section 2.1 footnote states that a sum of Poisson counts is Poisson
  * with the summed mean; the sampler uses the converse (the standard splitting property, not
  * stated in the paper): a Poisson total split over the points by their weights gives
- * independent Poisson counts.  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 192
+ * independent Poisson counts.  Weights in fixed point: L_i = floor(lambda_i 2^40) for 0 < lambda_i < 640
  * (lambda_i 2^40 is exact in FP64), and the pool of one half is every point with L_i > 0, in
- * point order (the others below 192 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
+ * point order (the others below 640 draw no star).  C_j = L_0 + ... + L_j and Lfix = C_(n-1)
  * are exact integers; the total's mean is Lambda = (float)(Lfix 2^-40), the FP64 conversion
  * rounding to nearest.  Star assignment thresholds T_j = min(floor(C_j 2^32 / Lfix), 2^32 - 1)
  * in exact integer arithmetic; a star with word u goes to the first pool entry with u < T_j,

@@ -8,7 +8,7 @@
 // pixel and split (a CTA's warps share a pixel tile and divide the isochrone points), with
 // the point tables streamed through shared memory by bulk copies.
 //
-// Draw word of inversion point i (lambda < 192) of half h at pixel p:
+// Draw word of inversion point i (lambda < 640) of half h at pixel p:
 //   x = b << 24 | l >> 8, b = byte i & 3 of word (i & 15) >> 2 of Philox(p, i >> 4, set, HI|h),
 //   l = word i & 3 of Philox(p, i >> 2, set, LO|h);  n = #{k : x > Z_k}.
 // The fast path only needs b: b < Z_0 >> 24 gives n = 0 without the LO call, and a certain hit
@@ -54,7 +54,7 @@ __device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
     return __fsub_rn(r, st);
 }
 
-// Transformed rejection with squeeze (Hormann 1993) for lambda >= 192.  Attempt `at` uses words
+// Transformed rejection with squeeze (Hormann 1993) for lambda >= 640.  Attempt `at` uses words
 // 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).  The cheap part of an attempt decides
 // the squeeze acceptance and the quick rejections; the rest takes the log-form test.
 struct PtrsTry {
@@ -183,11 +183,11 @@ __host__ __device__ constexpr uint32_t chunk_region_bytes(uint32_t chunk, uint32
 // beyond its length).  n = n0 + #{k : x > Z'_k}.  The search starts at the record's start index
 // k_s (near lambda - n0) and walks up or down; the count equals the linear scan's.
 __device__ __forceinline__ uint32_t count_from_thresholds(uint32_t x, const uint4 &sr, const uint32_t *tail) {
-    const uint32_t n0 = (sr.w >> 8) & 0xFFu;
+    const uint32_t n0 = slow_n0(sr.w);
     if (x <= sr.x) return n0;
     if (x <= sr.y) return n0 + 1u;
-    const uint32_t len = sr.w & 0xFFu;
-    uint32_t ks = sr.w >> 16;                       // 2 <= ks <= len + 1
+    const uint32_t len = slow_len(sr.w);
+    uint32_t ks = slow_ks(sr.w);                    // 2 <= ks <= len + 1
     if (ks < 2u) ks = 2u;
     auto z = [&](uint32_t k) { return k - 2u < len ? __ldg(tail + sr.z + (k - 2u)) : 0xFFFFFFFFu; };
     uint32_t k = ks;
@@ -376,13 +376,102 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
     if (__any_sync(0xffffffffu, qn > 0)) drain_warp<B, KAHAN, MODE, H>(a, ic, pf, cb, queue, qn, acc);
 }
 
+// One dense group (see process_dense).  WIDE: the word-table entries of a group with a mean of
+// kWideLam or more (8-bit counts, bits 1-23 of the threshold, multi flag in bit 31); otherwise
+// 7-bit counts, the multi flag in bit 7 and the low 24 bits of the threshold.
+template <int B, bool KAHAN, int MODE, int H, bool WIDE>
+__device__ __forceinline__ void dense_group(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
+                                            uint32_t gid, const uint32_t *bt, const uint32_t *zg,
+                                            const PhiloxPrefix &ph, const PhiloxPrefix &pl, Acc<B, KAHAN> &acc) {
+    const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
+    const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+    const uint16_t *n0r = reinterpret_cast<const uint16_t *>(r + kRecN0);
+    // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and the
+    // group total goes into the pixel's (compensated) accumulator once
+    float gs[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) gs[b] = 0.0f;
+#pragma unroll 2
+    for (uint32_t qd = 0; qd < 4u; ++qd) {
+        // the quad's four table entries and its 4 x B fluxes first: their loads overlap the LO call
+        // (B 16-byte flux loads: the record's flux block is 16-byte aligned; with four bands each
+        // slot's own 16-byte load below, fewer live registers)
+        uint32_t e[4];
+#pragma unroll
+        for (uint32_t t = 0; t < 4u; ++t) {
+            const uint32_t j = 4u * qd + t;
+            e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
+        }
+        constexpr int kFq = B < 4 ? 4 * B : 1;
+        float fq[kFq];
+#pragma unroll
+        for (int v = 0; v < (B < 4 ? B : 0); ++v) {
+            const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + qd * (uint32_t)B + (uint32_t)v);
+            fq[4 * v] = f4.x;
+            fq[4 * v + 1] = f4.y;
+            fq[4 * v + 2] = f4.z;
+            fq[4 * v + 3] = f4.w;
+        }
+        const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
+        const uint2 n0q = __ldg(reinterpret_cast<const uint2 *>(n0r) + qd);   // n0 of the quad's slots
+#pragma unroll
+        for (uint32_t t = 0; t < 4u; ++t) {
+            const uint32_t j = 4u * qd + t;
+            const uint32_t low = word_of(wlo, t) >> 8;
+            uint32_t k;                                         // relative to n0
+            if (WIDE) {
+                const uint32_t l23 = low >> 1, z23 = (e[t] >> 8) & 0x7FFFFFu;
+                k = e[t] & 0xFFu;
+                if (!(e[t] & 0x80000000u) && l23 != z23) {
+                    k += l23 > z23 ? 1u : 0u;
+                } else {
+                    // bits 1-23 equal (compare with the threshold itself), or several thresholds in
+                    // the byte (walk from the stored count)
+                    const uint32_t x = (hi_byte(whi, j) << 24) | low;
+                    const uint32_t *zs = zg + j * (uint32_t)kTailCap;
+                    const bool above = l23 != z23 ? l23 > z23 : x > __ldg(zs + k);
+                    if (e[t] & 0x80000000u) k = above ? slot_up(x, zs, k + 1u) : slot_down(x, zs, k);
+                    else k += above ? 1u : 0u;
+                }
+            } else {
+                const bool above = low > (e[t] >> 8);
+                k = (e[t] & 0x7Fu) + (above ? 1u : 0u);
+                if (e[t] & 0x80u) {   // several thresholds in the byte: walk from the stored count
+                    const uint32_t x = (hi_byte(whi, j) << 24) | low;
+                    const uint32_t *zs = zg + j * (uint32_t)kTailCap;
+                    k = above ? slot_up(x, zs, k) : slot_down(x, zs, k);
+                }
+            }
+            const uint32_t n0s = ((t < 2u ? n0q.x : n0q.y) >> (16u * (t & 1u))) & 0xFFFFu;
+            const uint32_t n = n0s + k;
+            const float nf = (float)n;
+            if (B < 4) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fq[(t * B + b) % kFq], gs[b]);
+            } else {
+                const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + j);
+                const float fs[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fs[b % 4], gs[b]);
+            }
+            if (MODE == kModeCounts && n) {
+                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * (uint32_t)kGroup + j] = n;
+            }
+        }
+    }
+    acc.template add_sum<H>(gs);
+}
+
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
 // the HI call and the four LO calls of the group are drawn up front.  Each slot's count comes
 // from its word table and the slot's leading count n0 (kept in the group record): n0 plus the
-// table's count at the lower edge of the HI byte, plus one when the word's low 24 bits exceed
-// those of the byte's first threshold.  A byte holding two or more thresholds (the tails of the
-// distribution) starts at its most frequent count m instead and walks through the point's
-// threshold slot from there, upwards when the word is above Z_m, downwards otherwise.
+// table's count at the lower edge of the HI byte, plus one when the word is above the byte's
+// first threshold (decided from the threshold bits stored in the entry).  A byte holding two or
+// more thresholds (the tails of the distribution) starts at its most frequent count m instead
+// and walks through the point's threshold slot from there, upwards when the word is above Z_m,
+// downwards otherwise.  A group's entry format (record header word 1) is the same for all its
+// lanes, so the branch on it does not diverge.
 template <int B, bool KAHAN, int MODE, int H>
 __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &ic, const SetDesc &d,
                                               int sidx, Acc<B, KAHAN> &acc) {
@@ -397,70 +486,11 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
     const PhiloxPrefix pl = philox_prefix_rk(ic.pix, ic.set, rng_tag(kKindLo, H, 0), a.rk0, a.rk1);
     for (uint32_t q = (uint32_t)sidx; q < nd; q += (uint32_t)a.split) {
         const uint8_t *r = base + (size_t)q * rec;
-        const uint32_t gid = __ldg(reinterpret_cast<const uint32_t *>(r));
-        const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
+        const uint2 hd = __ldg(reinterpret_cast<const uint2 *>(r));     // group id, wide format
         const uint32_t *bt = btab + (size_t)q * kBtabGroupEntries;
-        const uint32_t *zg = zh + (size_t)gid * kGroup * kTailCap;
-        const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
-        const uint4 n0w = __ldg(reinterpret_cast<const uint4 *>(r + kRecN0));
-        // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and
-        // the group total goes into the pixel's (compensated) accumulator once
-        float gs[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) gs[b] = 0.0f;
-#pragma unroll 2
-        for (uint32_t qd = 0; qd < 4u; ++qd) {
-            // the quad's four table entries and its 4 x B fluxes first: their loads overlap the LO
-            // call (B 16-byte flux loads: the record's flux block is 16-byte aligned; with four bands
-            // each slot's own 16-byte load below, fewer live registers)
-            uint32_t e[4];
-#pragma unroll
-            for (uint32_t t = 0; t < 4u; ++t) {
-                const uint32_t j = 4u * qd + t;
-                e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
-            }
-            constexpr int kFq = B < 4 ? 4 * B : 1;
-            float fq[kFq];
-#pragma unroll
-            for (int v = 0; v < (B < 4 ? B : 0); ++v) {
-                const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + qd * (uint32_t)B + (uint32_t)v);
-                fq[4 * v] = f4.x;
-                fq[4 * v + 1] = f4.y;
-                fq[4 * v + 2] = f4.z;
-                fq[4 * v + 3] = f4.w;
-            }
-            const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
-            const uint32_t n0q = word_of(n0w, qd);
-#pragma unroll
-            for (uint32_t t = 0; t < 4u; ++t) {
-                const uint32_t j = 4u * qd + t;
-                const uint32_t low = word_of(wlo, t) >> 8;
-                const bool above = low > (e[t] >> 8);
-                uint32_t k = (e[t] & 0x7Fu) + (above ? 1u : 0u);   // relative to n0
-                if (e[t] & 0x80u) {
-                    const uint32_t x = (hi_byte(whi, j) << 24) | low;
-                    const uint32_t *zs = zg + j * (uint32_t)kTailCap;
-                    k = above ? slot_up(x, zs, k) : slot_down(x, zs, k);
-                }
-                const uint32_t n = ((n0q >> (8u * t)) & 0xFFu) + k;
-                const float nf = (float)n;
-                if (B < 4) {
-#pragma unroll
-                    for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fq[(t * B + b) % kFq], gs[b]);
-                } else {
-                    const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + j);
-                    const float fs[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-                    for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fs[b % 4], gs[b]);
-                }
-                if (MODE == kModeCounts && n) {
-                    if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
-                        a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points +
-                                 gid * (uint32_t)kGroup + j] = n;
-                }
-            }
-        }
-        acc.template add_sum<H>(gs);
+        const uint32_t *zg = zh + (size_t)hd.x * kGroup * kTailCap;
+        if (hd.y) dense_group<B, KAHAN, MODE, H, true>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+        else dense_group<B, KAHAN, MODE, H, false>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
     }
 }
 
@@ -543,7 +573,7 @@ __device__ __forceinline__ void process_pool(const DrawArgs &a, const ItemCtx &i
     }
 }
 
-// Transformed-rejection points (lambda >= 192) of half H.  The lanes (pixels) of a warp start on
+// Transformed-rejection points (lambda >= 640) of half H.  The lanes (pixels) of a warp start on
 // the records q = sidx, sidx + split, ... and every iteration of a warp-wide loop makes one
 // cheap attempt for each lane's current draw: a squeeze acceptance gives the count and moves
 // the lane to its next record, a quick rejection moves it to the draw's next attempt, and an
@@ -756,7 +786,7 @@ __global__ void __launch_bounds__(256, (PATHS & kPathDense) ? 2 : ((PATHS & kPat
         }
         if (stop) break;
 
-        // ---- dense inversion groups, then transformed-rejection points (lambda >= 192) ----
+        // ---- dense inversion groups, then transformed-rejection points (lambda >= 640) ----
         if (PATHS & kPathPool) {
             process_pool<B, KAHAN, MODE, 0>(a, ic, d, sidx, acc);
             process_pool<B, KAHAN, MODE, 1>(a, ic, d, sidx, acc);

@@ -7,12 +7,13 @@ namespace pcmd {
 
 constexpr int kMaxBands = 4;
 constexpr int kGroup = 16;                // isochrone points per HI call (one byte each)
-constexpr float kPtrsThreshold = 192.0f;  // inversion below, transformed rejection at/above
-constexpr int kInvCap = 384;              // inversion counts are capped at 384 (P(n > 384) < 2^-110
-                                          // for every lambda below 192)
-// Tail thresholds per inversion point: Z'_2 .. up to the first saturated one (at most 174 below a
-// mean of 192: the CDF passes 1 - 2^-33 within ~176 counts of the first non-negative threshold).
-constexpr int kTailCap = 192;
+constexpr float kPtrsThreshold = 640.0f;  // inversion below, transformed rejection at/above
+constexpr int kInvCap = 1024;             // inversion counts are capped at 1024 (P(n > 1024) < 2^-140
+                                          // for every lambda below 640)
+// Threshold slot per inversion point: Z'_0, Z'_1, ... up to the first saturated one (at most 322
+// words below a mean of 640: the CDF passes 1 - 2^-33 within 321 counts of the first
+// non-negative threshold).
+constexpr int kTailCap = 352;
 // The total-count sampler draws its per-pixel total by inversion only below 10: a single draw
 // per pixel and half would otherwise need one serial FP64 threshold series of up to ~120 terms
 // per model and a walk of up to ~60 thresholds per pixel.
@@ -39,7 +40,8 @@ enum : uint32_t { kErrSampler = 1u, kErrTimeout = 2u, kErrBounds = 4u };
 // byte compares against z7 / zh.
 __host__ __device__ constexpr uint32_t group_rec_bytes(int nb) { return 64u + 64u * (uint32_t)nb; }
 constexpr uint32_t kRecZ7 = 16, kRecZh = 32, kRecZc1 = 48, kRecFlux = 64;
-// A dense group record holds each slot's leading count n0 (u8[16]) in place of the coarse bytes z7.
+// A dense group record holds each slot's leading count n0 (u16[16]) in place of the coarse bytes z7
+// and their top bits zh.
 constexpr uint32_t kRecN0 = kRecZ7;
 // The sparse list (streamed through shared memory) keeps only the first 64 bytes of a record:
 // its drain reads a hit's fluxes from the per-point flux table instead.
@@ -51,11 +53,17 @@ constexpr uint32_t kSparseRecBytes = 64;
 struct SlowRec {
     uint32_t z0, z1;        // Z'_0, Z'_1: n > n0 + k  <=>  x > Z'_k
     uint32_t tail_off;      // index of Z'_2 in the tail array
-    uint32_t tail_len;      // bits 0-7: number of Z'_k, k >= 2, below 0xFFFFFFFF; bits 8-15: n0;
-                            // bits 16-31: start index of the device's threshold walk
+    uint32_t tail_len;      // bits 0-9: number of Z'_k, k >= 2, below 0xFFFFFFFF; bits 10-19: n0;
+                            // bits 20-31: start index of the device's threshold walk
 };
+__host__ __device__ constexpr uint32_t slow_len(uint32_t w) { return w & 0x3FFu; }
+__host__ __device__ constexpr uint32_t slow_n0(uint32_t w) { return (w >> 10) & 0x3FFu; }
+__host__ __device__ constexpr uint32_t slow_ks(uint32_t w) { return w >> 20; }
+__host__ __device__ constexpr uint32_t slow_pack(uint32_t len, uint32_t n0, uint32_t ks) {
+    return len | (n0 << 10) | (ks << 20);
+}
 
-// Transformed-rejection record (lambda >= 192), 48 bytes.
+// Transformed-rejection record (lambda >= 640), 48 bytes.
 struct PtrsRec {
     uint32_t i;             // canonical point index
     float lam, b, a, twoa, vr, log_ia;
@@ -87,17 +95,24 @@ struct __align__(16) SetDesc {
     uint32_t pad_btab[3];
 };
 
-// Word table of a dense group: for each of its 16 slots and each HI byte b one 32-bit entry,
-// bits 0-6 a count c relative to the slot's n0 (the count at the byte's lower edge, count(b << 24)
-// - n0 <= 119 below a mean of 192), bit 7 set when two or more thresholds fall inside the byte,
-// bits 8-31 the low 24 bits of Z_(n0 + c) (0xFFFFFF when the count is the same over the whole
-// byte).  A word x of the byte has count n0 + c + (low24(x) > bits 8-31), exact unless bit 7 is
-// set; then c is the byte's most frequent count and the thresholds decide from there.
+// Word table of a dense group: for each of its 16 slots and each HI byte b one 32-bit entry with a
+// count c relative to the slot's n0 (the count at the byte's lower edge, count(b << 24) - n0),
+// the threshold Z_(n0 + c) (its bits inside the byte; all ones when the count is the same over
+// the whole byte) and a flag set when two or more thresholds fall inside the byte (then c is
+// the byte's most frequent count and the thresholds decide from there).  Two layouts, one per
+// group (dense record header word 1):
+//   narrow (every slot's mean below kWideLam: c - n0 <= 119): bits 0-6 c, bit 7 the flag, bits
+//     8-31 the low 24 bits of the threshold; a word x of the byte has count n0 + c + (low24(x) >
+//     bits 8-31) unless the flag is set;
+//   wide (a mean of kWideLam or more, up to 640: c - n0 <= 222): bits 0-7 c, bits 8-30 bits 1-23
+//     of the threshold, bit 31 the flag; equal bits 1-23 (1 word in 2^23) compare x with the
+//     threshold itself.
 // kBtabGroupBytes per group.
+constexpr float kWideLam = 192.0f;
 constexpr uint32_t kBtabGroupEntries = kGroup * 256u;
 constexpr uint32_t kBtabGroupBytes = kBtabGroupEntries * 4u;
 
-// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 192): header,
+// Total-count sampler of one dust half (the pool = every point with 0 < lambda < 640): header,
 // then Z[kInvCap] (inversion thresholds of Lambda, mode 1) or one PtrsRec (mode 2), then the guide
 // table (guide[b] = first entry j with T_j > b 2^(32 - bits), guide[2^bits] = n - 1), the pool's
 // point indices and their star-assignment thresholds T_j.

@@ -141,7 +141,7 @@ __device__ __forceinline__ PointCls classify(const PointIn &p, uint32_t *slot) {
     uint32_t z1 = 0xFFFFFFFFu, tail = 0u, nw = 0u;
     const ZHead zh = thresholds_dev(p.lam, [&](int k, uint32_t z) {
         if (k == 1) z1 = z;
-        if (nw < (uint32_t)kTailCap) slot[nw++] = z;    // k = nw: Z'_k at word k (the cap is unreachable below 192)
+        if (nw < (uint32_t)kTailCap) slot[nw++] = z;    // k = nw: Z'_k at word k (the cap is unreachable below 640)
         if (k >= 2 && !sat) {
             if (z == 0xFFFFFFFFu) sat = true;
             else ++tail;
@@ -169,7 +169,7 @@ __device__ __forceinline__ uint32_t group_scan(uint32_t v, int j, uint32_t &tota
     return s - v;
 }
 
-// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 192 (exact:
+// Total-count sampler weights in fixed point: L = floor(lambda 2^40) for 0 < lambda < 640 (exact:
 // lambda 2^40 is exact in FP64), 0 otherwise; a point is in the pool when L > 0.
 __device__ __forceinline__ uint64_t pool_weight(const PointIn &p) {
     if (!p.valid || !(p.lam > 0.0f) || !(p.lam < kPtrsThreshold)) return 0ull;
@@ -423,10 +423,12 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         c.z1 = pc.y;
         c.tail = pc.z;
         c.cls = (int)(pc.w & 0xFFu);
-        c.n0 = (pc.w >> 8) & 0xFFu;
+        c.n0 = pc.w >> 8;
     }
     uint32_t tot;
     const uint32_t my_ptrs = group_scan(p.valid && p.lam >= kPtrsThreshold ? 1u : 0u, j, tot);
+    // a dense group with an inversion mean of kWideLam or more takes the wide word-table layout
+    const uint32_t wide = __ballot_sync(0xffffffffu, inv && p.lam >= kWideLam) >> (threadIdx.x & 16u) & 0xFFFFu;
     // the count pass wrote Z'_0, Z'_1, ... into the point's fixed slot; the slow record's tail offset
     // points at Z'_2
     const uint32_t tail_off = (uint32_t)(((size_t)h * a.G * kGroup + t) * kTailCap) + 2u;
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         uint32_t ks = lk > c.n0 ? lk - c.n0 : 0u;
         if (ks > len + 1u) ks = len + 1u;
         if (ks < 2u) ks = 2u;
-        const uint4 sr = c.cls == 1 ? make_uint4(z0, z1, tail_off, len | (c.n0 << 8) | (ks << 16))
+        const uint4 sr = c.cls == 1 ? make_uint4(z0, z1, tail_off, slow_pack(len, c.n0, ks))
                                     : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
         reinterpret_cast<uint4 *>(tab + L.slow_off[h])[(size_t)g * kGroup + j] = sr;
     }
@@ -471,10 +473,15 @@ __global__ void __launch_bounds__(256) tab_write_kernel(const TabArgs a) {
         uint8_t *r = tab + (sc.x == 2u ? L.dense_off[h] : L.grp_off[h]) + (size_t)sc.y * rec;
         const uint32_t zc0 = c.cls == 1 ? (z0 >> 24) : 0xFFu;
         const uint32_t zc1 = c.cls == 1 ? (z1 >> 24) : 0xFFu;
-        if (j == 0) *reinterpret_cast<uint4 *>(r) = make_uint4(g, 0u, 0u, 0u);
-        // a dense record keeps each slot's leading count n0 where a sparse one has its coarse bytes
-        r[kRecZ7 + j] = sc.x == 2u ? (uint8_t)(c.cls == 1 ? c.n0 : 0u) : (uint8_t)(zc0 & 0x7Fu);
-        r[kRecZh + j] = (uint8_t)(zc0 & 0x80u);
+        if (j == 0) *reinterpret_cast<uint4 *>(r) = make_uint4(g, sc.x == 2u && wide ? 1u : 0u, 0u, 0u);
+        // a dense record keeps each slot's leading count n0 (u16) where a sparse one has its coarse
+        // bytes and their top bits
+        if (sc.x == 2u) {
+            reinterpret_cast<uint16_t *>(r + kRecN0)[j] = (uint16_t)(c.cls == 1 ? c.n0 : 0u);
+        } else {
+            r[kRecZ7 + j] = (uint8_t)(zc0 & 0x7Fu);
+            r[kRecZh + j] = (uint8_t)(zc0 & 0x80u);
+        }
         r[kRecZc1 + j] = (uint8_t)zc1;
         if (sc.x == 2u) {   // dense records carry their fluxes (sparse ones use the flux table)
             float *f = reinterpret_cast<float *>(r + kRecFlux) + j * B;
@@ -569,7 +576,7 @@ namespace {
 // n0 + (first k with x <= Z'_k): the count of word x from a slow record, by binary search over
 // the shifted thresholds (Z'_k saturated from len + 2 on).
 __device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, const uint32_t *tail) {
-    const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
+    const uint32_t n0 = slow_n0(sr.w), len = slow_len(sr.w);
     auto z = [&](uint32_t k) -> uint32_t {
         return k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
     };
@@ -585,9 +592,9 @@ __device__ __forceinline__ uint32_t count_bsearch(uint32_t x, const uint4 &sr, c
 // Word tables of the dense groups: one CTA per (dense-list position, half, model); 16 threads per
 // slot, each for 16 consecutive HI bytes, walking the slot's thresholds alongside the byte edges
 // (one binary search for the first byte, then a merge).  For byte b: c0 = count(b << 24), c1 =
-// count((b << 24) | 0xFFFFFF).  One threshold or none inside the byte: c0 and the low 24 bits of
-// Z_c0 (0xFFFFFF when c1 = c0).  Two or more (flag bit 7): the count m in [c0, c1] that holds the
-// most words of the byte and the low 24 bits of Z_m (0xFFFFFF when m = c1), so that most words of
+// count((b << 24) | 0xFFFFFF).  One threshold or none inside the byte: c0 and Z_c0's bits inside
+// the byte (all ones when c1 = c0).  Two or more (the flag): the count m in [c0, c1] that holds the
+// most words of the byte and Z_m's bits (all ones when m = c1), so that most words of
 // the byte end where the search starts.  Counts are stored relative to the slot's n0.
 __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const uint32_t q = blockIdx.x;
@@ -595,20 +602,22 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
     const SetDesc &d = a.desc[s];
     if (q >= d.n_dense[h]) return;
     const uint32_t rec = group_rec_bytes(a.n_bands);
-    const uint32_t gid = *reinterpret_cast<const uint32_t *>(a.tables + d.dense_off[h] + (uint64_t)q * rec);
+    const uint2 hd = *reinterpret_cast<const uint2 *>(a.tables + d.dense_off[h] + (uint64_t)q * rec);
+    const uint32_t gid = hd.x;
+    const bool wide = hd.y != 0u;
     const uint4 *slow = reinterpret_cast<const uint4 *>(a.tables + d.slow_off[h]) + (uint64_t)gid * kGroup;
     const uint32_t *tail = reinterpret_cast<const uint32_t *>(a.tables + d.tail_off);
     uint32_t *out = reinterpret_cast<uint32_t *>(a.btab + d.btab_off[h]) + (uint64_t)q * kBtabGroupEntries;
     for (uint32_t t = threadIdx.x; t < kGroup * 16u; t += blockDim.x) {
         const uint32_t j = t >> 4, b0 = (t & 15u) * 16u;
         const uint4 sr = slow[j];
-        const uint32_t n0 = (sr.w >> 8) & 0xFFu, len = sr.w & 0xFFu;
+        const uint32_t n0 = slow_n0(sr.w), len = slow_len(sr.w);
         // Z_c (c >= n0: every word exceeds the first n0 thresholds); 2^32 - 1 from len + 2 on
         auto zc = [&](uint32_t c) -> uint32_t {
             const uint32_t k = c - n0;
             return k == 0u ? sr.x : k == 1u ? sr.y : (k - 2u < len ? tail[sr.z + (k - 2u)] : 0xFFFFFFFFu);
         };
-        const uint32_t cmax = n0 + 0x7Fu;               // the entry holds c - n0 in 7 bits
+        const uint32_t cmax = n0 + (wide ? 0xFFu : 0x7Fu);   // c - n0 in 8 (wide) or 7 bits
         uint32_t cur = count_bsearch(b0 << 24, sr, tail);
         for (uint32_t b = b0; b < b0 + 16u; ++b) {
             const uint32_t lo = b << 24, hi = lo | 0xFFFFFFu;
@@ -616,9 +625,12 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
             const uint32_t c0 = cur;
             uint32_t c1 = c0;
             while (zc(c1) < hi) ++c1;                   // count(hi)
-            uint32_t c = c0, zl = 0xFFFFFFu;
+            // the threshold's bits inside the byte: low 24 (narrow) or bits 1-23 (wide); all ones
+            // when the count does not change over the byte
+            const uint32_t zshift = wide ? 1u : 0u, zmask = wide ? 0x7FFFFFu : 0xFFFFFFu;
+            uint32_t c = c0, zl = zmask;
             if (c1 == c0 + 1u) {
-                zl = zc(c0) & 0xFFFFFFu;                // Z_c0 lies inside the byte: its top byte is b
+                zl = (zc(c0) >> zshift) & zmask;        // Z_c0 lies inside the byte: its top byte is b
             } else if (c1 > c0 + 1u) {
                 // words of count m in the byte: [max(Z_{m-1} + 1, lo), min(Z_m, hi)] (empty when two
                 // thresholds are equal)
@@ -632,10 +644,13 @@ __global__ void __launch_bounds__(256) tab_btab_kernel(const TabArgs a) {
                     }
                     wlo = whi + 1u;
                 }
-                zl = c == c1 ? 0xFFFFFFu : (zc(c) & 0xFFFFFFu);
+                zl = c == c1 ? zmask : ((zc(c) >> zshift) & zmask);
             }
-            // below a mean of 192 the count at any byte's lower edge is at most n0 + 119
-            out[j * 256u + b] = ((c - n0) & 0x7Fu) | (c1 > c0 + 1u ? 0x80u : 0u) | (zl << 8);
+            // the count at any byte's lower edge is at most n0 + 119 below a mean of 192 (narrow)
+            // and n0 + 222 below 640 (wide)
+            const bool multi = c1 > c0 + 1u;
+            out[j * 256u + b] = wide ? (((c - n0) & 0xFFu) | (zl << 8) | (multi ? 0x80000000u : 0u))
+                                     : (((c - n0) & 0x7Fu) | (multi ? 0x80u : 0u) | (zl << 8));
             cur = c1;                                   // count((b + 1) << 24) >= count(hi)
         }
     }

@@ -48,7 +48,7 @@ struct TabArgs {
     uint4 *scratch;             // [n_sets][2][G]
     float *insp_lam;            // optional parity copies of model 0: lambda [2][P]
     float *insp_flux;           //   flux [P][B]
-    uint32_t *insp_z0;          //   Z_0 [2][P] (0xFFFFFFFF unless 0 < lambda < 192)
+    uint32_t *insp_z0;          //   Z_0 [2][P] (0xFFFFFFFF unless 0 < lambda < 640)
     int pool;                   // also build the total-count sampler regions
     uint4 *pool_scratch;        // [n_sets][2][G] pool entries and fixed-point sums (pool only)
     uint4 *pt_scratch;          // [n_sets][2][16 G] per point: Z_0, Z_1, tail length, class

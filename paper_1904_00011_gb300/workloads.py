@@ -41,7 +41,7 @@ FLAG_DUST = 1
 FLAG_NOISE = 2
 FLAG_KAHAN = 4
 FLAG_SIGMA_SQRTSUM = 8
-FLAG_POOL = 16                      # total-count sampler for the points below lambda 192
+FLAG_POOL = 16                      # total-count sampler for the points below lambda 640
 
 LL_PAPER = 0
 LL_POISSON = 1

@@ -71,8 +71,8 @@ def test_tables_match_oracle(name):
             assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i])) == 0
             if z0[h, i] < 0xFFFFFFFF:
                 assert O.poisson_inversion(float(lam[h, i]), int(z0[h, i]) + 1) >= 1
-        # from ~22.9 to 192 even the smallest word gives a star (e^-lambda 2^32 < 1/2): no Z_0
-        big = np.nonzero((lam[h] > 22.9) & (lam[h] < 192))[0]
+        # from ~22.9 to 640 even the smallest word gives a star (e^-lambda 2^32 < 1/2): no Z_0
+        big = np.nonzero((lam[h] > 22.9) & (lam[h] < 640))[0]
         for i in big[:20]:
             assert z0[h, i] == 0xFFFFFFFF
             assert O.poisson_inversion(float(lam[h, i]), 0) >= 1

@@ -1,6 +1,6 @@
 """The total-count (pool) sampler of the oracle (the Poisson additivity of the Section 2.1
 footnote, used in reverse as the splitting property): per pixel and half the
-points below lambda 192 get N ~ Poisson(sum lambda) stars assigned by their weights.  Pins: the
+points below lambda 640 get N ~ Poisson(sum lambda) stars assigned by their weights.  Pins: the
 per-point counts are independent Poisson(lambda_i) (means, variances, zero fractions, pairwise
 covariances, a joint chi-square), the total is Poisson, the image mean equals the per-point
 sampler's (CPU)."""
@@ -80,13 +80,13 @@ def test_pool_image_mean_matches_the_per_point_sampler():
 
 
 def test_pool_without_pool_points_draws_nothing_from_it():
-    """Points at or above lambda 192 (transformed rejection) keep their own draws in pool mode:
+    """Points at or above lambda 640 (transformed rejection) keep their own draws in pool mode:
     their counts equal the per-point sampler's; the points below differ by construction."""
     w = W.large(log_npix=6.5, n_im=4)
     wp = dataclasses.replace(w, flags=w.flags | W.FLAG_POOL)
     lam_h, _, _ = O.tables(w)
-    big = lam_h >= 192
-    assert big.any() and np.any((lam_h > 0) & (lam_h < 192))
+    big = lam_h >= 640
+    assert big.any() and np.any((lam_h > 0) & (lam_h < 640))
     _, ca = O.simulate(w, 0, 1, counts=True, pix_end=4, n_threads=8)
     _, cb = O.simulate(wp, 0, 1, counts=True, pix_end=4, n_threads=8)
     for h in range(2):
@@ -96,13 +96,13 @@ def test_pool_without_pool_points_draws_nothing_from_it():
 def test_pool_tables_assign_stars_in_proportion_to_lambda():
     """Star-assignment thresholds: entry j takes the words in [T_{j-1}, T_j), so its probability
     (T_j - T_{j-1}) / 2^32 is lambda_j / sum(lambda) up to the 2^-32 grid and the 2^-40 weights;
-    the pool is exactly the points with 0 < lambda < 192 (and lambda >= 2^-40), in point order."""
+    the pool is exactly the points with 0 < lambda < 640 (and lambda >= 2^-40), in point order."""
     rng = np.random.default_rng(5)
-    lam = np.concatenate([rng.gamma(0.3, 0.5, 3000), [0.0, 70.0, 192.0, 191.99, 64.0, 200.0, 12.0, 1e-13, 3e-12],
+    lam = np.concatenate([rng.gamma(0.3, 0.5, 3000), [0.0, 70.0, 640.0, 639.99, 192.0, 700.0, 12.0, 1e-13, 3e-12],
                           10.0 ** rng.uniform(-9, 0.9, 2000)]).astype(np.float32)
     rng.shuffle(lam)
     idx, thr, tot = O.pool_tables(lam)
-    keep = np.flatnonzero((lam > 0) & (lam < 192) & (lam.astype(np.float64) >= 2.0 ** -40))
+    keep = np.flatnonzero((lam > 0) & (lam < 640) & (lam.astype(np.float64) >= 2.0 ** -40))
     assert np.array_equal(idx, keep)
     l64 = lam[idx].astype(np.float64)
     assert abs(tot / l64.sum() - 1.0) < 1e-6
@@ -115,12 +115,12 @@ def test_pool_tables_assign_stars_in_proportion_to_lambda():
 
 def test_pool_tables_small_cases_are_exact():
     """lambda = (1, 3): T_0 = 2^32 / 4 exactly; one entry: it takes every star; nothing below
-    2^-40 or at 192: an empty pool."""
+    2^-40 or at 640: an empty pool."""
     idx, thr, tot = O.pool_tables(np.array([1.0, 3.0], np.float32))
     assert list(idx) == [0, 1] and int(thr[0]) == 2 ** 30 and int(thr[1]) == 2 ** 32 - 1 and tot == 4.0
-    idx, thr, tot = O.pool_tables(np.array([0.0, 0.25, 250.0], np.float32))
+    idx, thr, tot = O.pool_tables(np.array([0.0, 0.25, 700.0], np.float32))
     assert list(idx) == [1] and tot == 0.25
-    idx, thr, tot = O.pool_tables(np.array([1e-13, 192.0, 0.0], np.float32))
+    idx, thr, tot = O.pool_tables(np.array([1e-13, 640.0, 0.0], np.float32))
     assert idx.size == 0
 
 

@@ -58,8 +58,8 @@ def test_lnf_against_libm():
 def test_inversion_boundaries_are_the_poisson_cdf():
     """The inversion is monotone in the 32-bit word x; its k -> k+1 boundaries, found by
     bisection, must sit at 2^32 * CDF(k) of the exact Poisson law within quantisation."""
-    for lam in [1e-4, 0.1, 1.0, 4.5, 9.99, 27.3, 63.9, 120.25, 191.9]:
-        cdf = stats.poisson.cdf(np.arange(0, 385), lam)
+    for lam in [1e-4, 0.1, 1.0, 4.5, 9.99, 27.3, 63.9, 120.25, 191.9, 310.5, 639.9]:
+        cdf = stats.poisson.cdf(np.arange(0, 1025), lam)
         kmax = int(stats.poisson.ppf(1 - 1e-9, lam))
         for k in range(0, kmax + 1):
             # smallest x with n(x) > k
@@ -136,34 +136,35 @@ def test_log_pmf_against_scipy():
             assert abs(got - ref) <= tol, (lam, k, got, ref)
 
 
-def test_draw_switches_sampler_at_192():
+def test_draw_switches_sampler_at_640():
     seed = 77
-    # below 192: identical to inversion on the draw word; at/above: PTRS stream
-    below = float(np.nextafter(np.float32(192.0), np.float32(0.0)))
+    # below 640: identical to inversion on the draw word; at/above: PTRS stream
+    below = float(np.nextafter(np.float32(640.0), np.float32(0.0)))
     for p in range(50):
         x = O.draw_word(seed, p, 5, 1, 0)
         assert O.draw(below, seed, p, 5, 1, 0) == O.poisson_inversion(below, x)
         assert O.draw(12.0, seed, p, 5, 1, 0) == O.poisson_inversion(12.0, x)
         assert O.draw(64.0, seed, p, 5, 1, 0) == O.poisson_inversion(64.0, x)
-        assert O.draw(192.0, seed, p, 5, 1, 0) == O.poisson_ptrs(192.0, seed, p, 5, 1, 0)[0]
+        assert O.draw(192.0, seed, p, 5, 1, 0) == O.poisson_inversion(192.0, x)
+        assert O.draw(640.0, seed, p, 5, 1, 0) == O.poisson_ptrs(640.0, seed, p, 5, 1, 0)[0]
     assert O.draw(0.0, seed, 3, 3, 3, 1) == 0
 
 
-def test_inversion_cap_never_binds_below_192():
+def test_inversion_cap_never_binds_below_640():
     """The largest word (v = 1 - 2^-33) stops the walk where the CDF first exceeds 1 - 2^-33,
-    below the cap of 384 for every mean under 192: the cap never truncates the law."""
-    below = float(np.nextafter(np.float32(192.0), np.float32(0.0)))
+    below the cap of 1024 for every mean under 640: the cap never truncates the law."""
+    below = float(np.nextafter(np.float32(640.0), np.float32(0.0)))
     k = O.poisson_inversion(below, 0xFFFFFFFF)
-    first = min(j for j in range(600) if stats.poisson.sf(j, below) < 2.0 ** -33)
-    assert k < 384 and abs(k - first) <= 1, (k, first)
+    first = min(j for j in range(1200) if stats.poisson.sf(j, below) < 2.0 ** -33)
+    assert k < 1024 and abs(k - first) <= 1, (k, first)
     # the smallest word: the CDF's lower tail, n0 always-exceeded thresholds and the first
     # count whose CDF reaches 2^-33
     k0 = O.poisson_inversion(below, 0)
-    first0 = min(j for j in range(600) if stats.poisson.cdf(j, below) > 2.0 ** -33)
+    first0 = min(j for j in range(1200) if stats.poisson.cdf(j, below) > 2.0 ** -33)
     assert abs(k0 - first0) <= 1, (k0, first0)
 
 
-@pytest.mark.parametrize("lam", [12.5, 40.0, 63.5, 100.0, 150.0, 191.5])
+@pytest.mark.parametrize("lam", [12.5, 40.0, 63.5, 150.0, 300.0, 639.5])
 def test_inversion_matches_poisson_law_at_large_means(lam):
     """Draws of the inversion branch over Philox words at means between the old and new
     boundary follow the Poisson law (chi-square, mean and variance)."""
