@@ -235,6 +235,32 @@ float or_log_pmf(float kf, float lam)
     return r;
 }
 
+/* The log-form acceptance test of an attempt the squeeze leaves open (Hormann 1993):
+ * ln V + ln inv_alpha - ln q <= log pmf(k), q = a / us^2 + b.  For k >= 1 the pmf's term
+ * -ln(k) / 2 moves to the left-hand side, which takes one logarithm: ln(V sqrt(k) / q) +
+ * ln inv_alpha <= -lambda phi((k - lambda) / lambda) - ln(2 pi) / 2 - stirlerr(k); k = 0 keeps
+ * ln V + ln inv_alpha - ln q <= -lambda.  FP32 basic operations in this order. */
+static int or_ptrs_log_accept(float V, float q, float kf, float lam, float log_ia)
+{
+    if (kf == 0.0f) {
+        float lhs = or_lnf(V);
+        lhs = lhs + log_ia;
+        lhs = lhs - or_lnf(q);
+        return lhs <= -lam;
+    }
+    const float HALF_LN_2PI = (float)0.91893853320467274178;
+    float y = V * sqrtf(kf);
+    y = y / q;
+    float lhs = or_lnf(y);
+    lhs = lhs + log_ia;
+    float d = kf - lam;
+    float x = d / lam;
+    float rhs = -(lam * or_phi(x));
+    rhs = rhs - HALF_LN_2PI;
+    rhs = rhs - or_stirlerr(kf);
+    return lhs <= rhs;
+}
+
 #define OR_PTRS_MAX_ATTEMPTS 1024u
 
 /* Transformed rejection with squeeze (Hormann 1993) for lambda >= 640.  Returns the count,
@@ -262,10 +288,7 @@ uint32_t or_poisson_ptrs(const float c6[6], uint64_t seed, uint32_t pix, uint32_
         float q = us * us;
         q = a / q;
         q = q + b;
-        float lhs = or_lnf(V);
-        lhs = lhs + log_ia;
-        lhs = lhs - or_lnf(q);
-        if (lhs <= or_log_pmf(kf, lam)) { if (attempts_out) *attempts_out = at + 1; return (uint32_t)kf; }
+        if (or_ptrs_log_accept(V, q, kf, lam, log_ia)) { if (attempts_out) *attempts_out = at + 1; return (uint32_t)kf; }
     }
     if (attempts_out) *attempts_out = OR_PTRS_MAX_ATTEMPTS;
     return UINT32_MAX;
@@ -491,9 +514,15 @@ int or_pool_tables(const float *lam, int n_pts, uint32_t *idx, uint32_t *thr, fl
 
 static uint32_t or_pool_pick(const or_pool *pl, uint32_t u)
 {
-    for (uint32_t j = 0; j + 1 < pl->n; ++j)
-        if (u < pl->thr[j]) return pl->idx[j];
-    return pl->idx[pl->n - 1];
+    /* the first j < n - 1 with u < T_j, else n - 1; T_j is non-decreasing, so a bisection over
+     * j in [0, n - 1) finds the same entry as the scan in point order */
+    uint32_t lo = 0, hi = pl->n - 1u;
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2u;
+        if (u < pl->thr[mid]) hi = mid;
+        else lo = mid + 1u;
+    }
+    return pl->idx[lo];
 }
 
 /* Number of pool stars of (pixel, half): inversion on word 0 of Philox(p, 2^32 - 1, set, LO|h)

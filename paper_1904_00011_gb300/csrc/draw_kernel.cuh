@@ -39,21 +39,6 @@ __device__ __forceinline__ float stirlerr_dev(float kf) {
     return __fmul_rn(t, r);
 }
 
-// log Poisson pmf in the deviance form -lambda phi((k - lambda)/lambda) - ln(2 pi k)/2 -
-// stirlerr(k) (Loader 2000), which does not cancel k ln(lambda) against ln k!.
-__device__ __forceinline__ float log_pmf_dev(float kf, float lam) {
-    if (kf == 0.0f) return -lam;
-    const float x = __fdiv_rn(__fsub_rn(kf, lam), lam);
-    const float bd0 = __fmul_rn(lam, phi_dev(x));
-    const float st = stirlerr_dev(kf);
-    float t = ln_series(kf);
-    t = __fmul_rn(0.5f, t);
-    t = __fadd_rn(t, (float)0.91893853320467274178);
-    float r = -bd0;
-    r = __fsub_rn(r, t);
-    return __fsub_rn(r, st);
-}
-
 // Transformed rejection with squeeze (Hormann 1993) for lambda >= 640.  Attempt `at` uses words
 // 2(at&1), 2(at&1)+1 of Philox(p, i, set, PTRS|h|at>>1).  The cheap part of an attempt decides
 // the squeeze acceptance and the quick rejections; the rest takes the log-form test.
@@ -79,14 +64,28 @@ __device__ __forceinline__ PtrsTry ptrs_cheap(const PtrsRec &r, uint32_t wu, uin
     return t;
 }
 
+// The log-form test: ln V + ln inv_alpha - ln q <= log pmf(k), q = a / us^2 + b.  For k >= 1
+// the pmf's term -ln(k) / 2 moves to the left-hand side, which then takes one logarithm:
+// ln(V sqrt(k) / q) + ln inv_alpha <= -lambda phi((k - lambda) / lambda) - ln(2 pi) / 2 -
+// stirlerr(k); k = 0 keeps ln V + ln inv_alpha - ln q <= -lambda.
 __device__ __forceinline__ bool ptrs_log_accept(const PtrsRec &r, const PtrsTry &t) {
     float q = __fmul_rn(t.us, t.us);
     q = __fdiv_rn(r.a, q);
     q = __fadd_rn(q, r.b);
-    float lhs = ln_series(t.V);
-    lhs = __fadd_rn(lhs, r.log_ia);
-    lhs = __fsub_rn(lhs, ln_series(q));
-    return lhs <= log_pmf_dev(t.kf, r.lam);
+    if (t.kf == 0.0f) {
+        float lhs = ln_series(t.V);
+        lhs = __fadd_rn(lhs, r.log_ia);
+        lhs = __fsub_rn(lhs, ln_series(q));
+        return lhs <= -r.lam;
+    }
+    float y = __fmul_rn(t.V, __fsqrt_rn(t.kf));
+    y = __fdiv_rn(y, q);
+    const float lhs = __fadd_rn(ln_series(y), r.log_ia);
+    const float x = __fdiv_rn(__fsub_rn(t.kf, r.lam), r.lam);
+    float rhs = -__fmul_rn(r.lam, phi_dev(x));
+    rhs = __fsub_rn(rhs, (float)0.91893853320467274178);
+    rhs = __fsub_rn(rhs, stirlerr_dev(t.kf));
+    return lhs <= rhs;
 }
 
 __device__ __forceinline__ uint4 ptrs_words(const PtrsRec &r, uint32_t pix, uint32_t set, uint32_t half,
