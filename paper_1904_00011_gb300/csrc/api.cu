@@ -82,7 +82,7 @@ struct pcmd_ctx {
     uint32_t ptrs_cap = kPtrsMaxAttempts;   // transformed-rejection attempt cap of a draw
 
     SetDesc *desc_d = nullptr;  // the models' descriptors (inside tab_in, uploaded with it)
-    DevBuf btab;                // byte tables of the dense groups (allocated when needed)
+    DevBuf btab;                // word tables of the dense groups (allocated when needed)
     DevBuf tables, items, order, partials, part_begin, part_count, image, pix_off, hess,
         moments, counters, ll, psf_d, queue, err;
     DevBuf imf_d, bflux_d, tab_in, tab_scratch, insp;   // device table builder
