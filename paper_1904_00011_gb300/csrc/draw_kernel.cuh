@@ -375,11 +375,13 @@ __device__ __forceinline__ void process_chunk(const DrawArgs &a, const ItemCtx &
     if (__any_sync(0xffffffffu, qn > 0)) drain_warp<B, KAHAN, MODE, H>(a, ic, pf, cb, queue, qn, acc);
 }
 
-// One dense group (see process_dense).  WIDE: the word-table entries of a group with a mean of
-// kWideLam or more (8-bit counts, bits 1-23 of the threshold, multi flag in bit 31); otherwise
-// 7-bit counts, the multi flag in bit 7 and the low 24 bits of the threshold.
+// One dense group (see process_dense), quad by quad: each quad's table entries are loaded at the
+// quad's start.  The fused batched instantiation uses this form (the prefetching form below made
+// its larger kernel slower).  WIDE: the word-table entries of a group with a mean of kWideLam or
+// more (8-bit counts, bits 1-23 of the threshold, multi flag in bit 31); otherwise 7-bit counts,
+// the multi flag in bit 7 and the low 24 bits of the threshold.
 template <int B, bool KAHAN, int MODE, int H, bool WIDE>
-__device__ __forceinline__ void dense_group(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
+__device__ __forceinline__ void dense_group_direct(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
                                             uint32_t gid, const uint32_t *bt, const uint32_t *zg,
                                             const PhiloxPrefix &ph, const PhiloxPrefix &pl, Acc<B, KAHAN> &acc) {
     const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
@@ -462,6 +464,118 @@ __device__ __forceinline__ void dense_group(const DrawArgs &a, const ItemCtx &ic
     acc.template add_sum<H>(gs);
 }
 
+// One dense group (see process_dense), with its table entries loaded two quads ahead of their use
+// and, for a narrow group's bytes with several thresholds, the two thresholds bounding the stored
+// count loaded before the LO call (a word of that count then needs no further load).  Used by the
+// image and counts instantiations.
+template <int B, bool KAHAN, int MODE, int H, bool WIDE>
+__device__ __forceinline__ void dense_group(const DrawArgs &a, const ItemCtx &ic, const uint8_t *r,
+                                            uint32_t gid, const uint32_t *bt, const uint32_t *zg,
+                                            const PhiloxPrefix &ph, const PhiloxPrefix &pl, Acc<B, KAHAN> &acc) {
+    const uint4 whi = philox_from_prefix_rk(ph, gid, a.rk0, a.rk1);
+    const float *fl = reinterpret_cast<const float *>(r + kRecFlux);
+    const uint16_t *n0r = reinterpret_cast<const uint16_t *>(r + kRecN0);
+    constexpr uint32_t kMulti = WIDE ? 0x80000000u : 0x80u, kCount = WIDE ? 0xFFu : 0x7Fu;
+    // the table entries of a quad (issued two quads ahead of their use)
+    uint32_t ring[4][4];
+    auto load_quad = [&](uint32_t qd, uint32_t (&e)[4]) {
+#pragma unroll
+        for (uint32_t t = 0; t < 4u; ++t) {
+            const uint32_t j = 4u * qd + t;
+            e[t] = __ldg(bt + j * 256u + hi_byte(whi, j));
+        }
+    };
+    load_quad(0u, ring[0]);
+    load_quad(1u, ring[1]);
+    // the group's 16 contributions n f_b are summed with plain FMAs (at most 16 terms) and the
+    // group total goes into the pixel's (compensated) accumulator once
+    float gs[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) gs[b] = 0.0f;
+#pragma unroll
+    for (uint32_t qd = 0; qd < 4u; ++qd) {
+        if (qd < 2u) load_quad(qd + 2u, ring[qd + 2u]);
+        // narrow layout, a byte with several thresholds: its count's two bounding thresholds
+        // Z_(n0+c-1), Z_(n0+c) are loaded before the LO call, so that a word of count c needs no
+        // further load (wide groups, where such bytes are frequent, load only on a walk)
+        uint32_t zb[4], zt[4];
+#pragma unroll
+        for (uint32_t t = 0; t < 4u; ++t) {
+            const uint32_t e = ring[qd][t];
+            zb[t] = 0u;
+            zt[t] = 0u;
+            if (!WIDE && (e & kMulti)) {
+                const uint32_t *zs = zg + (4u * qd + t) * (uint32_t)kTailCap;
+                const uint32_t k = e & kCount;
+                zt[t] = __ldg(zs + k);
+                if (k) zb[t] = __ldg(zs + k - 1u);
+            }
+        }
+        // the quad's 4 x B fluxes: B 16-byte loads (the record's flux block is 16-byte aligned);
+        // with four bands each slot's own 16-byte load below (fewer live registers)
+        constexpr int kFq = B < 4 ? 4 * B : 1;
+        float fq[kFq];
+#pragma unroll
+        for (int v = 0; v < (B < 4 ? B : 0); ++v) {
+            const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + qd * (uint32_t)B + (uint32_t)v);
+            fq[4 * v] = f4.x;
+            fq[4 * v + 1] = f4.y;
+            fq[4 * v + 2] = f4.z;
+            fq[4 * v + 3] = f4.w;
+        }
+        const uint4 wlo = philox_from_prefix_rk(pl, gid * 4u + qd, a.rk0, a.rk1);
+        const uint2 n0q = __ldg(reinterpret_cast<const uint2 *>(n0r) + qd);   // n0 of the quad's slots
+#pragma unroll
+        for (uint32_t t = 0; t < 4u; ++t) {
+            const uint32_t j = 4u * qd + t;
+            const uint32_t e = ring[qd][t];
+            const uint32_t low = word_of(wlo, t) >> 8;
+            uint32_t k = e & kCount;                            // relative to n0
+            if (e & kMulti) {
+                // several thresholds in the byte: count k for Z_(k-1) < x <= Z_k, else a walk
+                const uint32_t x = (hi_byte(whi, j) << 24) | low;
+                const uint32_t *zs = zg + j * (uint32_t)kTailCap;
+                if (WIDE) {
+                    const uint32_t l23 = low >> 1, z23 = (e >> 8) & 0x7FFFFFu;
+                    const bool above = l23 != z23 ? l23 > z23 : x > __ldg(zs + k);
+                    k = above ? slot_up(x, zs, k + 1u) : slot_down(x, zs, k);
+                } else if (x > zt[t]) {
+                    k = slot_up(x, zs, k + 1u);
+                } else if (k && x <= zb[t]) {
+                    k = slot_down(x, zs, k - 1u);
+                }
+            } else if (WIDE) {
+                const uint32_t l23 = low >> 1, z23 = (e >> 8) & 0x7FFFFFu;
+                if (l23 != z23) {
+                    k += l23 > z23 ? 1u : 0u;
+                } else {   // bits 1-23 equal: compare with the threshold itself
+                    const uint32_t x = (hi_byte(whi, j) << 24) | low;
+                    k += x > __ldg(zg + j * (uint32_t)kTailCap + k) ? 1u : 0u;
+                }
+            } else {
+                k += low > (e >> 8) ? 1u : 0u;
+            }
+            const uint32_t n0s = ((t < 2u ? n0q.x : n0q.y) >> (16u * (t & 1u))) & 0xFFFFu;
+            const uint32_t n = n0s + k;
+            const float nf = (float)n;
+            if (B < 4) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fq[(t * B + b) % kFq], gs[b]);
+            } else {
+                const float4 f4 = __ldg(reinterpret_cast<const float4 *>(fl) + j);
+                const float fs[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int b = 0; b < B; ++b) gs[b] = fmaf(nf, fs[b % 4], gs[b]);
+            }
+            if (MODE == kModeCounts && n) {
+                if (ic.pix >= a.count_pix0 && ic.pix - a.count_pix0 < a.count_npix)
+                    a.counts[((size_t)(ic.pix - a.count_pix0) * 2u + H) * a.n_points + gid * (uint32_t)kGroup + j] = n;
+            }
+        }
+    }
+    acc.template add_sum<H>(gs);
+}
+
 // Dense inversion groups (a slot with lambda >= kDenseLam): nearly every slot is non-zero, so
 // the HI call and the four LO calls of the group are drawn up front.  Each slot's count comes
 // from its word table and the slot's leading count n0 (kept in the group record): n0 plus the
@@ -488,8 +602,13 @@ __device__ __forceinline__ void process_dense(const DrawArgs &a, const ItemCtx &
         const uint2 hd = __ldg(reinterpret_cast<const uint2 *>(r));     // group id, wide format
         const uint32_t *bt = btab + (size_t)q * kBtabGroupEntries;
         const uint32_t *zg = zh + (size_t)hd.x * kGroup * kTailCap;
-        if (hd.y) dense_group<B, KAHAN, MODE, H, true>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
-        else dense_group<B, KAHAN, MODE, H, false>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+        if (MODE == kModeFused) {
+            if (hd.y) dense_group_direct<B, KAHAN, MODE, H, true>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+            else dense_group_direct<B, KAHAN, MODE, H, false>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+        } else {
+            if (hd.y) dense_group<B, KAHAN, MODE, H, true>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+            else dense_group<B, KAHAN, MODE, H, false>(a, ic, r, hd.x, bt, zg, ph, pl, acc);
+        }
     }
 }
 
