@@ -40,7 +40,9 @@ typedef int pcmd_status;
 enum {
     PCMD_OK = 0,
     PCMD_ERR_ARG = 1,            /* invalid argument (reported before any launch) */
-    PCMD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    PCMD_ERR_CUDA = 2,           /* a CUDA runtime call failed, or a device-built list outgrew
+                                  * the room reserved for it (an internal error; the message says
+                                  * which) */
     PCMD_ERR_OOM = 3,            /* device or pinned-host allocation failed */
     PCMD_ERR_SAMPLER_LIMIT = 4,  /* transformed rejection hit its attempt cap */
     PCMD_ERR_STATE = 5,          /* call order violated (e.g. pcmd_hess before pcmd_simulate) */
