@@ -531,7 +531,7 @@ def run_large(P, W, torch, log_npix: float = 6.0, reps: int = 3, n_im: int = 102
     w = W.large(log_npix=log_npix, n_im=n_im)
     return run_line(P, W, torch, w, "%dx%d, 3 bands, 10 ages x 9 [Fe/H] x 400 masses, log10 Npix %.1f, "
                     "dust, 25x25 PSF, noise, Kahan sums" % (n_im, n_im, log_npix), reps=reps,
-                    candidates=LARGE_CANDIDATES)
+                    candidates=LARGE_CANDIDATES, tune_reps=2)
 
 
 def run_npix_range(P, W, torch) -> dict:
